@@ -1,0 +1,168 @@
+/*
+ * ade_sph.h -- C ABI of the GB300 SPH advection-dispersion library (libade_sph.so).
+ *
+ * The library evaluates, on one GPU, the SPH form of the Lagrangian advection-dispersion
+ * equation of Klapp et al., "Consistent SPH simulations of the anisotropic dispersion of a
+ * contaminant plume" (arXiv 2108.09488):
+ *   Sec. 2.1, Eq. 1-3   dC/dt = div(D grad C) - C div v, dx/dt = v, with the dispersion tensor
+ *                       D_ij = (aT|v| + Dm) delta_ij + (aL - aT) v_i v_j / |v|;
+ *   Sec. 2.2, Eq. 4-5   its SPH pair sum over the neighbours within the kernel support;
+ *   Sec. 2.3, Eq. 7     the Wendland kernels (C4 of the paper, support h; C2, support 2h);
+ *   Sec. 2.4, Eq. 8-10  the predictor-corrector update and the time-step rule.
+ * Neighbours come from a cell-linked list rebuilt every step by a stable radix sort of the
+ * particles by cell key.
+ *
+ * Conventions for every entry point:
+ *   - All functions are extern "C", take plain pointers and sizes and never throw.
+ *   - Pointers named *_dev are device pointers; *_host are host pointers.  The caller owns every
+ *     buffer it passes (particle state, workspace, outputs).  The library owns only the opaque
+ *     context and its CUDA graph.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All device work is enqueued on
+ *     it; only calls that return host values (ade_get_stats, ade_count_pairs, ade_step_timed,
+ *     ade_closed_form_error, and ade_run when asked for stats) wait.
+ *   - Return value: ADE_OK (0) or a negative ADE_ERR_* code; ade_last_error() gives the message
+ *     of the last failure on the calling thread.  A context stays usable after ADE_ERR_NUMERIC.
+ *   - Positions are fixed-point: coordinate u in [0, L) is the uint32 word round(u/L * 2^32)
+ *     mod 2^32, stored axis-major ([dim][n]).  The difference of two words read as int32 is
+ *     the minimum-image separation in the periodic box (Sec. 3 uses periodic borders).
+ *   - Particle arrays are in the caller's particle order; the sorted order is internal.
+ */
+#ifndef ADE_SPH_H
+#define ADE_SPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ADE_OK 0
+#define ADE_ERR_ARG (-1)      /* invalid argument or unsupported configuration */
+#define ADE_ERR_CUDA (-2)     /* a CUDA runtime call failed */
+#define ADE_ERR_NUMERIC (-3)  /* a NaN or Inf concentration was produced */
+#define ADE_ERR_TIMEOUT (-4)  /* a bounded device wait gave up */
+#define ADE_ERR_CAPACITY (-5) /* workspace or a static limit too small */
+#define ADE_ERR_STATE (-6)    /* call out of order (e.g. no particles bound) */
+
+#define ADE_WENDLAND_C2 0 /* W = B (1-q)^4 (1+4q), q = r/(2h): support 2h */
+#define ADE_WENDLAND_C4 1 /* Eq. 7: W = B (1-q)^6 (1+6q+35q^2/3), q = r/h: support h */
+
+#define ADE_DT_LAMBDA_MAX 0 /* dt = coef h^2 / lambda_max(D) */
+#define ADE_DT_TRACE 1      /* Eq. 10: dt = coef h^2 / (D_xx + D_yy [+ D_zz]) */
+
+typedef struct ade_ctx ade_ctx;
+
+/* Problem parameters (Sec. 2-3).  Passed by pointer, copied into the context. */
+typedef struct ade_params {
+    int dim;           /* 2 or 3 */
+    int kernel;        /* ADE_WENDLAND_C2 or ADE_WENDLAND_C4 */
+    double box[3];     /* periodic box side per axis (box[2] ignored in 2D) */
+    double h;          /* smoothing length; support radius 2h (C2) or h (C4) */
+    double alpha_L;    /* longitudinal dispersivity (Eq. 3) */
+    double alpha_T;    /* transverse dispersivity (Eq. 3) */
+    double D_m;        /* molecular diffusion (Eq. 3) */
+    double v[3];       /* uniform flow velocity (Sec. 3: constant in space and time) */
+    double mass;       /* particle mass m_b (uniform) */
+    double rho;        /* particle density rho_b (uniform; rhobar_ab = rho) */
+    double gamma;      /* Gamma of Eq. 5; <= 0 selects dim + 2 (4 in 2D as printed) */
+    double dt;         /* time step; <= 0 selects the rule in dt_rule */
+    int dt_rule;       /* ADE_DT_LAMBDA_MAX or ADE_DT_TRACE */
+    double dt_coef;    /* coefficient of the rule; <= 0 selects 0.1 (Eq. 10) */
+    int cell_subdiv;   /* cells per support radius along each axis, 1..4; 0 = automatic */
+    unsigned flags;    /* reserved, must be 0 */
+} ade_params;
+
+/* FP64 diagnostics of the current state. */
+typedef struct ade_stats {
+    double mass;      /* sum_a m_a C_a */
+    double c_min;     /* min_a C_a (negative values are reported, never clipped) */
+    double c_max;     /* max_a C_a */
+    double t;         /* simulated time */
+    long long step;   /* steps taken */
+    long long pairs;  /* ordered in-support pairs per rate evaluation (last counted) */
+    int status;       /* 0, or ADE_ERR_NUMERIC if a NaN/Inf was produced */
+} ade_stats;
+
+/* Derived configuration of a context. */
+typedef struct ade_info {
+    double support;   /* support radius H */
+    double dt;        /* time step in use */
+    double D[9];      /* dispersion tensor (dim x dim, row-major, Eq. 3) */
+    int nc[3];        /* cells per axis */
+    int ncells;       /* total cells */
+    int cell_subdiv;  /* cells per support radius in use */
+    int stencil_rows; /* rows of cells visited per particle */
+    int sort_passes;  /* radix-sort passes per cell build */
+    size_t workspace_bytes;
+} ade_info;
+
+/* Device workspace needed for n particles with parameters p (bytes, 256-byte aligned). */
+int ade_workspace_bytes(const ade_params *p, int n, size_t *bytes);
+
+/* Create a context bound to the caller's particle state and workspace.
+ *   xq_dev [dim][n] uint32 fixed-point positions, C_dev [n] float concentrations: updated in
+ *   place by ade_step / ade_run.  workspace_dev: at least ade_workspace_bytes(p, n) bytes,
+ *   256-byte aligned.  All three must stay valid until ade_destroy.  No device work is issued. */
+int ade_init_particles(ade_ctx **out, const ade_params *p, int n, uint32_t *xq_dev,
+                       float *C_dev, void *workspace_dev, size_t workspace_bytes);
+
+/* Configuration in use (support radius, dt, D, grid).  Host only. */
+int ade_get_info(const ade_ctx *ctx, ade_info *info_host);
+
+/* Cell-linked list of the current positions: cell keys, stable radix sort by key (ties keep the
+ * caller's particle order), sorted particle copy and the cell start table. */
+int ade_build_cells(ade_ctx *ctx, void *stream);
+
+/* Copy the last cell build out: perm_dev [n] (caller index at each sorted position) and
+ * cell_start_dev [ncells + 1] (cell c holds sorted positions cell_start[c] .. cell_start[c+1]-1).
+ * Either pointer may be NULL. */
+int ade_get_cells(ade_ctx *ctx, uint32_t *perm_dev, uint32_t *cell_start_dev, void *stream);
+
+/* Eq. 4 at the current state for every particle: builds the cell list, then writes dC/dt into
+ * dCdt_dev [n] (caller order). */
+int ade_dispersion_rate(ade_ctx *ctx, float *dCdt_dev, void *stream);
+
+/* Number of ordered in-support pairs (b != a, |x_ab| < H) of the current state, the unit of the
+ * interaction count: builds the cell list and runs one counting evaluation; waits for the stream. */
+int ade_count_pairs(ade_ctx *ctx, long long *pairs_host, void *stream);
+
+/* nsteps predictor-corrector steps (Eq. 8-9), each: cell build, rate at level l with the fused
+ * predictor, rate at level l+1/2 with the fused corrector and FP64 reductions. */
+int ade_step(ade_ctx *ctx, int nsteps, void *stream);
+
+/* As ade_step, replaying one captured CUDA graph per step (captured on the first call).  With
+ * stats_host non-NULL it waits for the stream and fills in the final diagnostics; with NULL it
+ * only enqueues. */
+int ade_run(ade_ctx *ctx, int nsteps, ade_stats *stats_host, void *stream);
+
+/* One step (as ade_step) bracketed by CUDA events on `stream`; waits for it and returns the device
+ * time of each phase in phase_ms_host[4] = {cell build, predictor rate, corrector rate, reduction}
+ * (milliseconds).  Used for per-kernel roofline measurements. */
+int ade_step_timed(ade_ctx *ctx, double *phase_ms_host, void *stream);
+
+/* Kernel launches one step enqueues (cell build passes, reorder, two rate launches, reduction). */
+int ade_launches_per_step(const ade_ctx *ctx, int *launches);
+
+/* FP64 mass, min and max of the current concentrations; waits for the stream. */
+int ade_get_stats(ade_ctx *ctx, ade_stats *stats_host, void *stream);
+
+/* Error of the current state against the closed form of Sec. 3 (Eq. 12-13 in 2D, the same
+ * Gaussian with covariance w^2 I + 2 t D in 3D), centre x0 + v t, summed over image shells
+ * |n_i| <= nimg, evaluated in FP64 on the device.  out_host[4] = {L2 = sqrt(sum_a V_a
+ * (C_a - C_an)^2) with V_a = m/rho, Linf = max |C_a - C_an|, RMSE of C/C0, max |C_an|}.
+ * Waits for the stream. */
+int ade_closed_form_error(ade_ctx *ctx, const double *x0_host, double w, double C0,
+                          int nimg, double *out_host, void *stream);
+
+/* Release the context (not the caller's buffers). */
+void ade_destroy(ade_ctx *ctx);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *ade_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADE_SPH_H */

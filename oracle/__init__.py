@@ -70,6 +70,9 @@ def _load():
             lib.orc_rate.argtypes = [_i, _i, _p, _p, _p, _p, _p, _p, _i, _d, _d, _d, _d, _d, _i,
                                      _p, _p, _p]
             lib.orc_rate.restype = _ll
+            lib.orc_rate_sel.argtypes = [_i, _i, _p, _p, _p, _p, _p, _p, _i, _d, _d, _d, _d, _d,
+                                         _i, _i, _p, _p, _p, _p]
+            lib.orc_rate_sel.restype = _ll
             lib.orc_step.argtypes = [_i, _i, _p, _p, _p, _p, _p, _p, _i, _d, _d, _d, _d, _d, _d, _i]
             lib.orc_step.restype = _ll
             lib.orc_cell_keys.argtypes = [_i, _i, _p, _p, _p]
@@ -191,6 +194,23 @@ def rate(x, v, C, m, rho, box, kind, H, gamma, alpha_L, alpha_T, D_m, brute=Fals
                              _ptr(rc))
     if split:
         return r, rd, rc, pairs
+    return r, pairs
+
+
+def rate_at(sel, x, v, C, m, rho, box, kind, H, gamma, alpha_L, alpha_T, D_m):
+    """Eq. 4 for the selected particles only (same arithmetic as :func:`rate`)."""
+    x = _f64(x)
+    n, dim = x.shape
+    v = _per_particle(v, n, dim)
+    C = _f64(C).ravel()
+    m = _per_particle(m, n)
+    rho = _per_particle(rho, n)
+    box = _f64(box).ravel()
+    sel = np.ascontiguousarray(sel, dtype=np.int32)
+    r = np.zeros(sel.size)
+    pairs = _load().orc_rate_sel(dim, n, _ptr(x), _ptr(v), _ptr(C), _ptr(m), _ptr(rho),
+                                 _ptr(box), kind, H, gamma, alpha_L, alpha_T, D_m, 0, sel.size,
+                                 _ptr(sel), _ptr(r), None, None)
     return r, pairs
 
 

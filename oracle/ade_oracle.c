@@ -301,13 +301,16 @@ long long orc_neighbours_cells(int dim, int n, const double *x, const double *bo
 /* x, v: [n][dim]; C, m, rho: [n].  The dispersive and convective sums are   */
 /* returned separately (either output may be NULL).  Neighbours come from the */
 /* cell list (or brute force when use_brute != 0 or the box has < 3 cells).  */
-/* Returns the number of ordered in-support pairs.                           */
+/* With sel != NULL only the nsel particles sel[0..nsel) are evaluated and   */
+/* output k belongs to particle sel[k].                                      */
+/* Returns the number of ordered in-support pairs of the evaluated particles. */
 /* ------------------------------------------------------------------------- */
-long long orc_rate(int dim, int n, const double *x, const double *v, const double *C,
-                   const double *m, const double *rho, const double *box, int kind, double H,
-                   double gamma, double aL, double aT, double Dm, int use_brute,
-                   double *rate, double *rate_disp, double *rate_conv)
+long long orc_rate_sel(int dim, int n, const double *x, const double *v, const double *C,
+                       const double *m, const double *rho, const double *box, int kind, double H,
+                       double gamma, double aL, double aT, double Dm, int use_brute, int nsel,
+                       const int *sel, double *rate, double *rate_disp, double *rate_conv)
 {
+    if (!sel) nsel = n;
     double *D = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * 9);
     for (int a = 0; a < n; ++a)
         orc_dispersion_tensor(dim, v + (size_t)a * dim, aL, aT, Dm, D + (size_t)a * 9);
@@ -320,7 +323,8 @@ long long orc_rate(int dim, int n, const double *x, const double *v, const doubl
     {
         int *buf = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
 #pragma omp for schedule(dynamic, 256)
-        for (int a = 0; a < n; ++a) {
+        for (int k_out = 0; k_out < nsel; ++k_out) {
+            const int a = sel ? sel[k_out] : k_out;
             int cnt;
             if (have_cells) {
                 cnt = cell_neighbours(&cl, x, box, H, a, buf);
@@ -341,9 +345,9 @@ long long orc_rate(int dim, int n, const double *x, const double *v, const doubl
                 sd += pd;
                 sc += pc;
             }
-            if (rate) rate[a] = sd + sc;
-            if (rate_disp) rate_disp[a] = sd;
-            if (rate_conv) rate_conv[a] = sc;
+            if (rate) rate[k_out] = sd + sc;
+            if (rate_disp) rate_disp[k_out] = sd;
+            if (rate_conv) rate_conv[k_out] = sc;
             npairs += cnt;
         }
         free(buf);
@@ -351,6 +355,15 @@ long long orc_rate(int dim, int n, const double *x, const double *v, const doubl
     if (have_cells) free_cell_list(&cl);
     free(D);
     return npairs;
+}
+
+long long orc_rate(int dim, int n, const double *x, const double *v, const double *C,
+                   const double *m, const double *rho, const double *box, int kind, double H,
+                   double gamma, double aL, double aT, double Dm, int use_brute,
+                   double *rate, double *rate_disp, double *rate_conv)
+{
+    return orc_rate_sel(dim, n, x, v, C, m, rho, box, kind, H, gamma, aL, aT, Dm, use_brute, n,
+                        NULL, rate, rate_disp, rate_conv);
 }
 
 /* ------------------------------------------------------------------------- */

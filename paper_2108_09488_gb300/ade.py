@@ -1,0 +1,292 @@
+"""Thin ctypes binding of libade_sph.so (include/ade_sph.h).
+
+Every function here marshals arguments and calls the C entry point of the same name; all
+computation happens in the library's CUDA kernels.  ``Simulation`` additionally owns the device
+buffers (allocated through PyTorch) that the C API expects from its caller.
+
+Loading fails loudly (``RuntimeError``) when the library has not been built: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libade_sph.so")
+
+ADE_OK = 0
+ERRORS = {-1: "ADE_ERR_ARG", -2: "ADE_ERR_CUDA", -3: "ADE_ERR_NUMERIC", -4: "ADE_ERR_TIMEOUT",
+          -5: "ADE_ERR_CAPACITY", -6: "ADE_ERR_STATE"}
+WENDLAND_C2 = 0
+WENDLAND_C4 = 1
+DT_LAMBDA_MAX = 0
+DT_TRACE = 1
+
+# every symbol declared in include/ade_sph.h
+EXPORTS = ("ade_workspace_bytes", "ade_init_particles", "ade_get_info", "ade_build_cells",
+           "ade_get_cells", "ade_dispersion_rate", "ade_count_pairs", "ade_step", "ade_run",
+           "ade_get_stats", "ade_closed_form_error", "ade_destroy", "ade_last_error",
+           "ade_step_timed", "ade_launches_per_step")
+
+
+class AdeError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("kernel", ctypes.c_int), ("box", ctypes.c_double * 3),
+                ("h", ctypes.c_double), ("alpha_L", ctypes.c_double), ("alpha_T", ctypes.c_double),
+                ("D_m", ctypes.c_double), ("v", ctypes.c_double * 3), ("mass", ctypes.c_double),
+                ("rho", ctypes.c_double), ("gamma", ctypes.c_double), ("dt", ctypes.c_double),
+                ("dt_rule", ctypes.c_int), ("dt_coef", ctypes.c_double),
+                ("cell_subdiv", ctypes.c_int), ("flags", ctypes.c_uint)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("c_min", ctypes.c_double), ("c_max", ctypes.c_double),
+                ("t", ctypes.c_double), ("step", ctypes.c_longlong), ("pairs", ctypes.c_longlong),
+                ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("support", ctypes.c_double), ("dt", ctypes.c_double), ("D", ctypes.c_double * 9),
+                ("nc", ctypes.c_int * 3), ("ncells", ctypes.c_int), ("cell_subdiv", ctypes.c_int),
+                ("stencil_rows", ctypes.c_int), ("sort_passes", ctypes.c_int),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+
+_lib = None
+
+
+def load():
+    """Load libade_sph.so (raises RuntimeError if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_2108_09488_gb300.build` (no CPU fallback exists)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, V, SZ, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_longlong
+    sig = {
+        "ade_workspace_bytes": (I, [ctypes.POINTER(Params), I, ctypes.POINTER(SZ)]),
+        "ade_init_particles": (I, [ctypes.POINTER(P), ctypes.POINTER(Params), I, P, P, P, SZ]),
+        "ade_get_info": (I, [P, ctypes.POINTER(Info)]),
+        "ade_build_cells": (I, [P, V]),
+        "ade_get_cells": (I, [P, P, P, V]),
+        "ade_dispersion_rate": (I, [P, P, V]),
+        "ade_count_pairs": (I, [P, ctypes.POINTER(LL), V]),
+        "ade_step": (I, [P, I, V]),
+        "ade_run": (I, [P, I, ctypes.POINTER(Stats), V]),
+        "ade_get_stats": (I, [P, ctypes.POINTER(Stats), V]),
+        "ade_closed_form_error": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                                      ctypes.c_double, I, ctypes.POINTER(ctypes.c_double), V]),
+        "ade_step_timed": (I, [P, ctypes.POINTER(ctypes.c_double), V]),
+        "ade_launches_per_step": (I, [P, ctypes.POINTER(I)]),
+        "ade_destroy": (None, [P]),
+        "ade_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != ADE_OK:
+        raise AdeError(rc, load().ade_last_error().decode())
+    return rc
+
+
+def params(dim, h, alpha_L, alpha_T, D_m, v, mass, rho=1.0, box=1.0, kernel=WENDLAND_C2,
+           gamma=0.0, dt=0.0, dt_rule=DT_LAMBDA_MAX, dt_coef=0.0, cell_subdiv=0):
+    p = Params()
+    p.dim = dim
+    p.kernel = kernel
+    b = np.ravel(np.asarray(box, dtype=np.float64))
+    vv = np.ravel(np.asarray(v, dtype=np.float64))
+    for i in range(3):
+        p.box[i] = float(b[min(i, b.size - 1)]) if i < dim else 1.0
+        p.v[i] = float(vv[i]) if i < min(dim, vv.size) else 0.0
+    p.h, p.alpha_L, p.alpha_T, p.D_m = h, alpha_L, alpha_T, D_m
+    p.mass, p.rho, p.gamma, p.dt = mass, rho, gamma, dt
+    p.dt_rule, p.dt_coef, p.cell_subdiv, p.flags = dt_rule, dt_coef, cell_subdiv, 0
+    return p
+
+
+def params_for(plume, **over):
+    """Params of an ``inputs.Plume`` workload (keyword overrides allowed)."""
+    kw = dict(dim=plume.dim, h=plume.h, alpha_L=plume.alpha_L, alpha_T=plume.alpha_T,
+              D_m=plume.D_m, v=plume.velocity, mass=plume.mass, rho=plume.rho, box=plume.box,
+              kernel=plume.kernel)
+    kw.update(over)
+    return params(**kw)
+
+
+# ---- entry points (same names as the C ABI, without the ade_ prefix) --------------------------
+def workspace_bytes(p, n):
+    out = ctypes.c_size_t(0)
+    _check(load().ade_workspace_bytes(ctypes.byref(p), n, ctypes.byref(out)))
+    return out.value
+
+
+def init_particles(p, n, xq_ptr, C_ptr, ws_ptr, ws_bytes):
+    ctx = ctypes.c_void_p()
+    _check(load().ade_init_particles(ctypes.byref(ctx), ctypes.byref(p), n, xq_ptr, C_ptr, ws_ptr,
+                                     ws_bytes))
+    return ctx
+
+
+def get_info(ctx):
+    info = Info()
+    _check(load().ade_get_info(ctx, ctypes.byref(info)))
+    return info
+
+
+def build_cells(ctx, stream=None):
+    _check(load().ade_build_cells(ctx, stream))
+
+
+def get_cells(ctx, perm_ptr, cell_start_ptr, stream=None):
+    _check(load().ade_get_cells(ctx, perm_ptr, cell_start_ptr, stream))
+
+
+def dispersion_rate(ctx, out_ptr, stream=None):
+    _check(load().ade_dispersion_rate(ctx, out_ptr, stream))
+
+
+def count_pairs(ctx, stream=None):
+    v = ctypes.c_longlong(0)
+    _check(load().ade_count_pairs(ctx, ctypes.byref(v), stream))
+    return v.value
+
+
+def step(ctx, nsteps=1, stream=None):
+    _check(load().ade_step(ctx, nsteps, stream))
+
+
+def run(ctx, nsteps, stream=None, stats=True):
+    st = Stats() if stats else None
+    _check(load().ade_run(ctx, nsteps, ctypes.byref(st) if stats else None, stream))
+    return st
+
+
+def step_timed(ctx, stream=None):
+    out = (ctypes.c_double * 4)()
+    _check(load().ade_step_timed(ctx, out, stream))
+    return list(out)
+
+
+def launches_per_step(ctx):
+    v = ctypes.c_int(0)
+    _check(load().ade_launches_per_step(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def get_stats(ctx, stream=None):
+    st = Stats()
+    rc = load().ade_get_stats(ctx, ctypes.byref(st), stream)
+    if rc not in (ADE_OK, -3):
+        _check(rc)
+    return st
+
+
+def closed_form_error(ctx, x0, w, C0=1.0, nimg=2, stream=None):
+    x = (ctypes.c_double * 3)(*([float(u) for u in x0] + [0.0] * (3 - len(x0))))
+    out = (ctypes.c_double * 4)()
+    _check(load().ade_closed_form_error(ctx, x, w, C0, nimg, out, stream))
+    return {"l2": out[0], "linf": out[1], "rmse": out[2], "c_an_max": out[3]}
+
+
+def destroy(ctx):
+    if ctx:
+        load().ade_destroy(ctx)
+
+
+# ---- device-memory owner ----------------------------------------------------------------------
+class Simulation:
+    """Particle state + workspace on the current CUDA device, bound to one library context.
+
+    ``xq`` (int32 [dim][n], the uint32 fixed-point words) and ``C`` (float32 [n]) are torch CUDA
+    tensors in the caller's particle order; the library updates them in place."""
+
+    def __init__(self, p, xq, C, device="cuda"):
+        import torch
+        self.torch = torch
+        self.p = p
+        xq = np.ascontiguousarray(xq, dtype=np.uint32)
+        self.dim, self.n = xq.shape
+        self.xq = torch.from_numpy(xq.view(np.int32)).to(device).contiguous()
+        self.C = torch.as_tensor(np.ascontiguousarray(C, dtype=np.float32)).to(device).contiguous()
+        nbytes = workspace_bytes(p, self.n)
+        self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        base = self.ws.data_ptr()
+        self.ws_ptr = (base + 255) // 256 * 256
+        self.ws_bytes = nbytes
+        self.ctx = init_particles(p, self.n, self.xq.data_ptr(), self.C.data_ptr(), self.ws_ptr, nbytes)
+        self.info = get_info(self.ctx)
+
+    @property
+    def stream(self):
+        return ctypes.c_void_p(self.torch.cuda.current_stream().cuda_stream)
+
+    def build_cells(self):
+        build_cells(self.ctx, self.stream)
+
+    def cells(self):
+        """(perm uint32 [n], cell_start uint32 [ncells+1]) of the last cell build, as numpy."""
+        t = self.torch
+        perm = t.empty(max(self.n, 1), dtype=t.int32, device=self.C.device)
+        cs = t.empty(self.info.ncells + 1, dtype=t.int32, device=self.C.device)
+        get_cells(self.ctx, perm.data_ptr(), cs.data_ptr(), self.stream)
+        t.cuda.synchronize()
+        return (perm.cpu().numpy().view(np.uint32)[: self.n], cs.cpu().numpy().view(np.uint32))
+
+    def rate(self):
+        out = self.torch.empty(max(self.n, 1), dtype=self.torch.float32, device=self.C.device)
+        dispersion_rate(self.ctx, out.data_ptr(), self.stream)
+        return out[: self.n]
+
+    def count_pairs(self):
+        return count_pairs(self.ctx, self.stream)
+
+    def step(self, nsteps=1):
+        step(self.ctx, nsteps, self.stream)
+
+    def run(self, nsteps, stats=True):
+        return run(self.ctx, nsteps, self.stream, stats)
+
+    def step_timed(self):
+        return step_timed(self.ctx, self.stream)
+
+    def stats(self):
+        return get_stats(self.ctx, self.stream)
+
+    def closed_form_error(self, x0, w, C0=1.0, nimg=2):
+        return closed_form_error(self.ctx, x0, w, C0, nimg, self.stream)
+
+    def state(self):
+        """(xq uint32 [dim][n], C float32 [n]) copied to the host."""
+        self.torch.cuda.synchronize()
+        return self.xq.cpu().numpy().view(np.uint32), self.C.cpu().numpy()
+
+    def close(self):
+        if self.ctx:
+            destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

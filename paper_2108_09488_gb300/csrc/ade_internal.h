@@ -1,0 +1,122 @@
+// ade_internal.h -- types shared by the host entry points and the kernels of libade_sph.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ade_sph.h"
+
+namespace ade {
+
+constexpr int kMaxSubdiv = 4;                                   // cells per support radius
+constexpr int kMaxRows = (2 * kMaxSubdiv + 1) * (2 * kMaxSubdiv + 1);
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;            // keys per sort block
+constexpr int kRateThreads = 128;
+constexpr int kMaxCellBits = 24;                                // ncells <= 2^24
+
+// One row of the neighbour-cell stencil: cells (cx - w .. cx + w, cy + dy, cz + dz).
+struct StencilRow {
+    signed char dy, dz, w, pad;
+};
+
+// Everything the interaction kernel needs, passed by value (kernel parameter space).
+// Lengths are in fixed-point units of the x axis (L_x / 2^32).
+struct RateParams {
+    int n;
+    int ncx, ncy, ncz;
+    int nrows;
+    StencilRow rows[kMaxRows];
+    float H2;        // support radius squared
+    float invH;      // 1 / support radius
+    float sy, sz;    // L_y / L_x, L_z / L_x (1 for a cubic box)
+    float Kc[6];     // Gamma (K - K_last I) with K = 2 D (uniform D): xx, yy, zz, 2xy, 2xz, 2yz,
+                     // K_last = K_yy in 2D and K_zz in 3D (so Kc[1] = 0 in 2D, Kc[2] = 0 in 3D)
+    float c0;        // Gamma K_last - tr K
+    float pf;        // 1/2 (m / rho) * kernel prefactor of W'(r)/r
+    float dt;        // step length used by the epilogue
+    uint32_t inc[3]; // fixed-point position increment used by the epilogue
+};
+
+// Outputs of the fused epilogues.
+struct EpiOut {
+    float *rate;              // EPI_RATE: dC/dt in caller order
+    uint4 *Pout;              // EPI_PREDICT: sorted half-step state
+    uint32_t *xq;             // EPI_CORRECT: caller state, updated in place
+    float *C;                 // EPI_CORRECT
+    double *partials;         // EPI_CORRECT: per-block {sum C, min C, max C}
+    int *status;              // EPI_CORRECT: set to 1 on a non-finite C
+    unsigned long long *pairs; // optional in-support pair counter
+};
+
+enum Epilogue { EPI_RATE = 0, EPI_PREDICT = 1, EPI_CORRECT = 2 };
+
+// Device buffers carved out of the caller's workspace.
+struct Work {
+    uint32_t *keys[2];
+    uint32_t *idx[2];
+    uint32_t *hist;
+    uint32_t *cell_start;
+    uint4 *P0;
+    uint4 *P1;
+    double *partials;
+    double *stats;        // {mass sum, min, max, (closed-form) ...}
+    double *cf_partials;  // closed-form error partials
+    int *status;
+    unsigned long long *pairs;
+};
+
+// Launchers (cells.cu, rate.cu, reduce.cu).  All return cudaGetLastError() of the launches.
+cudaError_t launch_build_cells(int dim, const uint32_t *xq, const float *C, int n, const int *nc,
+                               int ncells, int passes, int digit_bits, const Work &w,
+                               int sort_blocks, int *final_buf, cudaStream_t s);
+cudaError_t launch_rate(int dim, int kernel, bool iso, int epi, const uint4 *Pe, const uint4 *Pc,
+                        const uint32_t *cell_start, const uint32_t *perm, const RateParams &prm,
+                        const EpiOut &out, cudaStream_t s);
+cudaError_t launch_reduce_final(const double *partials, int nblocks, double *stats, cudaStream_t s);
+cudaError_t launch_closed_form_error(int dim, const uint32_t *xq, const float *C, int n,
+                                     const double *box, const double *center, const double *Sinv,
+                                     double amp, double C0, double vol, int nimg,
+                                     double *partials, int nblocks, double *out, cudaStream_t s);
+
+cudaError_t launch_state_stats(const float *C, int n, double *partials, double *stats, cudaStream_t s);
+
+int rate_blocks(int n);
+int closed_form_blocks(int n);
+
+}  // namespace ade
+
+struct ade_ctx {
+    ade_params p;
+    int n;
+    int dim;
+    int nc[3];
+    int ncells;
+    int subdiv;
+    int passes;
+    int digit_bits;
+    int sort_blocks;
+    int sorted_buf;       // which ping-pong buffer holds the final sort
+    uint32_t *xq;
+    float *C;
+    void *ws;
+    size_t ws_bytes;
+    ade::Work w;
+    double H;
+    double dt;
+    double D[9];
+    ade::RateParams rp;   // rate constants (dt/inc set per use)
+    uint32_t inc[3];
+    uint32_t inc_half[3];
+    bool iso;
+    double t;
+    long long step;
+    long long pairs;
+    cudaGraph_t graph;
+    cudaGraphExec_t graph_exec;
+    cudaStream_t cap_stream;
+    bool status_cleared;
+    cudaEvent_t ev[5];    // per-phase timing events (created on first timed step)
+    bool ev_ready;
+};

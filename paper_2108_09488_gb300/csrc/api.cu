@@ -1,0 +1,719 @@
+// api.cu -- extern "C" entry points of libade_sph.so (declared in include/ade_sph.h).
+//
+// Host-side set-up in FP64: the dispersion tensor (Eq. 3), the time step (Eq. 10 or the
+// largest-eigenvalue rule), the cell grid and neighbour stencil, the kernel constants of Eq. 4-5
+// and Eq. 7, and the fixed-point drift per (half) step.  Device work is enqueued on the caller's
+// stream; a step is a cell build followed by two fused rate launches and a reduction.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "ade_internal.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define ADE_CK(call)                                                                            \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) return fail(ADE_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTwo32 = 4294967296.0;
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Eq. 3: D_ij = (aT |v| + Dm) delta_ij + (aL - aT) v_i v_j / |v| (second term 0 when v = 0).
+void dispersion_tensor(int dim, const double *v, double aL, double aT, double Dm, double *D)
+{
+    double vv = 0.0;
+    for (int i = 0; i < dim; ++i) vv += v[i] * v[i];
+    const double vabs = sqrt(vv);
+    for (int i = 0; i < 9; ++i) D[i] = 0.0;
+    for (int i = 0; i < dim; ++i)
+        for (int j = 0; j < dim; ++j) {
+            double d = (i == j) ? aT * vabs + Dm : 0.0;
+            if (vabs > 0.0) d += (aL - aT) * v[i] * v[j] / vabs;
+            D[i * dim + j] = d;
+        }
+}
+
+// Largest eigenvalue of a symmetric dim x dim matrix by cyclic Jacobi rotations.
+double lambda_max(int dim, const double *Din)
+{
+    double a[3][3] = {{0}};
+    for (int i = 0; i < dim; ++i)
+        for (int j = 0; j < dim; ++j) a[i][j] = Din[i * dim + j];
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < dim; ++p)
+            for (int q = p + 1; q < dim; ++q) off += a[p][q] * a[p][q];
+        if (off < 1e-300) break;
+        for (int p = 0; p < dim; ++p)
+            for (int q = p + 1; q < dim; ++q) {
+                if (a[p][q] == 0.0) continue;
+                double theta = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < dim; ++k) {
+                    double akp = a[k][p], akq = a[k][q];
+                    a[k][p] = c * akp - s * akq;
+                    a[k][q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < dim; ++k) {
+                    double apk = a[p][k], aqk = a[q][k];
+                    a[p][k] = c * apk - s * aqk;
+                    a[q][k] = s * apk + c * aqk;
+                }
+            }
+    }
+    double m = a[0][0];
+    for (int i = 1; i < dim; ++i) m = fmax(m, a[i][i]);
+    return m;
+}
+
+// Neighbour-cell stencil for cells of side s[] and support H: every row (dy, dz) whose cells can
+// hold a point within H of a point in the centre cell, with the x half-width w of that row.
+// Two cells offset by o are at least sum_i (max(|o_i| - 1, 0) s_i)^2 apart (squared).
+int build_rows(int dim, int k, const double *s, double H, ade::StencilRow *rows)
+{
+    int nr = 0;
+    const int kz = dim == 3 ? k : 0;
+    const double H2 = H * H;
+    for (int dz = -kz; dz <= kz; ++dz)
+        for (int dy = -k; dy <= k; ++dy) {
+            double ey = fmax(fabs((double)dy) - 1.0, 0.0) * s[1];
+            double ez = dim == 3 ? fmax(fabs((double)dz) - 1.0, 0.0) * s[2] : 0.0;
+            double e2 = ey * ey + ez * ez;
+            if (e2 >= H2) continue;
+            int w = k;
+            while (w > 0) {
+                double ex = fmax((double)w - 1.0, 0.0) * s[0];
+                if (ex * ex + e2 < H2) break;
+                --w;
+            }
+            rows[nr].dy = (signed char)dy;
+            rows[nr].dz = (signed char)dz;
+            rows[nr].w = (signed char)w;
+            rows[nr].pad = 0;
+            ++nr;
+        }
+    return nr;
+}
+
+struct Grid {
+    int nc[3];
+    int ncells;
+    int subdiv;
+    int nrows;
+    ade::StencilRow rows[ade::kMaxRows];
+};
+
+// Grid with `k` cells per support radius: nc_i = floor(L_i k / H), so each cell is at least H/k
+// wide and a particle's neighbours lie within k cells along every axis.  Needs nc_i >= 2k+1 so
+// the stencil never wraps onto itself.
+bool make_grid(const ade_params &p, double H, int k, Grid *g)
+{
+    double ncells = 1.0;
+    double s[3] = {1, 1, 1};
+    for (int i = 0; i < 3; ++i) g->nc[i] = 1;
+    for (int i = 0; i < p.dim; ++i) {
+        double c = floor(p.box[i] * k / H);
+        if (c < 2 * k + 1 || c > 65535.0) return false;
+        g->nc[i] = (int)c;
+        s[i] = p.box[i] / c;
+        ncells *= c;
+    }
+    if (ncells > (double)(1u << ade::kMaxCellBits)) return false;
+    g->ncells = (int)ncells;
+    g->subdiv = k;
+    g->nrows = build_rows(p.dim, k, s, H, g->rows);
+    return true;
+}
+
+// Cost model for the automatic choice: candidates visited per particle plus a per-row overhead.
+double grid_cost(const Grid &g, int n)
+{
+    double ppc = (double)n / g.ncells;
+    double cand = 0.0;
+    for (int r = 0; r < g.nrows; ++r) cand += (2 * g.rows[r].w + 1) * ppc;
+    return cand + 4.0 * g.nrows;
+}
+
+int choose_grid(const ade_params &p, double H, int n, Grid *g)
+{
+    if (p.cell_subdiv > 0) {
+        if (p.cell_subdiv > ade::kMaxSubdiv || !make_grid(p, H, p.cell_subdiv, g))
+            return fail(ADE_ERR_ARG, "cell_subdiv=%d does not fit the box (need >= 2k+1 cells per axis, <= 2^24 cells)",
+                        p.cell_subdiv);
+        return ADE_OK;
+    }
+    bool found = false;
+    double best = 0.0;
+    for (int k = 1; k <= ade::kMaxSubdiv; ++k) {
+        Grid t;
+        if (!make_grid(p, H, k, &t)) continue;
+        double c = grid_cost(t, n);
+        if (!found || c < best) {
+            *g = t;
+            best = c;
+            found = true;
+        }
+    }
+    if (!found) return fail(ADE_ERR_ARG, "box too small for the support radius (need >= 3 cells per axis)");
+    return ADE_OK;
+}
+
+int validate(const ade_params *p, int n)
+{
+    if (!p) return fail(ADE_ERR_ARG, "params is NULL");
+    if (p->dim != 2 && p->dim != 3) return fail(ADE_ERR_ARG, "dim must be 2 or 3 (got %d)", p->dim);
+    if (p->kernel != ADE_WENDLAND_C2 && p->kernel != ADE_WENDLAND_C4)
+        return fail(ADE_ERR_ARG, "unknown kernel %d", p->kernel);
+    if (n < 0 || n > (1 << 28)) return fail(ADE_ERR_ARG, "n=%d out of range [0, 2^28]", n);
+    for (int i = 0; i < p->dim; ++i)
+        if (!(p->box[i] > 0.0) || !isfinite(p->box[i])) return fail(ADE_ERR_ARG, "box[%d] must be > 0", i);
+    if (!(p->h > 0.0) || !isfinite(p->h)) return fail(ADE_ERR_ARG, "h must be > 0");
+    if (!(p->alpha_L >= 0.0) || !(p->alpha_T >= 0.0) || !(p->D_m >= 0.0) || !isfinite(p->alpha_L) ||
+        !isfinite(p->alpha_T) || !isfinite(p->D_m))
+        return fail(ADE_ERR_ARG, "alpha_L, alpha_T, D_m must be finite and >= 0");
+    if (!(p->mass > 0.0) || !(p->rho > 0.0)) return fail(ADE_ERR_ARG, "mass and rho must be > 0");
+    for (int i = 0; i < p->dim; ++i)
+        if (!isfinite(p->v[i])) return fail(ADE_ERR_ARG, "v must be finite");
+    if (!isfinite(p->dt) || !isfinite(p->gamma)) return fail(ADE_ERR_ARG, "dt and gamma must be finite");
+    if (p->dt_rule != ADE_DT_LAMBDA_MAX && p->dt_rule != ADE_DT_TRACE) return fail(ADE_ERR_ARG, "unknown dt_rule");
+    if (p->cell_subdiv < 0 || p->cell_subdiv > ade::kMaxSubdiv) return fail(ADE_ERR_ARG, "cell_subdiv must be 0..4");
+    if (p->flags != 0u) return fail(ADE_ERR_ARG, "flags must be 0");
+    const double H = p->kernel == ADE_WENDLAND_C2 ? 2.0 * p->h : p->h;
+    for (int i = 0; i < p->dim; ++i)
+        if (!(H < 0.5 * p->box[i])) return fail(ADE_ERR_ARG, "support radius must be < box/2 (minimum image)");
+    return ADE_OK;
+}
+
+struct Layout {
+    size_t keys[2], idx[2], hist, cell_start, P0, P1, partials, stats, cf_partials, status, pairs, total;
+};
+
+Layout layout(int n, int ncells, int sort_blocks, int nb_partials)
+{
+    Layout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align256(bytes > 0 ? bytes : 1);
+        return o;
+    };
+    for (int b = 0; b < 2; ++b) L.keys[b] = take((size_t)n * 4);
+    for (int b = 0; b < 2; ++b) L.idx[b] = take((size_t)n * 4);
+    L.hist = take((size_t)256 * (sort_blocks > 0 ? sort_blocks : 1) * 4);
+    L.cell_start = take(((size_t)ncells + 1) * 4);
+    L.P0 = take((size_t)n * 16);
+    L.P1 = take((size_t)n * 16);
+    L.partials = take((size_t)3 * (nb_partials > 0 ? nb_partials : 1) * 8);
+    L.stats = take(8 * 8);
+    L.cf_partials = take((size_t)3 * (nb_partials > 0 ? nb_partials : 1) * 8);
+    L.status = take(64);
+    L.pairs = take(64);
+    L.total = off;
+    return L;
+}
+
+struct Derived {
+    double H;
+    Grid g;
+    int passes, digit_bits, sort_blocks, nb_partials;
+    Layout L;
+};
+
+int derive(const ade_params *p, int n, Derived *d)
+{
+    int rc = validate(p, n);
+    if (rc) return rc;
+    d->H = p->kernel == ADE_WENDLAND_C2 ? 2.0 * p->h : p->h;
+    rc = choose_grid(*p, d->H, n, &d->g);
+    if (rc) return rc;
+    int bits = 1;
+    while ((1ll << bits) < (long long)d->g.ncells) ++bits;
+    d->passes = (bits + 7) / 8;
+    d->digit_bits = (bits + d->passes - 1) / d->passes;
+    d->sort_blocks = (n + ade::kSortTile - 1) / ade::kSortTile;
+    int nbr = ade::rate_blocks(n), nbc = ade::closed_form_blocks(n);
+    d->nb_partials = nbr > nbc ? nbr : nbc;
+    d->L = layout(n, d->g.ncells, d->sort_blocks, d->nb_partials);
+    return ADE_OK;
+}
+
+uint32_t fixed_increment(double v, double dt, double L)
+{
+    double q = nearbyint(v * dt / L * kTwo32);
+    long long w = (long long)fmod(q, kTwo32);
+    return (uint32_t)w;
+}
+
+// Enqueue one cell build.
+int enqueue_cells(ade_ctx *c, cudaStream_t s)
+{
+    if (c->n == 0) {
+        ADE_CK(cudaMemsetAsync(c->w.cell_start, 0, ((size_t)c->ncells + 1) * 4, s));
+        c->sorted_buf = 0;
+        return ADE_OK;
+    }
+    ADE_CK(ade::launch_build_cells(c->dim, c->xq, c->C, c->n, c->nc, c->ncells, c->passes, c->digit_bits,
+                                   c->w, c->sort_blocks, &c->sorted_buf, s));
+    return ADE_OK;
+}
+
+ade::EpiOut epi_none()
+{
+    ade::EpiOut o;
+    memset(&o, 0, sizeof(o));
+    return o;
+}
+
+// Enqueue one predictor-corrector step (Eq. 8-9).
+int enqueue_step(ade_ctx *c, cudaStream_t s)
+{
+    int rc = enqueue_cells(c, s);
+    if (rc) return rc;
+    if (c->n == 0) return ADE_OK;
+    const uint32_t *perm = c->w.idx[c->sorted_buf];
+    ade::RateParams rp = c->rp;
+    ade::EpiOut out = epi_none();
+    // predictor: C^{l+1/2} = C^l + dt/2 r^l, x^{l+1/2} = x^l + dt/2 v
+    rp.dt = (float)(0.5 * c->dt);
+    for (int i = 0; i < 3; ++i) rp.inc[i] = c->inc_half[i];
+    out.Pout = c->w.P1;
+    ADE_CK(ade::launch_rate(c->dim, c->p.kernel, c->iso, ade::EPI_PREDICT, c->w.P0, c->w.P0, c->w.cell_start,
+                            perm, rp, out, s));
+    // corrector: C^{l+1} = C^l + dt r^{l+1/2}, x^{l+1} = x^l + dt v
+    rp.dt = (float)c->dt;
+    for (int i = 0; i < 3; ++i) rp.inc[i] = c->inc[i];
+    out = epi_none();
+    out.xq = c->xq;
+    out.C = c->C;
+    out.partials = c->w.partials;
+    out.status = c->w.status;
+    ADE_CK(ade::launch_rate(c->dim, c->p.kernel, c->iso, ade::EPI_CORRECT, c->w.P1, c->w.P0, c->w.cell_start,
+                            perm, rp, out, s));
+    ADE_CK(ade::launch_reduce_final(c->w.partials, ade::rate_blocks(c->n), c->w.stats, s));
+    return ADE_OK;
+}
+
+// The workspace arrives uninitialised: clear the status word once, before the first step.
+int clear_status_once(ade_ctx *c, cudaStream_t s)
+{
+    if (!c->status_cleared) {
+        ADE_CK(cudaMemsetAsync(c->w.status, 0, sizeof(int), s));
+        c->status_cleared = true;
+    }
+    return ADE_OK;
+}
+
+template <typename T>
+T *at(void *base, size_t off)
+{
+    return reinterpret_cast<T *>(static_cast<char *>(base) + off);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ade_last_error(void) { return g_err; }
+
+int ade_workspace_bytes(const ade_params *p, int n, size_t *bytes)
+{
+    if (!bytes) return fail(ADE_ERR_ARG, "bytes is NULL");
+    Derived d;
+    int rc = derive(p, n, &d);
+    if (rc) return rc;
+    *bytes = d.L.total;
+    return ADE_OK;
+}
+
+int ade_init_particles(ade_ctx **out, const ade_params *p, int n, uint32_t *xq_dev, float *C_dev,
+                       void *workspace_dev, size_t workspace_bytes)
+{
+    if (!out) return fail(ADE_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    Derived d;
+    int rc = derive(p, n, &d);
+    if (rc) return rc;
+    if (n > 0 && (!xq_dev || !C_dev)) return fail(ADE_ERR_ARG, "xq_dev and C_dev must be non-NULL");
+    if (!workspace_dev) return fail(ADE_ERR_ARG, "workspace_dev is NULL");
+    if (((uintptr_t)workspace_dev & 255u) != 0u) return fail(ADE_ERR_ARG, "workspace must be 256-byte aligned");
+    if (workspace_bytes < d.L.total)
+        return fail(ADE_ERR_CAPACITY, "workspace too small: %zu < %zu bytes", workspace_bytes, d.L.total);
+
+    ade_ctx *c = new (std::nothrow) ade_ctx;
+    if (!c) return fail(ADE_ERR_CAPACITY, "out of host memory");
+    memset(c, 0, sizeof(*c));
+    c->p = *p;
+    c->n = n;
+    c->dim = p->dim;
+    for (int i = 0; i < 3; ++i) c->nc[i] = d.g.nc[i];
+    c->ncells = d.g.ncells;
+    c->subdiv = d.g.subdiv;
+    c->passes = d.passes;
+    c->digit_bits = d.digit_bits;
+    c->sort_blocks = d.sort_blocks;
+    c->xq = xq_dev;
+    c->C = C_dev;
+    c->ws = workspace_dev;
+    c->ws_bytes = workspace_bytes;
+    c->H = d.H;
+    for (int b = 0; b < 2; ++b) {
+        c->w.keys[b] = at<uint32_t>(workspace_dev, d.L.keys[b]);
+        c->w.idx[b] = at<uint32_t>(workspace_dev, d.L.idx[b]);
+    }
+    c->w.hist = at<uint32_t>(workspace_dev, d.L.hist);
+    c->w.cell_start = at<uint32_t>(workspace_dev, d.L.cell_start);
+    c->w.P0 = at<uint4>(workspace_dev, d.L.P0);
+    c->w.P1 = at<uint4>(workspace_dev, d.L.P1);
+    c->w.partials = at<double>(workspace_dev, d.L.partials);
+    c->w.stats = at<double>(workspace_dev, d.L.stats);
+    c->w.cf_partials = at<double>(workspace_dev, d.L.cf_partials);
+    c->w.status = at<int>(workspace_dev, d.L.status);
+    c->w.pairs = at<unsigned long long>(workspace_dev, d.L.pairs);
+
+    // Eq. 3 and the time step
+    dispersion_tensor(p->dim, p->v, p->alpha_L, p->alpha_T, p->D_m, c->D);
+    double dt = p->dt;
+    if (!(dt > 0.0)) {
+        double coef = p->dt_coef > 0.0 ? p->dt_coef : 0.1;
+        double den;
+        if (p->dt_rule == ADE_DT_TRACE) {
+            den = 0.0;
+            for (int i = 0; i < p->dim; ++i) den += c->D[i * p->dim + i];
+        } else {
+            den = lambda_max(p->dim, c->D);
+        }
+        if (!(den > 0.0)) {
+            delete c;
+            return fail(ADE_ERR_ARG, "dispersion tensor is zero: give dt explicitly");
+        }
+        dt = coef * p->h * p->h / den;
+    }
+    c->dt = dt;
+    for (int i = 0; i < 3; ++i) {
+        double L = i < p->dim ? p->box[i] : 1.0;
+        double vi = i < p->dim ? p->v[i] : 0.0;
+        c->inc[i] = fixed_increment(vi, dt, L);
+        c->inc_half[i] = fixed_increment(vi, 0.5 * dt, L);
+    }
+
+    // Rate constants, lengths in fixed-point units of the x axis.
+    ade::RateParams &rp = c->rp;
+    memset(&rp, 0, sizeof(rp));
+    rp.n = n;
+    rp.ncx = d.g.nc[0];
+    rp.ncy = d.g.nc[1];
+    rp.ncz = d.g.nc[2];
+    rp.nrows = d.g.nrows;
+    for (int r = 0; r < d.g.nrows; ++r) rp.rows[r] = d.g.rows[r];
+    const double u = p->box[0] / kTwo32;
+    const double Hu = d.H / u;
+    rp.H2 = (float)(Hu * Hu);
+    rp.invH = (float)(1.0 / Hu);
+    rp.sy = (float)(p->box[1] / p->box[0]);
+    rp.sz = p->dim == 3 ? (float)(p->box[2] / p->box[0]) : 1.0f;
+    c->iso = p->box[1] == p->box[0] && (p->dim == 2 || p->box[2] == p->box[0]);
+    const double gamma = p->gamma > 0.0 ? p->gamma : p->dim + 2.0;
+    const int dm = p->dim;
+    auto K = [&](int i, int j) { return 2.0 * c->D[i * dm + j]; };  // harmonic mean of equal D
+    // Gamma x^T K x / r^2 - tr K = x^T Gamma (K - K_last I) x / r^2 + (Gamma K_last - tr K)
+    const double Klast = K(dm - 1, dm - 1);
+    double trK = 0.0;
+    for (int i = 0; i < dm; ++i) trK += K(i, i);
+    rp.Kc[0] = (float)(gamma * (K(0, 0) - Klast));
+    rp.Kc[1] = dm == 3 ? (float)(gamma * (K(1, 1) - Klast)) : 0.0f;
+    rp.Kc[2] = 0.0f;
+    rp.Kc[3] = (float)(2.0 * gamma * K(0, 1));
+    rp.Kc[4] = dm == 3 ? (float)(2.0 * gamma * K(0, 2)) : 0.0f;
+    rp.Kc[5] = dm == 3 ? (float)(2.0 * gamma * K(1, 2)) : 0.0f;
+    rp.c0 = (float)(gamma * Klast - trK);
+    const double H = d.H;
+    double B, kc;
+    if (p->kernel == ADE_WENDLAND_C2) {
+        B = dm == 2 ? 7.0 / (kPi * H * H) : 21.0 / (2.0 * kPi * H * H * H);
+        kc = -20.0 * B / (H * H);
+    } else {
+        B = dm == 2 ? 9.0 / (kPi * H * H) : 495.0 / (32.0 * kPi * H * H * H);
+        kc = -(56.0 / 3.0) * B / (H * H);
+    }
+    rp.pf = (float)(0.5 * (p->mass / p->rho) * kc);
+    *out = c;
+    return ADE_OK;
+}
+
+int ade_get_info(const ade_ctx *c, ade_info *info)
+{
+    if (!c || !info) return fail(ADE_ERR_ARG, "NULL argument");
+    memset(info, 0, sizeof(*info));
+    info->support = c->H;
+    info->dt = c->dt;
+    for (int i = 0; i < 9; ++i) info->D[i] = c->D[i];
+    for (int i = 0; i < 3; ++i) info->nc[i] = c->nc[i];
+    info->ncells = c->ncells;
+    info->cell_subdiv = c->subdiv;
+    info->stencil_rows = c->rp.nrows;
+    info->sort_passes = c->passes;
+    info->workspace_bytes = c->ws_bytes;
+    return ADE_OK;
+}
+
+int ade_build_cells(ade_ctx *c, void *stream)
+{
+    if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
+    return enqueue_cells(c, (cudaStream_t)stream);
+}
+
+int ade_get_cells(ade_ctx *c, uint32_t *perm_dev, uint32_t *cell_start_dev, void *stream)
+{
+    if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (perm_dev && c->n > 0)
+        ADE_CK(cudaMemcpyAsync(perm_dev, c->w.idx[c->sorted_buf], (size_t)c->n * 4, cudaMemcpyDeviceToDevice, s));
+    if (cell_start_dev)
+        ADE_CK(cudaMemcpyAsync(cell_start_dev, c->w.cell_start, ((size_t)c->ncells + 1) * 4,
+                               cudaMemcpyDeviceToDevice, s));
+    return ADE_OK;
+}
+
+int ade_dispersion_rate(ade_ctx *c, float *dCdt_dev, void *stream)
+{
+    if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
+    if (c->n > 0 && !dCdt_dev) return fail(ADE_ERR_ARG, "dCdt_dev is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = enqueue_cells(c, s);
+    if (rc || c->n == 0) return rc;
+    ade::EpiOut out = epi_none();
+    out.rate = dCdt_dev;
+    ADE_CK(ade::launch_rate(c->dim, c->p.kernel, c->iso, ade::EPI_RATE, c->w.P0, c->w.P0, c->w.cell_start,
+                            c->w.idx[c->sorted_buf], c->rp, out, s));
+    return ADE_OK;
+}
+
+int ade_count_pairs(ade_ctx *c, long long *pairs_host, void *stream)
+{
+    if (!c || !pairs_host) return fail(ADE_ERR_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    *pairs_host = 0;
+    int rc = enqueue_cells(c, s);
+    if (rc || c->n == 0) return rc;
+    ADE_CK(cudaMemsetAsync(c->w.pairs, 0, 8, s));
+    ade::EpiOut out = epi_none();
+    out.pairs = c->w.pairs;
+    ADE_CK(ade::launch_rate(c->dim, c->p.kernel, c->iso, ade::EPI_RATE, c->w.P0, c->w.P0, c->w.cell_start,
+                            c->w.idx[c->sorted_buf], c->rp, out, s));
+    unsigned long long v = 0;
+    ADE_CK(cudaMemcpyAsync(&v, c->w.pairs, 8, cudaMemcpyDeviceToHost, s));
+    ADE_CK(cudaStreamSynchronize(s));
+    c->pairs = (long long)v;
+    *pairs_host = (long long)v;
+    return ADE_OK;
+}
+
+int ade_step(ade_ctx *c, int nsteps, void *stream)
+{
+    if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
+    if (nsteps < 0) return fail(ADE_ERR_ARG, "nsteps must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc0 = clear_status_once(c, s);
+    if (rc0) return rc0;
+    for (int k = 0; k < nsteps; ++k) {
+        int rc = enqueue_step(c, s);
+        if (rc) return rc;
+    }
+    c->step += nsteps;
+    c->t += nsteps * c->dt;
+    return ADE_OK;
+}
+
+int ade_get_stats(ade_ctx *c, ade_stats *st, void *stream)
+{
+    if (!c || !st) return fail(ADE_ERR_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc0 = clear_status_once(c, s);
+    if (rc0) return rc0;
+    ADE_CK(ade::launch_state_stats(c->C, c->n, c->w.partials, c->w.stats, s));
+    double h[3];
+    int status = 0;
+    ADE_CK(cudaMemcpyAsync(h, c->w.stats, sizeof(h), cudaMemcpyDeviceToHost, s));
+    ADE_CK(cudaMemcpyAsync(&status, c->w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ADE_CK(cudaStreamSynchronize(s));
+    st->mass = h[0] * c->p.mass;
+    st->c_min = h[1];
+    st->c_max = h[2];
+    st->t = c->t;
+    st->step = c->step;
+    st->pairs = c->pairs;
+    st->status = status ? ADE_ERR_NUMERIC : ADE_OK;
+    return status ? fail(ADE_ERR_NUMERIC, "non-finite concentration produced") : ADE_OK;
+}
+
+int ade_run(ade_ctx *c, int nsteps, ade_stats *st, void *stream)
+{
+    if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
+    if (nsteps < 0) return fail(ADE_ERR_ARG, "nsteps must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc0 = clear_status_once(c, s);
+    if (rc0) return rc0;
+    if (!c->graph_exec && nsteps > 0) {
+        if (!c->cap_stream) ADE_CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        ADE_CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_step(c, c->cap_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        ADE_CK(e);
+        cudaError_t ei = cudaGraphInstantiate(&c->graph_exec, g, 0);
+        if (ei != cudaSuccess) {
+            cudaGraphDestroy(g);
+            c->graph_exec = nullptr;
+            return fail(ADE_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ei));
+        }
+        c->graph = g;
+    }
+    for (int k = 0; k < nsteps; ++k) ADE_CK(cudaGraphLaunch(c->graph_exec, s));
+    c->step += nsteps;
+    c->t += nsteps * c->dt;
+    if (st) return ade_get_stats(c, st, stream);
+    return ADE_OK;
+}
+
+int ade_step_timed(ade_ctx *c, double *phase_ms, void *stream)
+{
+    if (!c || !phase_ms) return fail(ADE_ERR_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = clear_status_once(c, s);
+    if (rc) return rc;
+    if (!c->ev_ready) {
+        for (int k = 0; k < 5; ++k) ADE_CK(cudaEventCreate(&c->ev[k]));
+        c->ev_ready = true;
+    }
+    ADE_CK(cudaEventRecord(c->ev[0], s));
+    rc = enqueue_cells(c, s);
+    if (rc) return rc;
+    ADE_CK(cudaEventRecord(c->ev[1], s));
+    if (c->n > 0) {
+        const uint32_t *perm = c->w.idx[c->sorted_buf];
+        ade::RateParams rp = c->rp;
+        ade::EpiOut out = epi_none();
+        rp.dt = (float)(0.5 * c->dt);
+        for (int i = 0; i < 3; ++i) rp.inc[i] = c->inc_half[i];
+        out.Pout = c->w.P1;
+        ADE_CK(ade::launch_rate(c->dim, c->p.kernel, c->iso, ade::EPI_PREDICT, c->w.P0, c->w.P0,
+                                c->w.cell_start, perm, rp, out, s));
+        ADE_CK(cudaEventRecord(c->ev[2], s));
+        rp.dt = (float)c->dt;
+        for (int i = 0; i < 3; ++i) rp.inc[i] = c->inc[i];
+        out = epi_none();
+        out.xq = c->xq;
+        out.C = c->C;
+        out.partials = c->w.partials;
+        out.status = c->w.status;
+        ADE_CK(ade::launch_rate(c->dim, c->p.kernel, c->iso, ade::EPI_CORRECT, c->w.P1, c->w.P0,
+                                c->w.cell_start, perm, rp, out, s));
+        ADE_CK(cudaEventRecord(c->ev[3], s));
+        ADE_CK(ade::launch_reduce_final(c->w.partials, ade::rate_blocks(c->n), c->w.stats, s));
+    } else {
+        ADE_CK(cudaEventRecord(c->ev[2], s));
+        ADE_CK(cudaEventRecord(c->ev[3], s));
+    }
+    ADE_CK(cudaEventRecord(c->ev[4], s));
+    ADE_CK(cudaEventSynchronize(c->ev[4]));
+    for (int k = 0; k < 4; ++k) {
+        float ms = 0.f;
+        ADE_CK(cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]));
+        phase_ms[k] = ms;
+    }
+    c->step += 1;
+    c->t += c->dt;
+    return ADE_OK;
+}
+
+int ade_launches_per_step(const ade_ctx *c, int *launches)
+{
+    if (!c || !launches) return fail(ADE_ERR_ARG, "NULL argument");
+    *launches = c->n > 0 ? 3 * c->passes + 1 + 2 + 1 : 0;
+    return ADE_OK;
+}
+
+int ade_closed_form_error(ade_ctx *c, const double *x0, double w, double C0, int nimg, double *outh,
+                          void *stream)
+{
+    if (!c || !x0 || !outh) return fail(ADE_ERR_ARG, "NULL argument");
+    if (!(w > 0.0) || nimg < 0 || nimg > 8) return fail(ADE_ERR_ARG, "need w > 0 and 0 <= nimg <= 8");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int dm = c->dim;
+    double center[3] = {0, 0, 0}, box[3] = {1, 1, 1};
+    for (int i = 0; i < dm; ++i) {
+        box[i] = c->p.box[i];
+        double u = x0[i] + c->p.v[i] * c->t;
+        center[i] = u - box[i] * floor(u / box[i]);
+    }
+    // S = w^2 I + 2 t D, its inverse and determinant (2x2 or 3x3 by cofactors)
+    double S[3][3] = {{0}};
+    for (int i = 0; i < dm; ++i)
+        for (int j = 0; j < dm; ++j) S[i][j] = 2.0 * c->t * c->D[i * dm + j] + (i == j ? w * w : 0.0);
+    if (dm == 2) S[2][2] = 1.0;
+    double c00 = S[1][1] * S[2][2] - S[1][2] * S[2][1];
+    double c01 = S[1][2] * S[2][0] - S[1][0] * S[2][2];
+    double c02 = S[1][0] * S[2][1] - S[1][1] * S[2][0];
+    double det = S[0][0] * c00 + S[0][1] * c01 + S[0][2] * c02;
+    double inv[9];
+    inv[0] = c00 / det;
+    inv[1] = (S[0][2] * S[2][1] - S[0][1] * S[2][2]) / det;
+    inv[2] = (S[0][1] * S[1][2] - S[0][2] * S[1][1]) / det;
+    inv[3] = c01 / det;
+    inv[4] = (S[0][0] * S[2][2] - S[0][2] * S[2][0]) / det;
+    inv[5] = (S[0][2] * S[1][0] - S[0][0] * S[1][2]) / det;
+    inv[6] = c02 / det;
+    inv[7] = (S[0][1] * S[2][0] - S[0][0] * S[2][1]) / det;
+    inv[8] = (S[0][0] * S[1][1] - S[0][1] * S[1][0]) / det;
+    const double amp = C0 * pow(w, dm) / sqrt(det);
+    const int nb = ade::closed_form_blocks(c->n);
+    ADE_CK(ade::launch_closed_form_error(dm, c->xq, c->C, c->n, box, center, inv, amp, C0, 0.0, nimg,
+                                         c->w.cf_partials, nb, c->w.stats + 4, s));
+    double h[3];
+    ADE_CK(cudaMemcpyAsync(h, c->w.stats + 4, sizeof(h), cudaMemcpyDeviceToHost, s));
+    ADE_CK(cudaStreamSynchronize(s));
+    const double V = c->p.mass / c->p.rho;
+    outh[0] = sqrt(V * h[0]);
+    outh[1] = c->n > 0 ? h[1] : 0.0;
+    outh[2] = c->n > 0 ? sqrt(h[0] / c->n) / C0 : 0.0;
+    outh[3] = c->n > 0 ? h[2] : 0.0;
+    return ADE_OK;
+}
+
+void ade_destroy(ade_ctx *c)
+{
+    if (!c) return;
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->ev_ready)
+        for (int k = 0; k < 5; ++k) cudaEventDestroy(c->ev[k]);
+    delete c;
+}
+
+}  // extern "C"

@@ -17,3 +17,11 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def adelib():
+    """The built libade_sph.so (compiled here if nvcc is available)."""
+    from paper_2108_09488_gb300 import ade, build
+    build.build()
+    return ade

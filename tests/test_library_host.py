@@ -1,0 +1,124 @@
+"""Host-side checks of libade_sph.so that need no GPU: the library loads, exports every entry
+point declared in include/ade_sph.h, validates arguments, and derives the time step, grid and
+stencil from the parameters (no device work is issued by these calls)."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2108_09488_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ade_sph.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ade_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(adelib):
+    lib = adelib.load()
+    names = _declared()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(adelib.EXPORTS)
+
+
+FAKE = 1 << 40          # 256-aligned placeholder device addresses; never dereferenced here
+
+
+def _ctx(adelib, p, n):
+    nbytes = adelib.workspace_bytes(p, n)
+    return adelib.init_particles(p, n, FAKE, FAKE + (1 << 30), FAKE + (2 << 30), nbytes), nbytes
+
+
+def test_info_matches_oracle_time_step_and_grid(adelib, orc):
+    plume = inputs.lattice_2d_64()
+    p = adelib.params_for(plume)
+    ctx, nbytes = _ctx(adelib, p, plume.n)
+    try:
+        info = adelib.get_info(ctx)
+        D = orc.dispersion_tensor(plume.velocity, plume.alpha_L, plume.alpha_T, plume.D_m)
+        assert info.dt == pytest.approx(orc.dt_rule(D, plume.h), rel=1e-14)
+        assert np.allclose(np.array(info.D[:4]).reshape(2, 2), D, rtol=1e-14, atol=0)
+        assert info.support == pytest.approx(2 * plume.h)
+        k = info.cell_subdiv
+        assert info.nc[0] == math.floor(1.0 * k / (2 * plume.h))
+        assert info.ncells == info.nc[0] * info.nc[1]
+        assert info.workspace_bytes == nbytes
+    finally:
+        adelib.destroy(ctx)
+    # Eq. 10 trace rule
+    p2 = adelib.params_for(plume, dt_rule=adelib.DT_TRACE)
+    ctx, _ = _ctx(adelib, p2, plume.n)
+    try:
+        assert adelib.get_info(ctx).dt == pytest.approx(orc.dt_rule(D, plume.h, "trace"), rel=1e-14)
+    finally:
+        adelib.destroy(ctx)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_stencil_covers_support(adelib, k):
+    """Every cell offset that can hold a neighbour is inside the stencil (checked by sampling
+    point pairs in a fine sub-grid of the centre cell and its neighbours)."""
+    plume = inputs.ladder_2d(256, 10)
+    p = adelib.params_for(plume, cell_subdiv=k)
+    ctx, _ = _ctx(adelib, p, plume.n)
+    try:
+        info = adelib.get_info(ctx)
+        assert info.cell_subdiv == k
+        s = 1.0 / info.nc[0]
+        H = info.support
+        assert s >= H / k
+        # offsets reachable within H from the centre cell
+        need = set()
+        g = np.linspace(0, s, 9)[:-1] + s / 16
+        for o in range(-k - 1, k + 2):
+            for q in range(-k - 1, k + 2):
+                for ax in g:
+                    for ay in g:
+                        bx = o * s + g[:, None]
+                        by = q * s + g[None, :]
+                        if np.any((bx - ax) ** 2 + (by - ay) ** 2 < H * H):
+                            need.add((o, q))
+        assert all(abs(o) <= k and abs(q) <= k for o, q in need)
+        assert info.stencil_rows >= len({q for _, q in need})
+    finally:
+        adelib.destroy(ctx)
+
+
+@pytest.mark.parametrize("bad,code", [
+    (dict(dim=4), -1), (dict(h=0.0), -1), (dict(h=0.3), -1), (dict(alpha_L=-1.0), -1),
+    (dict(mass=0.0), -1), (dict(cell_subdiv=7), -1), (dict(kernel=5), -1),
+    (dict(alpha_L=0.0, alpha_T=0.0, D_m=0.0), -1)])
+def test_invalid_arguments(adelib, bad, code):
+    plume = inputs.lattice_2d_64()
+    p = adelib.params_for(plume, **bad)
+    with pytest.raises(adelib.AdeError) as e:
+        nbytes = adelib.workspace_bytes(p, plume.n)
+        adelib.init_particles(p, plume.n, FAKE, FAKE, FAKE, nbytes)
+    assert e.value.code == code
+
+
+def test_workspace_too_small_and_misaligned(adelib):
+    plume = inputs.lattice_2d_64()
+    p = adelib.params_for(plume)
+    nbytes = adelib.workspace_bytes(p, plume.n)
+    with pytest.raises(adelib.AdeError) as e:
+        adelib.init_particles(p, plume.n, FAKE, FAKE, FAKE, nbytes - 1)
+    assert e.value.code == -5
+    with pytest.raises(adelib.AdeError) as e:
+        adelib.init_particles(p, plume.n, FAKE, FAKE, FAKE + 8, nbytes)
+    assert e.value.code == -1
+
+
+def test_empty_particle_set_is_valid(adelib):
+    plume = inputs.lattice_2d_64()
+    p = adelib.params_for(plume)
+    ctx, nbytes = _ctx(adelib, p, 0)
+    assert nbytes > 0
+    adelib.destroy(ctx)
