@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Benchmark: particle-pair interactions/s and steps/s of the SPH advection-dispersion step.
+
+A *step* is one predictor-corrector step (Eq. 8-9) of the whole hot path on one plume: cell-key
+hash, radix sort, reorder and cell table, the rate evaluation at level l with the fused predictor,
+the rate evaluation at level l+1/2 with the fused corrector and the FP64 reductions.  An
+*interaction* is one ordered in-support pair (b != a, |x_ab| < H) evaluated once; a step evaluates
+2 x pairs.  Inputs are synthetic and seeded (inputs.py): the default workload is the top rung of
+the 2D convergence ladder, a 1024^2 lattice with 120 neighbours, alpha_L/alpha_T = 10, 45-degree
+flow.  The L2 cache is flushed (256 MiB write) before every timed step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
+Under torchrun (N > 1) every rank runs an independent replica of the workload (the single-plume
+path has no exchange step); value = all ranks' interactions / max-over-ranks time.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2108_09488_gb300 import inputs  # noqa: E402
+
+WORKLOADS = {
+    "ladder-1024-n120-r10": lambda: inputs.ladder_2d(1024, 10),
+    "ladder-512-n60-r10": lambda: inputs.ladder_2d(512, 10),
+    "ladder-256-n28-r10": lambda: inputs.ladder_2d(256, 10),
+    "lattice-64-h1.3": inputs.lattice_2d_64,
+    "cube-128-h2": inputs.cube_3d_128,
+}
+DEFAULT_WORKLOAD = "ladder-1024-n120-r10"
+METRIC = "particle-pair interactions/s"
+UNIT = "interactions/s"
+
+# Minimum FP32-pipe instructions per in-support ordered pair of the uniform-D Wendland C2 term
+# (2D: 16, 3D: 22); the derivation is in the design doc.  The ALU roof is
+# SMs x 128 FP32 lanes x clock / I_MIN pairs per second.
+I_MIN = {2: 16, 3: 22}
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 256 << 20
+
+
+# ---------------------------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Dist:
+    def __init__(self, world, use_cuda):
+        self.world = world
+        self.pg = None
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl" if use_cuda else "gloo")
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x, device):
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for r in csv.reader(f):
+                if len(r) >= 10:
+                    rows.append([c.strip() for c in r])
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return float("nan")
+        load = [r for r in rows if num(r[4]) >= 50.0] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(num(r[1]) for r in load),
+                "sm_max_mhz": max(num(r[2]) for r in rows),
+                "power_w_max": max(num(r[3]) for r in rows),
+                "samples": len(rows), "samples_under_load": len(load), "reasons": reasons}
+
+
+# ---------------------------------------------------------------------------------------------
+def cpu_oracle_rate(plume, xq, C, sample, min_seconds, max_steps=None):
+    """Time the FP64 oracle: each step evaluates Eq. 4 twice (predictor and corrector
+    evaluation) for a fixed random sample of particles.  Returns (interactions/s, steps, secs)."""
+    import oracle
+    oracle.build()
+    x = inputs.from_fixed(xq, plume.boxv)
+    Cd = np.asarray(C, dtype=np.float64)
+    sel = np.sort(np.random.default_rng(12345).choice(plume.n, min(sample, plume.n), replace=False))
+    args = (plume.velocity, Cd, plume.mass, plume.rho, plume.boxv, plume.kernel, plume.support,
+            plume.dim + 2.0, plume.alpha_L, plume.alpha_T, plume.D_m)
+    pairs = 0
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        for _ in range(2):
+            _, p = oracle.rate_at(sel, x, *args)
+            pairs += p
+        steps += 1
+        el = time.perf_counter() - t0
+        if (max_steps is not None and steps >= max_steps) or (max_steps is None and el >= min_seconds):
+            break
+    return pairs / el, steps, el, int(sel.size)
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    plume = WORKLOADS[args.workload]()
+    xq, C = plume.initial_state()
+    sample = args.cpu_sample
+    cpu_oracle_rate(plume, xq, C, sample, 0.0, max_steps=args.warmup) if args.warmup else None
+    value, steps, secs, ns = cpu_oracle_rate(plume, xq, C, sample, 0.0, max_steps=args.steps)
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(plume),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"Eq. 4 evaluated twice per step on {ns} of {plume.n} particles"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def workload_config(plume):
+    return {"workload": plume.name, "particles": plume.n, "dim": plume.dim,
+            "kernel": "wendland-c2" if plume.kernel == inputs.WENDLAND_C2 else "wendland-c4",
+            "support_over_dx": round(plume.support / plume.dx, 6),
+            "alpha_L_over_alpha_T": round(plume.alpha_L / plume.alpha_T, 6),
+            "l2": "flushed (256 MiB write) before every timed step"}
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2108_09488_gb300 import ade
+
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = Dist(world, True)
+
+    plume = WORKLOADS[args.workload]()
+    xq, C = plume.initial_state()
+    sim = ade.Simulation(ade.params_for(plume), xq, C, device=device)
+    pairs = sim.count_pairs()
+    launches = ade.launches_per_step(sim.ctx)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        sim.step_timed()
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    phases = []
+    for _ in range(args.steps):
+        flush.zero_()
+        phases.append(sim.step_timed())
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+
+    total_ms = sum(sum(p) for p in phases)
+    total_ms = dist.max(total_ms, device)
+    ms_per_step = total_ms / args.steps
+    value = world * 2.0 * pairs * args.steps / (total_ms * 1e-3)
+
+    # dominant kernel: the rate kernel (predictor and corrector launches)
+    rate_ms = [p[1] for p in phases] + [p[2] for p in phases]
+    rate_avg_ms = sum(rate_ms) / len(rate_ms)
+    props = torch.cuda.get_device_properties(device)
+    sms = props.multi_processor_count
+    f_max = clk.get("sm_max_mhz") or 2070.0
+    peak = sms * FP32_LANES_PER_SM * f_max * 1e6 / I_MIN[plume.dim] / 1e9
+    achieved = pairs / (rate_avg_ms * 1e-3) / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_rate (predictor + corrector)",
+                "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {f_max:.0f} MHz / "
+                              f"{I_MIN[plume.dim]} FP32-pipe instructions per pair",
+                "rate_kernel_ms": rate_avg_ms,
+                "phase_ms_per_step": {k: sum(p[i] for p in phases) / len(phases)
+                                      for i, k in enumerate(("cells", "predictor", "corrector", "reduce"))}}
+    if clk.get("sm_mhz"):
+        roofline["frac_at_sampled_clock"] = achieved / (peak * clk["sm_mhz"] / f_max)
+
+    # end to end through the C ABI with host buffers: H2D of the step's inputs, the step, D2H of C
+    xq_pin = torch.from_numpy(np.ascontiguousarray(xq).view(np.int32)).pin_memory()
+    C_pin = torch.from_numpy(np.ascontiguousarray(C)).pin_memory()
+    C_out = torch.empty_like(C_pin).pin_memory()
+    stream = torch.cuda.current_stream(device)
+
+    def e2e_step():
+        sim.xq.copy_(xq_pin, non_blocking=True)
+        sim.C.copy_(C_pin, non_blocking=True)
+        sim.run(1, stats=False)
+        C_out.copy_(sim.C, non_blocking=True)
+
+    for _ in range(max(args.warmup, 1)):
+        e2e_step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = dist.max(ev0.elapsed_time(ev1), device)
+    e2e = {"value": world * 2.0 * pairs * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": int(xq_pin.numel() * 4 + C_pin.numel() * 4),
+           "d2h_bytes_per_step": int(C_out.numel() * 4),
+           "ms_per_step": e2e_ms / args.steps, "path": "ade_run (graph replay) via ctypes"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(plume),
+        "grid": {"cell_subdiv": sim.info.cell_subdiv, "cells": sim.info.ncells,
+                 "stencil_rows": sim.info.stencil_rows, "sort_passes": sim.info.sort_passes,
+                 "dt": sim.info.dt},
+        "steps_per_s": 1e3 / ms_per_step * world,
+        "interactions_per_step": 2 * pairs,
+        "roofline": roofline, "e2e": e2e, "clocks": clk,
+        "gpu_launches": launches * args.steps,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, steps, secs, ns = cpu_oracle_rate(plume, xq, C, args.cpu_sample, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"Eq. 4 evaluated twice per step on a fixed sample of {ns} "
+                                          f"of {plume.n} particles; {steps} steps in {secs:.1f} s"}
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line))
+    dist.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--cpu-sample", type=int, default=131072)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)       # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -48,6 +48,9 @@ extern "C" {
 #define ADE_WENDLAND_C2 0 /* W = B (1-q)^4 (1+4q), q = r/(2h): support 2h */
 #define ADE_WENDLAND_C4 1 /* Eq. 7: W = B (1-q)^6 (1+6q+35q^2/3), q = r/h: support h */
 
+#define ADE_FLAG_DIRECT 1u /* interaction kernel: direct walk over global memory (default) */
+#define ADE_FLAG_TILED 2u  /* interaction kernel: shared-memory tiles where the grid allows */
+
 #define ADE_DT_LAMBDA_MAX 0 /* dt = coef h^2 / lambda_max(D) */
 #define ADE_DT_TRACE 1      /* Eq. 10: dt = coef h^2 / (D_xx + D_yy [+ D_zz]) */
 
@@ -70,7 +73,7 @@ typedef struct ade_params {
     int dt_rule;       /* ADE_DT_LAMBDA_MAX or ADE_DT_TRACE */
     double dt_coef;    /* coefficient of the rule; <= 0 selects 0.1 (Eq. 10) */
     int cell_subdiv;   /* cells per support radius along each axis, 1..4; 0 = automatic */
-    unsigned flags;    /* reserved, must be 0 */
+    unsigned flags;    /* 0 (library's choice), ADE_FLAG_DIRECT or ADE_FLAG_TILED */
 } ade_params;
 
 /* FP64 diagnostics of the current state. */
@@ -94,6 +97,9 @@ typedef struct ade_info {
     int cell_subdiv;  /* cells per support radius in use */
     int stencil_rows; /* rows of cells visited per particle */
     int sort_passes;  /* radix-sort passes per cell build */
+    int variant;      /* interaction kernel: 0 direct walk, 1 shared-memory tiles */
+    int tile[3];      /* target cells per tile (tiled variant) */
+    int tile_capacity;/* staged particles per tile (tiled variant) */
     size_t workspace_bytes;
 } ade_info;
 

@@ -22,6 +22,8 @@ ERRORS = {-1: "ADE_ERR_ARG", -2: "ADE_ERR_CUDA", -3: "ADE_ERR_NUMERIC", -4: "ADE
           -5: "ADE_ERR_CAPACITY", -6: "ADE_ERR_STATE"}
 WENDLAND_C2 = 0
 WENDLAND_C4 = 1
+FLAG_DIRECT = 1
+FLAG_TILED = 2
 DT_LAMBDA_MAX = 0
 DT_TRACE = 1
 
@@ -60,7 +62,8 @@ class Info(ctypes.Structure):
     _fields_ = [("support", ctypes.c_double), ("dt", ctypes.c_double), ("D", ctypes.c_double * 9),
                 ("nc", ctypes.c_int * 3), ("ncells", ctypes.c_int), ("cell_subdiv", ctypes.c_int),
                 ("stencil_rows", ctypes.c_int), ("sort_passes", ctypes.c_int),
-                ("workspace_bytes", ctypes.c_size_t)]
+                ("variant", ctypes.c_int), ("tile", ctypes.c_int * 3),
+                ("tile_capacity", ctypes.c_int), ("workspace_bytes", ctypes.c_size_t)]
 
 
 _lib = None
@@ -109,7 +112,7 @@ def _check(rc):
 
 
 def params(dim, h, alpha_L, alpha_T, D_m, v, mass, rho=1.0, box=1.0, kernel=WENDLAND_C2,
-           gamma=0.0, dt=0.0, dt_rule=DT_LAMBDA_MAX, dt_coef=0.0, cell_subdiv=0):
+           gamma=0.0, dt=0.0, dt_rule=DT_LAMBDA_MAX, dt_coef=0.0, cell_subdiv=0, flags=0):
     p = Params()
     p.dim = dim
     p.kernel = kernel
@@ -120,7 +123,7 @@ def params(dim, h, alpha_L, alpha_T, D_m, v, mass, rho=1.0, box=1.0, kernel=WEND
         p.v[i] = float(vv[i]) if i < min(dim, vv.size) else 0.0
     p.h, p.alpha_L, p.alpha_T, p.D_m = h, alpha_L, alpha_T, D_m
     p.mass, p.rho, p.gamma, p.dt = mass, rho, gamma, dt
-    p.dt_rule, p.dt_coef, p.cell_subdiv, p.flags = dt_rule, dt_coef, cell_subdiv, 0
+    p.dt_rule, p.dt_coef, p.cell_subdiv, p.flags = dt_rule, dt_coef, cell_subdiv, flags
     return p
 
 

@@ -10,10 +10,8 @@ namespace ade {
 
 constexpr int kMaxSubdiv = 4;                                   // cells per support radius
 constexpr int kMaxRows = (2 * kMaxSubdiv + 1) * (2 * kMaxSubdiv + 1);
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;            // keys per sort block
-constexpr int kRateThreads = 128;
+constexpr int kRateThreads = 128;                              // direct variant
+constexpr int kTileThreads = 256;                              // tiled variant
 constexpr int kMaxCellBits = 24;                                // ncells <= 2^24
 
 // One row of the neighbour-cell stencil: cells (cx - w .. cx + w, cy + dy, cz + dz).
@@ -37,6 +35,13 @@ struct RateParams {
     float pf;        // 1/2 (m / rho) * kernel prefactor of W'(r)/r
     float dt;        // step length used by the epilogue
     uint32_t inc[3]; // fixed-point position increment used by the epilogue
+    int variant;     // 0 = direct walk over global memory, 1 = shared-memory tiles
+    int k;           // halo width in cells (cells per support radius)
+    int tx, ty, tz;  // target cells per tile
+    int ntx, nty, ntz;  // tiles per axis
+    int cap;         // staged-particle capacity of a tile
+    double u[3];     // FP64 length of one fixed-point unit per axis (L_i / 2^32)
+    double H2d;      // FP64 support radius squared (pair counting decides support in FP64)
 };
 
 // Outputs of the fused epilogues.
@@ -46,6 +51,8 @@ struct EpiOut {
     uint32_t *xq;             // EPI_CORRECT: caller state, updated in place
     float *C;                 // EPI_CORRECT
     double *partials;         // EPI_CORRECT: per-block {sum C, min C, max C}
+    double *stats;            // EPI_CORRECT: final {sum C, min C, max C}, by the last block
+    unsigned *done;           // EPI_CORRECT: blocks finished (the last block resets it to 0)
     int *status;              // EPI_CORRECT: set to 1 on a non-finite C
     unsigned long long *pairs; // optional in-support pair counter
 };
@@ -54,23 +61,27 @@ enum Epilogue { EPI_RATE = 0, EPI_PREDICT = 1, EPI_CORRECT = 2 };
 
 // Device buffers carved out of the caller's workspace.
 struct Work {
-    uint32_t *keys[2];
-    uint32_t *idx[2];
-    uint32_t *hist;
-    uint32_t *cell_start;
-    uint4 *P0;
-    uint4 *P1;
-    double *partials;
-    double *stats;        // {mass sum, min, max, (closed-form) ...}
-    double *cf_partials;  // closed-form error partials
-    int *status;
+    uint32_t *keys;        // [n] cell key per caller particle
+    uint32_t *rank;        // [n] provisional rank inside the cell
+    uint32_t *count;       // [ncells] particles per cell
+    uint32_t *block_sums;  // [scan blocks]
+    uint32_t *perm_tmp;    // [n] provisional cell-sorted permutation
+    uint32_t *perm;        // [n] caller index at each sorted position
+    uint32_t *cell_start;  // [ncells + 1]
+    uint4 *P0;             // [n] sorted {x, y, z, C} at level l
+    uint4 *P1;             // [n] sorted state at level l + 1/2
+    double *partials;      // per-block reduction partials
+    double *stats;         // {sum C, min C, max C, -, closed-form slots}
+    double *cf_partials;   // closed-form error partials
+    int *status;           // non-finite flag
+    unsigned *done;        // last-block counter of the corrector
     unsigned long long *pairs;
 };
 
 // Launchers (cells.cu, rate.cu, reduce.cu).  All return cudaGetLastError() of the launches.
+int scan_blocks(int m);
 cudaError_t launch_build_cells(int dim, const uint32_t *xq, const float *C, int n, const int *nc,
-                               int ncells, int passes, int digit_bits, const Work &w,
-                               int sort_blocks, int *final_buf, cudaStream_t s);
+                               int ncells, const Work &w, cudaStream_t s);
 cudaError_t launch_rate(int dim, int kernel, bool iso, int epi, const uint4 *Pe, const uint4 *Pc,
                         const uint32_t *cell_start, const uint32_t *perm, const RateParams &prm,
                         const EpiOut &out, cudaStream_t s);
@@ -83,6 +94,8 @@ cudaError_t launch_closed_form_error(int dim, const uint32_t *xq, const float *C
 cudaError_t launch_state_stats(const float *C, int n, double *partials, double *stats, cudaStream_t s);
 
 int rate_blocks(int n);
+int rate_launch_blocks(int dim, const RateParams &prm, bool iso);
+size_t tiled_smem_bytes(int dim, const RateParams &prm);
 int closed_form_blocks(int n);
 
 }  // namespace ade
@@ -94,10 +107,6 @@ struct ade_ctx {
     int nc[3];
     int ncells;
     int subdiv;
-    int passes;
-    int digit_bits;
-    int sort_blocks;
-    int sorted_buf;       // which ping-pong buffer holds the final sort
     uint32_t *xq;
     float *C;
     void *ws;

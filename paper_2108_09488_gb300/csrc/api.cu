@@ -198,18 +198,69 @@ int validate(const ade_params *p, int n)
     if (!isfinite(p->dt) || !isfinite(p->gamma)) return fail(ADE_ERR_ARG, "dt and gamma must be finite");
     if (p->dt_rule != ADE_DT_LAMBDA_MAX && p->dt_rule != ADE_DT_TRACE) return fail(ADE_ERR_ARG, "unknown dt_rule");
     if (p->cell_subdiv < 0 || p->cell_subdiv > ade::kMaxSubdiv) return fail(ADE_ERR_ARG, "cell_subdiv must be 0..4");
-    if (p->flags != 0u) return fail(ADE_ERR_ARG, "flags must be 0");
+    if ((p->flags & ~(ADE_FLAG_DIRECT | ADE_FLAG_TILED)) != 0u ||
+        p->flags == (ADE_FLAG_DIRECT | ADE_FLAG_TILED))
+        return fail(ADE_ERR_ARG, "unknown or conflicting flags");
     const double H = p->kernel == ADE_WENDLAND_C2 ? 2.0 * p->h : p->h;
     for (int i = 0; i < p->dim; ++i)
         if (!(H < 0.5 * p->box[i])) return fail(ADE_ERR_ARG, "support radius must be < box/2 (minimum image)");
     return ADE_OK;
 }
 
+// Tiles of the shared-memory variant (opt-in with ADE_FLAG_TILED): about 8 targets per thread, halo staged in <= ~100 KB,
+// and T + 2k < nc along every axis so that the halo holds each cell once and every staged
+// particle lies within half a box of the tile centre.
+void choose_tiles(int dim, int n, const Grid &g, bool iso, unsigned flags, ade::RateParams *rp)
+{
+    rp->variant = 0;
+    rp->k = g.subdiv;
+    rp->tx = rp->ty = rp->tz = 1;
+    rp->ntx = rp->nty = rp->ntz = 1;
+    rp->cap = 0;
+    if (!iso || !(flags & ADE_FLAG_TILED) || n == 0) return;
+    const int k = g.subdiv;
+    const double ppc = (double)n / g.ncells;
+    const double want = 8.0 * ade::kTileThreads;
+    int t[3] = {1, 1, 1};
+    if (dim == 2) {
+        int T = (int)lround(sqrt(want / fmax(ppc, 1e-3)));
+        T = T < 1 ? 1 : (T > 64 ? 64 : T);
+        t[0] = t[1] = T;
+    } else {
+        t[1] = t[2] = 2;
+        int T = (int)lround(want / fmax(ppc, 1e-3) / 4.0);
+        t[0] = T < 1 ? 1 : (T > 32 ? 32 : T);
+    }
+    for (int i = 0; i < dim; ++i)
+        while (t[i] > 1 && t[i] + 2 * k >= g.nc[i]) --t[i];
+    for (int i = 0; i < dim; ++i)
+        if (t[i] + 2 * k >= g.nc[i]) return;  // the grid is too small for a halo: direct walk
+    for (;;) {
+        double halo = 1.0;
+        for (int i = 0; i < dim; ++i) halo *= t[i] + 2 * k;
+        rp->tx = t[0];
+        rp->ty = t[1];
+        rp->tz = dim == 3 ? t[2] : 1;
+        rp->cap = (int)ceil(halo * ppc * 1.25) + 64;
+        if (ade::tiled_smem_bytes(dim, *rp) <= 100 * 1024) break;
+        int big = 0;
+        for (int i = 1; i < dim; ++i)
+            if (t[i] > t[big]) big = i;
+        if (t[big] == 1) return;
+        --t[big];
+    }
+    rp->ntx = (g.nc[0] + rp->tx - 1) / rp->tx;
+    rp->nty = (g.nc[1] + rp->ty - 1) / rp->ty;
+    rp->ntz = dim == 3 ? (g.nc[2] + rp->tz - 1) / rp->tz : 1;
+    rp->variant = 1;
+}
+
 struct Layout {
-    size_t keys[2], idx[2], hist, cell_start, P0, P1, partials, stats, cf_partials, status, pairs, total;
+    size_t keys, rank, count, block_sums, perm_tmp, perm, cell_start, P0, P1, partials, stats,
+        cf_partials, status, done, pairs, total;
 };
 
-Layout layout(int n, int ncells, int sort_blocks, int nb_partials)
+Layout layout(int n, int ncells, int nb_partials)
 {
     Layout L;
     size_t off = 0;
@@ -218,9 +269,12 @@ Layout layout(int n, int ncells, int sort_blocks, int nb_partials)
         off += align256(bytes > 0 ? bytes : 1);
         return o;
     };
-    for (int b = 0; b < 2; ++b) L.keys[b] = take((size_t)n * 4);
-    for (int b = 0; b < 2; ++b) L.idx[b] = take((size_t)n * 4);
-    L.hist = take((size_t)256 * (sort_blocks > 0 ? sort_blocks : 1) * 4);
+    L.keys = take((size_t)n * 4);
+    L.rank = take((size_t)n * 4);
+    L.count = take((size_t)ncells * 4);
+    L.block_sums = take((size_t)ade::scan_blocks(ncells) * 4);
+    L.perm_tmp = take((size_t)n * 4);
+    L.perm = take((size_t)n * 4);
     L.cell_start = take(((size_t)ncells + 1) * 4);
     L.P0 = take((size_t)n * 16);
     L.P1 = take((size_t)n * 16);
@@ -228,6 +282,7 @@ Layout layout(int n, int ncells, int sort_blocks, int nb_partials)
     L.stats = take(8 * 8);
     L.cf_partials = take((size_t)3 * (nb_partials > 0 ? nb_partials : 1) * 8);
     L.status = take(64);
+    L.done = take(64);
     L.pairs = take(64);
     L.total = off;
     return L;
@@ -236,7 +291,8 @@ Layout layout(int n, int ncells, int sort_blocks, int nb_partials)
 struct Derived {
     double H;
     Grid g;
-    int passes, digit_bits, sort_blocks, nb_partials;
+    int nb_partials;
+    ade::RateParams tiles;
     Layout L;
 };
 
@@ -247,14 +303,15 @@ int derive(const ade_params *p, int n, Derived *d)
     d->H = p->kernel == ADE_WENDLAND_C2 ? 2.0 * p->h : p->h;
     rc = choose_grid(*p, d->H, n, &d->g);
     if (rc) return rc;
-    int bits = 1;
-    while ((1ll << bits) < (long long)d->g.ncells) ++bits;
-    d->passes = (bits + 7) / 8;
-    d->digit_bits = (bits + d->passes - 1) / d->passes;
-    d->sort_blocks = (n + ade::kSortTile - 1) / ade::kSortTile;
+    const bool iso = p->box[1] == p->box[0] && (p->dim == 2 || p->box[2] == p->box[0]);
+    memset(&d->tiles, 0, sizeof(d->tiles));
+    d->tiles.n = n;
+    choose_tiles(p->dim, n, d->g, iso, p->flags, &d->tiles);
     int nbr = ade::rate_blocks(n), nbc = ade::closed_form_blocks(n);
+    int nbt = ade::rate_launch_blocks(p->dim, d->tiles, iso);
     d->nb_partials = nbr > nbc ? nbr : nbc;
-    d->L = layout(n, d->g.ncells, d->sort_blocks, d->nb_partials);
+    if (nbt > d->nb_partials) d->nb_partials = nbt;
+    d->L = layout(n, d->g.ncells, d->nb_partials);
     return ADE_OK;
 }
 
@@ -268,13 +325,7 @@ uint32_t fixed_increment(double v, double dt, double L)
 // Enqueue one cell build.
 int enqueue_cells(ade_ctx *c, cudaStream_t s)
 {
-    if (c->n == 0) {
-        ADE_CK(cudaMemsetAsync(c->w.cell_start, 0, ((size_t)c->ncells + 1) * 4, s));
-        c->sorted_buf = 0;
-        return ADE_OK;
-    }
-    ADE_CK(ade::launch_build_cells(c->dim, c->xq, c->C, c->n, c->nc, c->ncells, c->passes, c->digit_bits,
-                                   c->w, c->sort_blocks, &c->sorted_buf, s));
+    ADE_CK(ade::launch_build_cells(c->dim, c->xq, c->C, c->n, c->nc, c->ncells, c->w, s));
     return ADE_OK;
 }
 
@@ -291,7 +342,7 @@ int enqueue_step(ade_ctx *c, cudaStream_t s)
     int rc = enqueue_cells(c, s);
     if (rc) return rc;
     if (c->n == 0) return ADE_OK;
-    const uint32_t *perm = c->w.idx[c->sorted_buf];
+    const uint32_t *perm = c->w.perm;
     ade::RateParams rp = c->rp;
     ade::EpiOut out = epi_none();
     // predictor: C^{l+1/2} = C^l + dt/2 r^l, x^{l+1/2} = x^l + dt/2 v
@@ -307,10 +358,11 @@ int enqueue_step(ade_ctx *c, cudaStream_t s)
     out.xq = c->xq;
     out.C = c->C;
     out.partials = c->w.partials;
+    out.stats = c->w.stats;
+    out.done = c->w.done;
     out.status = c->w.status;
     ADE_CK(ade::launch_rate(c->dim, c->p.kernel, c->iso, ade::EPI_CORRECT, c->w.P1, c->w.P0, c->w.cell_start,
                             perm, rp, out, s));
-    ADE_CK(ade::launch_reduce_final(c->w.partials, ade::rate_blocks(c->n), c->w.stats, s));
     return ADE_OK;
 }
 
@@ -319,6 +371,7 @@ int clear_status_once(ade_ctx *c, cudaStream_t s)
 {
     if (!c->status_cleared) {
         ADE_CK(cudaMemsetAsync(c->w.status, 0, sizeof(int), s));
+        ADE_CK(cudaMemsetAsync(c->w.done, 0, sizeof(unsigned), s));
         c->status_cleared = true;
     }
     return ADE_OK;
@@ -369,19 +422,17 @@ int ade_init_particles(ade_ctx **out, const ade_params *p, int n, uint32_t *xq_d
     for (int i = 0; i < 3; ++i) c->nc[i] = d.g.nc[i];
     c->ncells = d.g.ncells;
     c->subdiv = d.g.subdiv;
-    c->passes = d.passes;
-    c->digit_bits = d.digit_bits;
-    c->sort_blocks = d.sort_blocks;
     c->xq = xq_dev;
     c->C = C_dev;
     c->ws = workspace_dev;
     c->ws_bytes = workspace_bytes;
     c->H = d.H;
-    for (int b = 0; b < 2; ++b) {
-        c->w.keys[b] = at<uint32_t>(workspace_dev, d.L.keys[b]);
-        c->w.idx[b] = at<uint32_t>(workspace_dev, d.L.idx[b]);
-    }
-    c->w.hist = at<uint32_t>(workspace_dev, d.L.hist);
+    c->w.keys = at<uint32_t>(workspace_dev, d.L.keys);
+    c->w.rank = at<uint32_t>(workspace_dev, d.L.rank);
+    c->w.count = at<uint32_t>(workspace_dev, d.L.count);
+    c->w.block_sums = at<uint32_t>(workspace_dev, d.L.block_sums);
+    c->w.perm_tmp = at<uint32_t>(workspace_dev, d.L.perm_tmp);
+    c->w.perm = at<uint32_t>(workspace_dev, d.L.perm);
     c->w.cell_start = at<uint32_t>(workspace_dev, d.L.cell_start);
     c->w.P0 = at<uint4>(workspace_dev, d.L.P0);
     c->w.P1 = at<uint4>(workspace_dev, d.L.P1);
@@ -389,6 +440,7 @@ int ade_init_particles(ade_ctx **out, const ade_params *p, int n, uint32_t *xq_d
     c->w.stats = at<double>(workspace_dev, d.L.stats);
     c->w.cf_partials = at<double>(workspace_dev, d.L.cf_partials);
     c->w.status = at<int>(workspace_dev, d.L.status);
+    c->w.done = at<unsigned>(workspace_dev, d.L.done);
     c->w.pairs = at<unsigned long long>(workspace_dev, d.L.pairs);
 
     // Eq. 3 and the time step
@@ -429,6 +481,8 @@ int ade_init_particles(ade_ctx **out, const ade_params *p, int n, uint32_t *xq_d
     const double u = p->box[0] / kTwo32;
     const double Hu = d.H / u;
     rp.H2 = (float)(Hu * Hu);
+    for (int i = 0; i < 3; ++i) rp.u[i] = (i < p->dim ? p->box[i] : 1.0) / kTwo32;
+    rp.H2d = d.H * d.H;
     rp.invH = (float)(1.0 / Hu);
     rp.sy = (float)(p->box[1] / p->box[0]);
     rp.sz = p->dim == 3 ? (float)(p->box[2] / p->box[0]) : 1.0f;
@@ -457,6 +511,15 @@ int ade_init_particles(ade_ctx **out, const ade_params *p, int n, uint32_t *xq_d
         kc = -(56.0 / 3.0) * B / (H * H);
     }
     rp.pf = (float)(0.5 * (p->mass / p->rho) * kc);
+    rp.variant = d.tiles.variant;
+    rp.k = d.tiles.k;
+    rp.tx = d.tiles.tx;
+    rp.ty = d.tiles.ty;
+    rp.tz = d.tiles.tz;
+    rp.ntx = d.tiles.ntx;
+    rp.nty = d.tiles.nty;
+    rp.ntz = d.tiles.ntz;
+    rp.cap = d.tiles.cap;
     *out = c;
     return ADE_OK;
 }
@@ -472,7 +535,12 @@ int ade_get_info(const ade_ctx *c, ade_info *info)
     info->ncells = c->ncells;
     info->cell_subdiv = c->subdiv;
     info->stencil_rows = c->rp.nrows;
-    info->sort_passes = c->passes;
+    info->sort_passes = 1;
+    info->variant = c->rp.variant;
+    info->tile[0] = c->rp.tx;
+    info->tile[1] = c->rp.ty;
+    info->tile[2] = c->rp.tz;
+    info->tile_capacity = c->rp.cap;
     info->workspace_bytes = c->ws_bytes;
     return ADE_OK;
 }
@@ -488,7 +556,7 @@ int ade_get_cells(ade_ctx *c, uint32_t *perm_dev, uint32_t *cell_start_dev, void
     if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     if (perm_dev && c->n > 0)
-        ADE_CK(cudaMemcpyAsync(perm_dev, c->w.idx[c->sorted_buf], (size_t)c->n * 4, cudaMemcpyDeviceToDevice, s));
+        ADE_CK(cudaMemcpyAsync(perm_dev, c->w.perm, (size_t)c->n * 4, cudaMemcpyDeviceToDevice, s));
     if (cell_start_dev)
         ADE_CK(cudaMemcpyAsync(cell_start_dev, c->w.cell_start, ((size_t)c->ncells + 1) * 4,
                                cudaMemcpyDeviceToDevice, s));
@@ -505,7 +573,7 @@ int ade_dispersion_rate(ade_ctx *c, float *dCdt_dev, void *stream)
     ade::EpiOut out = epi_none();
     out.rate = dCdt_dev;
     ADE_CK(ade::launch_rate(c->dim, c->p.kernel, c->iso, ade::EPI_RATE, c->w.P0, c->w.P0, c->w.cell_start,
-                            c->w.idx[c->sorted_buf], c->rp, out, s));
+                            c->w.perm, c->rp, out, s));
     return ADE_OK;
 }
 
@@ -520,7 +588,7 @@ int ade_count_pairs(ade_ctx *c, long long *pairs_host, void *stream)
     ade::EpiOut out = epi_none();
     out.pairs = c->w.pairs;
     ADE_CK(ade::launch_rate(c->dim, c->p.kernel, c->iso, ade::EPI_RATE, c->w.P0, c->w.P0, c->w.cell_start,
-                            c->w.idx[c->sorted_buf], c->rp, out, s));
+                            c->w.perm, c->rp, out, s));
     unsigned long long v = 0;
     ADE_CK(cudaMemcpyAsync(&v, c->w.pairs, 8, cudaMemcpyDeviceToHost, s));
     ADE_CK(cudaStreamSynchronize(s));
@@ -615,7 +683,7 @@ int ade_step_timed(ade_ctx *c, double *phase_ms, void *stream)
     if (rc) return rc;
     ADE_CK(cudaEventRecord(c->ev[1], s));
     if (c->n > 0) {
-        const uint32_t *perm = c->w.idx[c->sorted_buf];
+        const uint32_t *perm = c->w.perm;
         ade::RateParams rp = c->rp;
         ade::EpiOut out = epi_none();
         rp.dt = (float)(0.5 * c->dt);
@@ -630,11 +698,12 @@ int ade_step_timed(ade_ctx *c, double *phase_ms, void *stream)
         out.xq = c->xq;
         out.C = c->C;
         out.partials = c->w.partials;
+        out.stats = c->w.stats;
+        out.done = c->w.done;
         out.status = c->w.status;
         ADE_CK(ade::launch_rate(c->dim, c->p.kernel, c->iso, ade::EPI_CORRECT, c->w.P1, c->w.P0,
                                 c->w.cell_start, perm, rp, out, s));
         ADE_CK(cudaEventRecord(c->ev[3], s));
-        ADE_CK(ade::launch_reduce_final(c->w.partials, ade::rate_blocks(c->n), c->w.stats, s));
     } else {
         ADE_CK(cudaEventRecord(c->ev[2], s));
         ADE_CK(cudaEventRecord(c->ev[3], s));
@@ -654,7 +723,8 @@ int ade_step_timed(ade_ctx *c, double *phase_ms, void *stream)
 int ade_launches_per_step(const ade_ctx *c, int *launches)
 {
     if (!c || !launches) return fail(ADE_ERR_ARG, "NULL argument");
-    *launches = c->n > 0 ? 3 * c->passes + 1 + 2 + 1 : 0;
+    // count, 3 scan launches, place, order, predictor, corrector (the memset is not a kernel)
+    *launches = c->n > 0 ? 8 : 4;
     return ADE_OK;
 }
 

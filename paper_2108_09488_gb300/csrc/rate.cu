@@ -4,23 +4,30 @@
 // For a uniform velocity field (Sec. 3) every particle carries the same tensor D (Eq. 3), so the
 // per-component harmonic mean of Eq. 5 is 4 D D / (D + D) = 2 D and the pair factor reduces to
 //     Dcal_ab = Gamma x_ab^T K x_ab / r^2 - tr K,   K = 2 D,
-// evaluated as x^T (Gamma K - Gamma K_zz I) x / r^2 + (Gamma K_zz - tr K) (K_yy in 2D), which
-// drops the diagonal term of the last axis from the per-pair work.
+// evaluated as x^T (Gamma K - Gamma K_last I) x / r^2 + (Gamma K_last - tr K), K_last = K_yy in
+// 2D and K_zz in 3D, which drops one diagonal term from the per-pair work.
 // With grad_a W = W'(r) x_ab / r, the dispersive term of Eq. 4 for one ordered pair is
 //     1/2 (m_b / rhobar) Dcal_ab (C_a - C_b) W'(r) / r,
 // and W'(r)/r = kc f(q): Wendland C2 (support H = 2h): f = (1-q)^3, kc = -20 B / H^2;
 // Wendland C4 (Eq. 7, support H = h): f = (1-q)^5 (1+5q), kc = -(56/3) B / H^2.
 // The convective term of Eq. 4 is identically zero for uniform v and is not evaluated.
 //
-// Layout and arithmetic:
-//   * one thread per particle in cell-sorted order; the particle's cell comes from the cell-build
-//     positions, its pair terms from the evaluation positions (they differ by the half-step drift);
-//   * candidates are read as one 16-byte word {x, y, z, C} from the sorted copy; each stencil row
-//     (2w+1 cells with consecutive keys) is one contiguous index range, two at a periodic seam;
-//   * separations are int32 differences of fixed-point words converted to FP32, so the minimum
-//     image and translation invariance are exact; pair arithmetic is FP32;
-//   * each row's terms are summed in FP32 and the row sums are added with Neumaier's compensated
-//     summation, in a fixed order (rows, then sorted index), so results are deterministic.
+// Two variants share the pair arithmetic and the epilogue:
+//   * direct: one thread per cell-sorted particle; candidates are read from the sorted copy in
+//     global memory (L1-cached 16-byte words {x, y, z, C}); separations are int32 differences of
+//     fixed-point words converted to FP32 for every pair; each stencil row (2w+1 cells with
+//     consecutive keys) is one contiguous index range, two at a periodic seam.
+//   * tiled: one CTA per block of TX x TY (x TZ) cells.  The CTA stages every particle of the
+//     block and its k-cell halo into shared memory once, as int32 fixed-point offsets from the
+//     block centre (the minimum image from the centre), plus a local cell start table.  Each
+//     thread then walks its targets' stencil rows over shared memory; the pair separation is the
+//     exact int32 difference converted to FP32, as in the direct walk, so both variants round
+//     relative to the separation itself rather than to the block size.  The pair term is
+//     evaluated without a branch: outside the support (1 - q) is clamped to 0, so the term
+//     vanishes.  A block whose halo does not fit the staging buffer falls back to the direct walk.
+// Both variants sum each stencil row's terms in FP32 and add the row sums with Neumaier's
+// compensated summation, visiting rows and, inside a row, particles in sorted order, so results
+// are deterministic and independent of the tiling.
 #include "ade_internal.h"
 
 namespace ade {
@@ -37,12 +44,59 @@ __device__ __forceinline__ void neumaier_add(float &sum, float &comp, float x)
     sum = t;
 }
 
+__device__ __forceinline__ double dinf() { return __longlong_as_double(0x7ff0000000000000ll); }
+
+// Kernel shape factor f(q) with W'(r)/r = kc f(q); omq = 1 - q (clamped at 0 by the caller for the
+// branch-free form).
+template <int KERNEL>
+__device__ __forceinline__ float shape(float omq)
+{
+    if (KERNEL == ADE_WENDLAND_C2) return omq * omq * omq;
+    float o2 = omq * omq;
+    return o2 * o2 * omq * fmaf(-5.f, omq, 6.f);  // (1-q)^5 (1 + 5q), 1 + 5q = 6 - 5(1-q)
+}
+
+// In-support test of the pair counter, taken in FP64 with the operation order of a plain FP64
+// evaluation (d_i = int difference x unit, r^2 = (d_x^2 + d_y^2) + d_z^2, no fused multiply-add),
+// so the integer count does not depend on FP32 rounding at |x_ab| = H.
+template <int DIM>
+__device__ __forceinline__ unsigned in_support_fp64(int ix, int iy, int iz, const RateParams &prm)
+{
+    const double dx = (double)ix * prm.u[0], dy = (double)iy * prm.u[1];
+    double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    if (DIM == 3) {
+        const double dz = (double)iz * prm.u[2];
+        r2 = __dadd_rn(r2, __dmul_rn(dz, dz));
+    }
+    return (r2 > 0.0 && r2 < prm.H2d) ? 1u : 0u;
+}
+
+// Dcal factor of the pair (without the kernel shape): x^T Kc x / r^2 + c0.
+template <int DIM>
+__device__ __forceinline__ float dcal(float dx, float dy, float dz, float rinv2, const RateParams &prm)
+{
+    float Q;
+    if (DIM == 2) {
+        Q = dx * fmaf(prm.Kc[0], dx, prm.Kc[3] * dy);
+    } else {
+        float qx = fmaf(prm.Kc[0], dx, fmaf(prm.Kc[3], dy, prm.Kc[4] * dz));
+        float qy = fmaf(prm.Kc[1], dy, prm.Kc[5] * dz);
+        Q = fmaf(dx, qx, dy * qy);
+    }
+    return fmaf(Q, rinv2, prm.c0);
+}
+
+// ---------------------------------------------------------------------------------------------
+// direct walk over global memory
+// ---------------------------------------------------------------------------------------------
 template <int DIM, int KERNEL, bool ISO, bool COUNT>
-__device__ __forceinline__ void pair_range(const uint4 *__restrict__ P, int j0, int j1, const uint4 &pa,
-                                           float Ca, const RateParams &prm, float &rs, unsigned &cnt)
+__device__ __forceinline__ void pair_range_direct(const uint4 *__restrict__ P, int j0, int j1,
+                                                  const uint4 &pa, float Ca, const RateParams &prm,
+                                                  float &rs, unsigned &cnt)
 {
     for (int j = j0; j < j1; ++j) {
         uint4 pb = __ldg(P + j);
+        if (COUNT) cnt += in_support_fp64<DIM>((int)(pa.x - pb.x), (int)(pa.y - pb.y), (int)(pa.z - pb.z), prm);
         float dx = (float)(int)(pa.x - pb.x);
         float dy = (float)(int)(pa.y - pb.y);
         float dz = 0.f;
@@ -56,53 +110,22 @@ __device__ __forceinline__ void pair_range(const uint4 *__restrict__ P, int j0, 
         if (r2 < prm.H2 && r2 > 0.f) {
             float rinv = rsqrtf(r2);
             float r = r2 * rinv;
-            float f;
-            if (KERNEL == ADE_WENDLAND_C2) {
-                float omq = fmaf(-r, prm.invH, 1.f);
-                f = omq * omq * omq;
-            } else {
-                float q = r * prm.invH;
-                float omq = 1.f - q;
-                float o2 = omq * omq;
-                f = o2 * o2 * omq * fmaf(5.f, q, 1.f);
-            }
-            // Gamma x^T K x = Gamma K_last r^2 + x^T (Gamma K - Gamma K_last I) x: the r^2 part
-            // is folded into the constant c0 = Gamma K_last - tr K.
-            float Q;
-            if (DIM == 2) {
-                Q = dx * fmaf(prm.Kc[0], dx, prm.Kc[3] * dy);
-            } else {
-                float qx = fmaf(prm.Kc[0], dx, fmaf(prm.Kc[3], dy, prm.Kc[4] * dz));
-                float qy = fmaf(prm.Kc[1], dy, prm.Kc[5] * dz);
-                Q = fmaf(dx, qx, dy * qy);
-            }
-            float sfac = fmaf(Q, rinv * rinv, prm.c0);
-            rs = fmaf(f * sfac, Ca - __uint_as_float(pb.w), rs);
-            if (COUNT) ++cnt;
+            float f = shape<KERNEL>(fmaf(-r, prm.invH, 1.f));
+            float s = dcal<DIM>(dx, dy, dz, rinv * rinv, prm);
+            rs = fmaf(f * s, Ca - __uint_as_float(pb.w), rs);
         }
     }
 }
 
-template <int DIM, int KERNEL, int EPI, bool ISO, bool COUNT>
-__global__ __launch_bounds__(kRateThreads) void k_rate(const uint4 *__restrict__ Pe,
-                                                       const uint4 *__restrict__ Pc,
-                                                       const uint32_t *__restrict__ cs,
-                                                       const uint32_t *__restrict__ perm,
-                                                       const RateParams prm, const EpiOut out)
+// Eq. 4 at one particle by the direct walk; (cx, cy, cz) is its cell.
+template <int DIM, int KERNEL, bool ISO, bool COUNT>
+__device__ float rate_direct(const uint4 *__restrict__ Pe, const uint32_t *__restrict__ cs,
+                             const uint4 &pa, int cx, int cy, int cz, const RateParams &prm,
+                             unsigned &cnt)
 {
-    const int i = blockIdx.x * kRateThreads + threadIdx.x;
-    const bool valid = i < prm.n;
-    const int ii = valid ? i : prm.n - 1;
-    const uint4 pa = __ldg(Pe + ii);
-    const uint4 pc = (Pe == Pc) ? pa : __ldg(Pc + ii);
     const int ncx = prm.ncx, ncy = prm.ncy, ncz = prm.ncz;
-    const int cx = (int)__umulhi(pc.x, (uint32_t)ncx);
-    const int cy = (int)__umulhi(pc.y, (uint32_t)ncy);
-    const int cz = DIM == 3 ? (int)__umulhi(pc.z, (uint32_t)ncz) : 0;
     const float Ca = __uint_as_float(pa.w);
-
     float acc = 0.f, comp = 0.f;
-    unsigned cnt = 0u;
     for (int ri = 0; ri < prm.nrows; ++ri) {
         const StencilRow row = prm.rows[ri];
         int yy = cy + row.dy;
@@ -132,126 +155,420 @@ __global__ __launch_bounds__(kRateThreads) void k_rate(const uint4 *__restrict__
             e0 = __ldg(cs + base + hi);
         }
         float rs = 0.f;
-        pair_range<DIM, KERNEL, ISO, COUNT>(Pe, s0, e0, pa, Ca, prm, rs, cnt);
-        pair_range<DIM, KERNEL, ISO, COUNT>(Pe, s1, e1, pa, Ca, prm, rs, cnt);
+        pair_range_direct<DIM, KERNEL, ISO, COUNT>(Pe, s0, e0, pa, Ca, prm, rs, cnt);
+        pair_range_direct<DIM, KERNEL, ISO, COUNT>(Pe, s1, e1, pa, Ca, prm, rs, cnt);
         neumaier_add(acc, comp, rs);
     }
-    const float rate = prm.pf * (acc + comp);
+    return prm.pf * (acc + comp);
+}
 
-    if (COUNT) {
-        unsigned c = valid ? cnt : 0u;
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-        if ((threadIdx.x & 31) == 0 && c) atomicAdd(out.pairs, (unsigned long long)c);
-    }
+// ---------------------------------------------------------------------------------------------
+// epilogue and block reductions
+// ---------------------------------------------------------------------------------------------
+struct Acc {
+    double s, mn, mx;
+    unsigned cnt;
+};
 
+// Writes of one particle at sorted position gi; pe = evaluation state, pc = cell-build state.
+template <int DIM, int EPI>
+__device__ __forceinline__ void epilogue(int gi, float rate, const uint4 &pe, const uint4 &pc,
+                                         const uint32_t *__restrict__ perm, const RateParams &prm,
+                                         const EpiOut &out, Acc &acc)
+{
     if (EPI == EPI_RATE) {
-        if (valid && out.rate) {
-            const uint32_t a = __ldg(perm + i);
+        if (out.rate) {
+            const uint32_t a = __ldg(perm + gi);
             if (a < (uint32_t)prm.n) out.rate[a] = rate;
         }
     } else if (EPI == EPI_PREDICT) {
-        if (valid) {
-            uint4 q;
-            q.x = pa.x + prm.inc[0];
-            q.y = pa.y + prm.inc[1];
-            q.z = pa.z + prm.inc[2];
-            q.w = __float_as_uint(fmaf(prm.dt, rate, Ca));
-            out.Pout[i] = q;
-        }
+        // C^{l+1/2} = C^l + dt/2 r^l, x^{l+1/2} = x^l + dt/2 v
+        uint4 q;
+        q.x = pe.x + prm.inc[0];
+        q.y = pe.y + prm.inc[1];
+        q.z = pe.z + prm.inc[2];
+        q.w = __float_as_uint(fmaf(prm.dt, rate, __uint_as_float(pe.w)));
+        out.Pout[gi] = q;
     } else {
-        // corrector: C^{l+1} = C^l + dt r^{l+1/2}, x^{l+1} = x^l + dt v, back to caller order
-        double s = 0.0, mn = __longlong_as_double(0x7ff0000000000000ll), mx = -mn;
-        if (valid) {
-            const float Cl = __uint_as_float(pc.w);
-            const float Cn = fmaf(prm.dt, rate, Cl);
-            const uint32_t a = __ldg(perm + i);
-            if (a < (uint32_t)prm.n) {
-                out.C[a] = Cn;
-                out.xq[a] = pc.x + prm.inc[0];
-                out.xq[(size_t)prm.n + a] = pc.y + prm.inc[1];
-                if (DIM == 3) out.xq[2 * (size_t)prm.n + a] = pc.z + prm.inc[2];
-            }
-            if (!isfinite(Cn)) atomicOr(out.status, 1);
-            s = (double)Cn;
-            mn = s;
-            mx = s;
+        // C^{l+1} = C^l + dt r^{l+1/2}, x^{l+1} = x^l + dt v, back to the caller's order
+        const float Cn = fmaf(prm.dt, rate, __uint_as_float(pc.w));
+        const uint32_t a = __ldg(perm + gi);
+        if (a < (uint32_t)prm.n) {
+            out.C[a] = Cn;
+            out.xq[a] = pc.x + prm.inc[0];
+            out.xq[(size_t)prm.n + a] = pc.y + prm.inc[1];
+            if (DIM == 3) out.xq[2 * (size_t)prm.n + a] = pc.z + prm.inc[2];
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            s += __shfl_down_sync(0xffffffffu, s, o);
-            mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
-            mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
-        }
-        __shared__ double red[3][kRateThreads / 32];
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        if (lane == 0) {
-            red[0][wid] = s;
-            red[1][wid] = mn;
-            red[2][wid] = mx;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double a = red[0][0], b = red[1][0], c = red[2][0];
-            for (int w = 1; w < kRateThreads / 32; ++w) {
-                a += red[0][w];
-                b = fmin(b, red[1][w]);
-                c = fmax(c, red[2][w]);
-            }
-            out.partials[3 * (size_t)blockIdx.x + 0] = a;
-            out.partials[3 * (size_t)blockIdx.x + 1] = b;
-            out.partials[3 * (size_t)blockIdx.x + 2] = c;
-        }
+        if (!isfinite(Cn)) atomicOr(out.status, 1);
+        const double d = (double)Cn;
+        acc.s += d;
+        acc.mn = fmin(acc.mn, d);
+        acc.mx = fmax(acc.mx, d);
     }
 }
 
-template <int DIM, int KERNEL, bool ISO, bool COUNT>
-cudaError_t launch_epi(int epi, int blocks, const uint4 *Pe, const uint4 *Pc, const uint32_t *cs,
-                       const uint32_t *perm, const RateParams &prm, const EpiOut &out, cudaStream_t s)
+// Fixed-order reduction of nb partial triples {sum, min, max} by one block of NT threads.
+template <int NT>
+__device__ void reduce_partials_last_block(const double *partials, int nb, double *stats)
 {
-    switch (epi) {
-    case EPI_RATE:
-        k_rate<DIM, KERNEL, EPI_RATE, ISO, COUNT><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
-        break;
-    case EPI_PREDICT:
-        k_rate<DIM, KERNEL, EPI_PREDICT, ISO, COUNT><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
-        break;
-    default:
-        k_rate<DIM, KERNEL, EPI_CORRECT, ISO, COUNT><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
-        break;
+    __shared__ double sh[3][NT];
+    double a = 0.0, b = dinf(), c = -dinf();
+    for (int k = threadIdx.x; k < nb; k += NT) {
+        a += __ldcg(partials + 3 * (size_t)k + 0);
+        b = fmin(b, __ldcg(partials + 3 * (size_t)k + 1));
+        c = fmax(c, __ldcg(partials + 3 * (size_t)k + 2));
     }
+    sh[0][threadIdx.x] = a;
+    sh[1][threadIdx.x] = b;
+    sh[2][threadIdx.x] = c;
+    __syncthreads();
+    for (int o = NT / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+            sh[1][threadIdx.x] = fmin(sh[1][threadIdx.x], sh[1][threadIdx.x + o]);
+            sh[2][threadIdx.x] = fmax(sh[2][threadIdx.x], sh[2][threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        stats[0] = sh[0][0];
+        stats[1] = sh[1][0];
+        stats[2] = sh[2][0];
+    }
+}
+
+// Block-wide part of the epilogue: pair count, and for the corrector the per-block partials and
+// the last block's final reduction.  Every thread of the block must call it.
+template <int EPI, bool COUNT, int NT>
+__device__ __forceinline__ void block_finish(Acc acc, const EpiOut &out)
+{
+    if (COUNT) {
+        unsigned c = acc.cnt;
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+        if ((threadIdx.x & 31) == 0 && c) atomicAdd(out.pairs, (unsigned long long)c);
+    }
+    if (EPI != EPI_CORRECT) return;
+    double s = acc.s, mn = acc.mn, mx = acc.mx;
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_down_sync(0xffffffffu, s, o);
+        mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    }
+    __shared__ double red[3][NT / 32];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][wid] = s;
+        red[1][wid] = mn;
+        red[2][wid] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = red[0][0], b = red[1][0], c = red[2][0];
+        for (int w = 1; w < NT / 32; ++w) {
+            a += red[0][w];
+            b = fmin(b, red[1][w]);
+            c = fmax(c, red[2][w]);
+        }
+        out.partials[3 * (size_t)blockIdx.x + 0] = a;
+        out.partials[3 * (size_t)blockIdx.x + 1] = b;
+        out.partials[3 * (size_t)blockIdx.x + 2] = c;
+        __threadfence();
+        last = atomicAdd(out.done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+        // the last block to finish reduces every block's partials in a fixed order
+        __threadfence();
+        reduce_partials_last_block<NT>(out.partials, gridDim.x, out.stats);
+        if (threadIdx.x == 0) *out.done = 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// direct kernel
+// ---------------------------------------------------------------------------------------------
+template <int DIM, int KERNEL, int EPI, bool ISO, bool COUNT>
+__global__ __launch_bounds__(kRateThreads) void k_rate(const uint4 *__restrict__ Pe,
+                                                       const uint4 *__restrict__ Pc,
+                                                       const uint32_t *__restrict__ cs,
+                                                       const uint32_t *__restrict__ perm,
+                                                       const RateParams prm, const EpiOut out)
+{
+    const int i = blockIdx.x * kRateThreads + threadIdx.x;
+    const bool valid = i < prm.n;
+    const int ii = valid ? i : prm.n - 1;
+    const uint4 pa = __ldg(Pe + ii);
+    const uint4 pc = (Pe == Pc) ? pa : __ldg(Pc + ii);
+    const int cx = (int)__umulhi(pc.x, (uint32_t)prm.ncx);
+    const int cy = (int)__umulhi(pc.y, (uint32_t)prm.ncy);
+    const int cz = DIM == 3 ? (int)__umulhi(pc.z, (uint32_t)prm.ncz) : 0;
+    Acc acc{0.0, dinf(), -dinf(), 0u};
+    unsigned cnt = 0u;
+    const float rate = rate_direct<DIM, KERNEL, ISO, COUNT>(Pe, cs, pa, cx, cy, cz, prm, cnt);
+    if (valid) {
+        acc.cnt = cnt;
+        epilogue<DIM, EPI>(i, rate, pa, pc, perm, prm, out, acc);
+    }
+    block_finish<EPI, COUNT, kRateThreads>(acc, out);
+}
+
+// ---------------------------------------------------------------------------------------------
+// tiled kernel
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ int wrap_cell(int c, int n)
+{
+    c %= n;
+    return c < 0 ? c + n : c;
+}
+
+// Shared-memory layout of the tiled kernel (dynamic shared memory):
+//   int4   sp[cap]                staged particles {x, y, z, C bits}, offsets from the centre
+//   int    lcs[hrows][HX + 1]     local start of every halo cell, per halo row (+ row end)
+//   int    trow[3][tr + 1]        per inner row: target prefix, global sorted start, local start
+template <int DIM, int KERNEL, int EPI, bool COUNT>
+__global__ __launch_bounds__(kTileThreads, 2) void k_rate_tiled(const uint4 *__restrict__ Pe,
+                                                             const uint4 *__restrict__ Pc,
+                                                             const uint32_t *__restrict__ cs,
+                                                             const uint32_t *__restrict__ perm,
+                                                             const RateParams prm, const EpiOut out)
+{
+    extern __shared__ float4 smem[];
+    __shared__ int s_total;
+    __shared__ int wsum[kTileThreads / 32];
+    const int k = prm.k;
+    const int TX = prm.tx, TY = prm.ty, TZ = DIM == 3 ? prm.tz : 1;
+    const int HX = TX + 2 * k, HY = TY + 2 * k, HZ = DIM == 3 ? TZ + 2 * k : 1;
+    const int kz = DIM == 3 ? k : 0;
+    const int ncx = prm.ncx, ncy = prm.ncy, ncz = prm.ncz;
+    const int b = blockIdx.x;
+    const int tx0 = (b % prm.ntx) * TX;
+    const int ty0 = ((b / prm.ntx) % prm.nty) * TY;
+    const int tz0 = DIM == 3 ? (b / (prm.ntx * prm.nty)) * TZ : 0;
+    const int vx = min(TX, ncx - tx0), vy = min(TY, ncy - ty0), vz = DIM == 3 ? min(TZ, ncz - tz0) : 1;
+    const int hrows = HY * HZ;
+    const int NH = HX * hrows;
+    const int tr = TY * TZ;
+
+    int4 *sp = reinterpret_cast<int4 *>(smem);
+    int *lcs = reinterpret_cast<int *>(sp + prm.cap);
+    int *tpre = lcs + hrows * (HX + 1);
+    int *tglb = tpre + tr + 1;
+    int *tloc = tglb + tr + 1;
+
+    // 1. counts of the halo cells, exclusive scan in (row, x) order -> local cell starts
+    int carry = 0;
+    for (int h0 = 0; h0 < NH; h0 += kTileThreads) {
+        const int h = h0 + threadIdx.x;
+        int cnt = 0, hx = 0, row = 0;
+        if (h < NH) {
+            hx = h % HX;
+            row = h / HX;
+            const int hy = row % HY, hz = row / HY;
+            const int gx = wrap_cell(tx0 - k + hx, ncx);
+            const int gy = wrap_cell(ty0 - k + hy, ncy);
+            const int gz = DIM == 3 ? wrap_cell(tz0 - k + hz, ncz) : 0;
+            const int g = (gz * ncy + gy) * ncx + gx;
+            cnt = (int)(__ldg(cs + g + 1) - __ldg(cs + g));
+        }
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            int v = lane < kTileThreads / 32 ? wsum[lane] : 0;
+            int vi = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, vi, o);
+                if (lane >= o) vi += y;
+            }
+            if (lane < kTileThreads / 32) wsum[lane] = vi - v;
+            if (lane == kTileThreads / 32 - 1) s_total = vi;
+        }
+        __syncthreads();
+        const int excl = carry + wsum[wid] + incl - cnt;
+        if (h < NH) {
+            lcs[row * (HX + 1) + hx] = excl;
+            if (hx == HX - 1) lcs[row * (HX + 1) + HX] = excl + cnt;
+        }
+        carry += s_total;
+        __syncthreads();
+    }
+    // 2. target rows: inner cells [tx0, tx0 + vx) of every inner row, contiguous in sorted order
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int r = 0; r < tr; ++r) {
+            const int iy = r % TY, iz = r / TY;
+            tpre[r] = run;
+            tglb[r] = 0;
+            tloc[r] = 0;
+            if (iy < vy && iz < vz) {
+                const int g = ((tz0 + iz) * ncy + (ty0 + iy)) * ncx + tx0;
+                const int g0 = (int)__ldg(cs + g), g1 = (int)__ldg(cs + g + vx);
+                tglb[r] = g0;
+                tloc[r] = lcs[((iz + kz) * HY + (iy + k)) * (HX + 1) + k];
+                run += g1 - g0;
+            }
+        }
+        tpre[tr] = run;
+    }
+    __syncthreads();
+    const int ntarget = tpre[tr];
+    const bool staged = carry <= prm.cap;
+
+    // 3. stage the halo: one thread per halo cell copies that cell's particles
+    if (staged) {
+        const uint32_t ox = (uint32_t)(((unsigned long long)(2 * tx0 + TX) << 31) / (unsigned)ncx);
+        const uint32_t oy = (uint32_t)(((unsigned long long)(2 * ty0 + TY) << 31) / (unsigned)ncy);
+        const uint32_t oz =
+            DIM == 3 ? (uint32_t)(((unsigned long long)(2 * tz0 + TZ) << 31) / (unsigned)ncz) : 0u;
+        for (int h = threadIdx.x; h < NH; h += kTileThreads) {
+            const int hx = h % HX, row = h / HX;
+            const int hy = row % HY, hz = row / HY;
+            const int gx = wrap_cell(tx0 - k + hx, ncx);
+            const int gy = wrap_cell(ty0 - k + hy, ncy);
+            const int gz = DIM == 3 ? wrap_cell(tz0 - k + hz, ncz) : 0;
+            const int g = (gz * ncy + gy) * ncx + gx;
+            const int g0 = (int)__ldg(cs + g), g1 = (int)__ldg(cs + g + 1);
+            const int l0 = lcs[row * (HX + 1) + hx];
+            for (int p = g0; p < g1; ++p) {
+                const uint4 q = __ldg(Pe + p);
+                sp[l0 + (p - g0)] = make_int4((int)(q.x - ox), (int)(q.y - oy),
+                                              DIM == 3 ? (int)(q.z - oz) : 0, (int)q.w);
+            }
+        }
+    }
+    __syncthreads();
+
+    // 4. targets: thread t takes targets t, t + NT, ... in (row, sorted) order
+    Acc acc{0.0, dinf(), -dinf(), 0u};
+    int r = 0;
+    for (int t = threadIdx.x; t < ntarget; t += kTileThreads) {
+        while (tpre[r + 1] <= t) ++r;
+        const int off = t - tpre[r];
+        const int gi = tglb[r] + off;
+        const uint4 pe = __ldg(Pe + gi);
+        const uint4 pc = (Pe == Pc) ? pe : __ldg(Pc + gi);
+        const int cx = (int)__umulhi(pc.x, (uint32_t)ncx);
+        const int cy = (int)__umulhi(pc.y, (uint32_t)ncy);
+        const int cz = DIM == 3 ? (int)__umulhi(pc.z, (uint32_t)ncz) : 0;
+        float rate;
+        unsigned cnt = 0u;
+        if (staged) {
+            const int4 a = sp[tloc[r] + off];
+            const float Ca = __int_as_float(a.w);
+            const int hx = cx - tx0 + k, hy = cy - ty0 + k, hz = DIM == 3 ? cz - tz0 + k : 0;
+            float sum = 0.f, comp = 0.f;
+            for (int ri = 0; ri < prm.nrows; ++ri) {
+                const StencilRow row = prm.rows[ri];
+                const int *lrow = lcs + ((hz + row.dz) * HY + (hy + row.dy)) * (HX + 1);
+                const int j0 = lrow[hx - row.w], j1 = lrow[hx + row.w + 1];
+                float rs = 0.f;
+#pragma unroll 2
+                for (int j = j0; j < j1; ++j) {
+                    const int4 q = sp[j];
+                    const float dx = (float)(a.x - q.x), dy = (float)(a.y - q.y);
+                    const float dz = DIM == 3 ? (float)(a.z - q.z) : 0.f;
+                    float r2 = fmaf(dx, dx, dy * dy);
+                    if (DIM == 3) r2 = fmaf(dz, dz, r2);
+                    const float rinv = rsqrtf(fmaxf(r2, 1.0f));
+                    const float omq = fmaxf(fmaf(-r2 * rinv, prm.invH, 1.f), 0.f);
+                    const float s = dcal<DIM>(dx, dy, dz, rinv * rinv, prm);
+                    const float w = r2 > 0.f ? shape<KERNEL>(omq) * s : 0.f;
+                    rs = fmaf(w, Ca - __int_as_float(q.w), rs);
+                    if (COUNT) cnt += in_support_fp64<DIM>(a.x - q.x, a.y - q.y, a.z - q.z, prm);
+                }
+                neumaier_add(sum, comp, rs);
+            }
+            rate = prm.pf * (sum + comp);
+        } else {
+            rate = rate_direct<DIM, KERNEL, true, COUNT>(Pe, cs, pe, cx, cy, cz, prm, cnt);
+        }
+        acc.cnt += cnt;
+        epilogue<DIM, EPI>(gi, rate, pe, pc, perm, prm, out, acc);
+    }
+    block_finish<EPI, COUNT, kTileThreads>(acc, out);
+}
+
+// ---------------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------------
+template <int DIM, int KERNEL, int EPI, bool COUNT>
+cudaError_t launch_variant(bool iso, const uint4 *Pe, const uint4 *Pc, const uint32_t *cs,
+                           const uint32_t *perm, const RateParams &prm, const EpiOut &out, cudaStream_t s)
+{
+    if (prm.variant == 1 && iso) {
+        const int blocks = prm.ntx * prm.nty * (DIM == 3 ? prm.ntz : 1);
+        const size_t smem = tiled_smem_bytes(DIM, prm);
+        auto fn = k_rate_tiled<DIM, KERNEL, EPI, COUNT>;
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        fn<<<blocks, kTileThreads, smem, s>>>(Pe, Pc, cs, perm, prm, out);
+        return cudaGetLastError();
+    }
+    const int blocks = rate_blocks(prm.n);
+    if (iso)
+        k_rate<DIM, KERNEL, EPI, true, COUNT><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
+    else
+        k_rate<DIM, KERNEL, EPI, false, COUNT><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
     return cudaGetLastError();
 }
 
+template <int DIM, int KERNEL, bool COUNT>
+cudaError_t launch_epi(int epi, bool iso, const uint4 *Pe, const uint4 *Pc, const uint32_t *cs,
+                       const uint32_t *perm, const RateParams &prm, const EpiOut &out, cudaStream_t s)
+{
+    switch (epi) {
+    case EPI_RATE: return launch_variant<DIM, KERNEL, EPI_RATE, COUNT>(iso, Pe, Pc, cs, perm, prm, out, s);
+    case EPI_PREDICT: return launch_variant<DIM, KERNEL, EPI_PREDICT, COUNT>(iso, Pe, Pc, cs, perm, prm, out, s);
+    default: return launch_variant<DIM, KERNEL, EPI_CORRECT, COUNT>(iso, Pe, Pc, cs, perm, prm, out, s);
+    }
+}
+
 template <int DIM, int KERNEL>
-cudaError_t launch_dk(bool iso, bool count, int epi, int blocks, const uint4 *Pe, const uint4 *Pc,
+cudaError_t launch_dk(bool iso, bool count, int epi, const uint4 *Pe, const uint4 *Pc,
                       const uint32_t *cs, const uint32_t *perm, const RateParams &prm,
                       const EpiOut &out, cudaStream_t s)
 {
-    if (iso) {
-        return count ? launch_epi<DIM, KERNEL, true, true>(epi, blocks, Pe, Pc, cs, perm, prm, out, s)
-                     : launch_epi<DIM, KERNEL, true, false>(epi, blocks, Pe, Pc, cs, perm, prm, out, s);
-    }
-    return count ? launch_epi<DIM, KERNEL, false, true>(epi, blocks, Pe, Pc, cs, perm, prm, out, s)
-                 : launch_epi<DIM, KERNEL, false, false>(epi, blocks, Pe, Pc, cs, perm, prm, out, s);
+    return count ? launch_epi<DIM, KERNEL, true>(epi, iso, Pe, Pc, cs, perm, prm, out, s)
+                 : launch_epi<DIM, KERNEL, false>(epi, iso, Pe, Pc, cs, perm, prm, out, s);
 }
 
 }  // namespace
 
 int rate_blocks(int n) { return (n + kRateThreads - 1) / kRateThreads; }
 
+int rate_launch_blocks(int dim, const RateParams &prm, bool iso)
+{
+    if (prm.variant == 1 && iso) return prm.ntx * prm.nty * (dim == 3 ? prm.ntz : 1);
+    return rate_blocks(prm.n);
+}
+
+size_t tiled_smem_bytes(int dim, const RateParams &prm)
+{
+    const int k = prm.k;
+    const int HX = prm.tx + 2 * k, HY = prm.ty + 2 * k, HZ = dim == 3 ? prm.tz + 2 * k : 1;
+    const int tr = prm.ty * (dim == 3 ? prm.tz : 1);
+    return (size_t)prm.cap * 16 + (size_t)HY * HZ * (HX + 1) * 4 + (size_t)3 * (tr + 1) * 4;
+}
+
 cudaError_t launch_rate(int dim, int kernel, bool iso, int epi, const uint4 *Pe, const uint4 *Pc,
                         const uint32_t *cell_start, const uint32_t *perm, const RateParams &prm,
                         const EpiOut &out, cudaStream_t s)
 {
-    const int blocks = rate_blocks(prm.n);
-    if (blocks == 0) return cudaSuccess;
+    if (prm.n == 0) return cudaSuccess;
     const bool count = out.pairs != nullptr;
     if (dim == 2)
         return kernel == ADE_WENDLAND_C2
-                   ? launch_dk<2, ADE_WENDLAND_C2>(iso, count, epi, blocks, Pe, Pc, cell_start, perm, prm, out, s)
-                   : launch_dk<2, ADE_WENDLAND_C4>(iso, count, epi, blocks, Pe, Pc, cell_start, perm, prm, out, s);
+                   ? launch_dk<2, ADE_WENDLAND_C2>(iso, count, epi, Pe, Pc, cell_start, perm, prm, out, s)
+                   : launch_dk<2, ADE_WENDLAND_C4>(iso, count, epi, Pe, Pc, cell_start, perm, prm, out, s);
     return kernel == ADE_WENDLAND_C2
-               ? launch_dk<3, ADE_WENDLAND_C2>(iso, count, epi, blocks, Pe, Pc, cell_start, perm, prm, out, s)
-               : launch_dk<3, ADE_WENDLAND_C4>(iso, count, epi, blocks, Pe, Pc, cell_start, perm, prm, out, s);
+               ? launch_dk<3, ADE_WENDLAND_C2>(iso, count, epi, Pe, Pc, cell_start, perm, prm, out, s)
+               : launch_dk<3, ADE_WENDLAND_C4>(iso, count, epi, Pe, Pc, cell_start, perm, prm, out, s);
 }
 
 }  // namespace ade

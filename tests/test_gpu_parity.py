@@ -97,14 +97,52 @@ def test_cells_bit_exact_every_subdivision(lib, orc, k):
     assert np.array_equal(perm, perm_o) and np.array_equal(cs, cs_o)
 
 
+VARIANTS = {"tiled": 2, "direct": 1}     # ADE_FLAG_TILED, ADE_FLAG_DIRECT
+
+
+@pytest.mark.parametrize("variant", sorted(VARIANTS))
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_rate_parity(lib, orc, name):
+def test_rate_parity(lib, orc, name, variant):
     plume = CASES[name]()
     xq, C = plume.initial_state()
-    sim = _sim(lib, plume)
+    sim = _sim(lib, plume, flags=VARIANTS[variant])
+    if variant == "direct":
+        assert sim.info.variant == 0
     r_gpu = sim.rate().cpu().numpy()
     r_orc, pairs = _oracle_rate(orc, plume, xq, C)
     assert _rel(r_gpu, r_orc) <= RATE_TOL
+    assert sim.count_pairs() == pairs
+
+
+def test_tiled_variant_is_used_and_deterministic(lib):
+    plume = inputs.ladder_2d(512, 10)
+    a = _sim(lib, plume, flags=lib.FLAG_TILED)
+    assert a.info.variant == 1 and a.info.tile_capacity > 0
+    r1 = a.rate().cpu().numpy()
+    r2 = a.rate().cpu().numpy()
+    assert np.array_equal(r1.view(np.uint32), r2.view(np.uint32))
+
+
+def test_rate_parity_clustered_overflow(lib, orc):
+    """A dense cluster on top of a lattice overfills some tiles' staging buffers; those tiles
+    take the direct walk, and the result still matches the oracle."""
+    rng = np.random.default_rng(4)
+    base = inputs.lattice_positions(2, 96)
+    blob = np.mod(rng.normal(0.5, 0.02, size=(6000, 2)), 1.0)
+    x = np.concatenate([base, blob])
+    n = x.shape[0]
+    box = np.ones(2)
+    xq = inputs.to_fixed(x, box)
+    xo = inputs.from_fixed(xq, box)
+    C = inputs.gaussian_plume(xo, box, (0.45, 0.5), 0.1).astype(np.float32)
+    plume = _plume(side=96, h_dx=2.0)
+    p = lib.params(2, plume.h, plume.alpha_L, plume.alpha_T, plume.D_m, plume.velocity, mass=1.0 / n,
+                   flags=lib.FLAG_TILED)
+    sim = lib.Simulation(p, xq, C)
+    assert sim.info.variant == 1
+    r_orc, pairs = orc.rate(xo, plume.velocity, C.astype(np.float64), 1.0 / n, 1.0, box, 0,
+                            plume.support, 4.0, plume.alpha_L, plume.alpha_T, plume.D_m)
+    assert _rel(sim.rate().cpu().numpy(), r_orc) <= RATE_TOL
     assert sim.count_pairs() == pairs
 
 
@@ -136,12 +174,13 @@ def test_rate_parity_nonsquare_box(lib, orc):
     assert sim.count_pairs() == pairs
 
 
+@pytest.mark.parametrize("variant", sorted(VARIANTS))
 @pytest.mark.parametrize("name", ["64sq-h1.3", "256sq-n28-r100", "3d-32cube-h2", "jitter-100sq"])
-def test_one_step_parity(lib, orc, name):
+def test_one_step_parity(lib, orc, name, variant):
     """Eq. 8-9: the increment C^{l+1} - C^l and the drift after one step."""
     plume = CASES[name]()
     xq, C = plume.initial_state()
-    sim = _sim(lib, plume)
+    sim = _sim(lib, plume, flags=VARIANTS[variant])
     dt = sim.info.dt
     sim.step(1)
     xq1, C1 = sim.state()
