@@ -161,6 +161,28 @@ int ade_get_stats(ade_ctx *ctx, ade_stats *stats_host, void *stream);
 int ade_closed_form_error(ade_ctx *ctx, const double *x0_host, double w, double C0,
                           int nimg, double *out_host, void *stream);
 
+/* Cell build that allocates nothing (no counterpart in the paper: it is a service for callers).
+ * Some callers cannot call cudaMalloc or give the library a workspace -- plug-ins handed only
+ * their input and output buffers, code whose device memory belongs to another allocator, loops
+ * that cannot accept cudaMalloc's implicit synchronisation.  This call performs the same work as
+ * ade_build_cells (cell keys, one-digit counting sort, per-cell order by caller index, sorted
+ * copy), with its scratch in one static device array of the library (about 16 MiB, reserved on
+ * every GPU that loads the library until the process exits).
+ *   dim 2 or 3; n particles (0 <= n <= ADE_NOALLOC_MAX_PARTICLES); xq_dev [dim][n] fixed-point
+ *   positions and C_dev [n] (inputs); nc_host [dim] cells per axis, product <= ADE_NOALLOC_MAX_CELLS.
+ *   Outputs: perm_dev [n] caller index at each sorted position, cell_start_dev [ncells + 1],
+ *   sorted_dev [n] 16-byte records {x, y, z (0 in 2D), C bits} in sorted order.
+ * Larger sizes return ADE_ERR_CAPACITY without touching the GPU.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the array and it keeps the last call's
+ * contents (the per-cell counters are cleared by every call): calls that overlap on the GPU race,
+ * so order them on one stream.  Work is enqueued on `stream`; the call does not wait. */
+#define ADE_NOALLOC_MAX_PARTICLES 1048576
+#define ADE_NOALLOC_MAX_CELLS 1048576
+int ade_build_cells_noalloc(int dim, int n, const uint32_t *xq_dev, const float *C_dev,
+                            const int *nc_host, uint32_t *perm_dev, uint32_t *cell_start_dev,
+                            void *sorted_dev, void *stream);
+
 /* Release the context (not the caller's buffers). */
 void ade_destroy(ade_ctx *ctx);
 

@@ -31,7 +31,9 @@ DT_TRACE = 1
 EXPORTS = ("ade_workspace_bytes", "ade_init_particles", "ade_get_info", "ade_build_cells",
            "ade_get_cells", "ade_dispersion_rate", "ade_count_pairs", "ade_step", "ade_run",
            "ade_get_stats", "ade_closed_form_error", "ade_destroy", "ade_last_error",
-           "ade_step_timed", "ade_launches_per_step")
+           "ade_step_timed", "ade_launches_per_step", "ade_build_cells_noalloc")
+NOALLOC_MAX_PARTICLES = 1 << 20
+NOALLOC_MAX_CELLS = 1 << 20
 
 
 class AdeError(RuntimeError):
@@ -94,6 +96,7 @@ def load():
                                       ctypes.c_double, I, ctypes.POINTER(ctypes.c_double), V]),
         "ade_step_timed": (I, [P, ctypes.POINTER(ctypes.c_double), V]),
         "ade_launches_per_step": (I, [P, ctypes.POINTER(I)]),
+        "ade_build_cells_noalloc": (I, [I, I, P, P, ctypes.POINTER(I), P, P, P, V]),
         "ade_destroy": (None, [P]),
         "ade_last_error": (ctypes.c_char_p, []),
     }
@@ -209,6 +212,14 @@ def closed_form_error(ctx, x0, w, C0=1.0, nimg=2, stream=None):
     out = (ctypes.c_double * 4)()
     _check(load().ade_closed_form_error(ctx, x, w, C0, nimg, out, stream))
     return {"l2": out[0], "linf": out[1], "rmse": out[2], "c_an_max": out[3]}
+
+
+def build_cells_noalloc(dim, n, xq_ptr, C_ptr, nc, perm_ptr, cell_start_ptr, sorted_ptr,
+                        stream=None):
+    """Cell build with the library's static scratch (no allocation); see include/ade_sph.h."""
+    ncv = (ctypes.c_int * 3)(*([int(c) for c in nc[:dim]] + [1] * (3 - dim)))
+    _check(load().ade_build_cells_noalloc(dim, n, xq_ptr, C_ptr, ncv, perm_ptr, cell_start_ptr,
+                                          sorted_ptr, stream))
 
 
 def destroy(ctx):

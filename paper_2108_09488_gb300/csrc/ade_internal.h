@@ -13,6 +13,7 @@ constexpr int kMaxRows = (2 * kMaxSubdiv + 1) * (2 * kMaxSubdiv + 1);
 constexpr int kRateThreads = 128;                              // direct variant
 constexpr int kTileThreads = 256;                              // tiled variant
 constexpr int kMaxCellBits = 24;                                // ncells <= 2^24
+constexpr int kScanTileCells = 2048;                            // cells per scan block (cells.cu)
 
 // One row of the neighbour-cell stencil: cells (cx - w .. cx + w, cy + dy, cz + dz).
 struct StencilRow {
@@ -77,6 +78,9 @@ struct Work {
     unsigned *done;        // last-block counter of the corrector
     unsigned long long *pairs;
 };
+
+// Records msg as the calling thread's last error (read by ade_last_error) and returns code.
+int report_error(int code, const char *msg);
 
 // Launchers (cells.cu, rate.cu, reduce.cu).  All return cudaGetLastError() of the launches.
 int scan_blocks(int m);

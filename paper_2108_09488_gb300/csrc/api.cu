@@ -385,6 +385,8 @@ T *at(void *base, size_t off)
 
 }  // namespace
 
+int ade::report_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
 extern "C" {
 
 const char *ade_last_error(void) { return g_err; }

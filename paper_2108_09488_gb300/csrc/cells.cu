@@ -52,6 +52,7 @@ __global__ __launch_bounds__(kThreads) void k_count(const uint32_t *__restrict__
 // Three-launch exclusive scan of count[0..m) into start[0..m] (start[m] = total).
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kThreads * kScanItems;   // elements per scan block
+static_assert(kScanTile == kScanTileCells, "scan tile size is shared with the workspace layouts");
 
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total)
 {
