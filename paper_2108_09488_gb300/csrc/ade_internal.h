@@ -36,6 +36,7 @@ struct RateParams {
     float pf;        // 1/2 (m / rho) * kernel prefactor of W'(r)/r
     float dt;        // step length used by the epilogue
     uint32_t inc[3]; // fixed-point position increment used by the epilogue
+    uint32_t back[3];// evaluation position minus cell-build position (0, or the half-step drift)
     int variant;     // 0 = direct walk over global memory, 1 = shared-memory tiles
     int k;           // halo width in cells (cells per support radius)
     int tx, ty, tz;  // target cells per tile

@@ -347,13 +347,19 @@ int enqueue_step(ade_ctx *c, cudaStream_t s)
     ade::EpiOut out = epi_none();
     // predictor: C^{l+1/2} = C^l + dt/2 r^l, x^{l+1/2} = x^l + dt/2 v
     rp.dt = (float)(0.5 * c->dt);
-    for (int i = 0; i < 3; ++i) rp.inc[i] = c->inc_half[i];
+    for (int i = 0; i < 3; ++i) {
+        rp.inc[i] = c->inc_half[i];
+        rp.back[i] = 0u;
+    }
     out.Pout = c->w.P1;
     ADE_CK(ade::launch_rate(c->dim, c->p.kernel, c->iso, ade::EPI_PREDICT, c->w.P0, c->w.P0, c->w.cell_start,
                             perm, rp, out, s));
     // corrector: C^{l+1} = C^l + dt r^{l+1/2}, x^{l+1} = x^l + dt v
     rp.dt = (float)c->dt;
-    for (int i = 0; i < 3; ++i) rp.inc[i] = c->inc[i];
+    for (int i = 0; i < 3; ++i) {
+        rp.inc[i] = c->inc[i];
+        rp.back[i] = c->inc_half[i];
+    }
     out = epi_none();
     out.xq = c->xq;
     out.C = c->C;
@@ -689,13 +695,19 @@ int ade_step_timed(ade_ctx *c, double *phase_ms, void *stream)
         ade::RateParams rp = c->rp;
         ade::EpiOut out = epi_none();
         rp.dt = (float)(0.5 * c->dt);
-        for (int i = 0; i < 3; ++i) rp.inc[i] = c->inc_half[i];
+        for (int i = 0; i < 3; ++i) {
+            rp.inc[i] = c->inc_half[i];
+            rp.back[i] = 0u;
+        }
         out.Pout = c->w.P1;
         ADE_CK(ade::launch_rate(c->dim, c->p.kernel, c->iso, ade::EPI_PREDICT, c->w.P0, c->w.P0,
                                 c->w.cell_start, perm, rp, out, s));
         ADE_CK(cudaEventRecord(c->ev[2], s));
         rp.dt = (float)c->dt;
-        for (int i = 0; i < 3; ++i) rp.inc[i] = c->inc[i];
+        for (int i = 0; i < 3; ++i) {
+            rp.inc[i] = c->inc[i];
+            rp.back[i] = c->inc_half[i];
+        }
         out = epi_none();
         out.xq = c->xq;
         out.C = c->C;

@@ -165,14 +165,17 @@ __device__ float rate_direct(const uint4 *__restrict__ Pe, const uint32_t *__res
 // ---------------------------------------------------------------------------------------------
 // epilogue and block reductions
 // ---------------------------------------------------------------------------------------------
+// Per-thread accumulators of the corrector's reductions: FP64 sum of C, FP32 min and max (exact:
+// the values are FP32), in-support pair count.
 struct Acc {
-    double s, mn, mx;
+    double s;
+    float mn, mx;
     unsigned cnt;
 };
 
-// Writes of one particle at sorted position gi; pe = evaluation state, pc = cell-build state.
+// Writes of one particle at sorted position gi; pe = evaluation state {x, y, z, C}.
 template <int DIM, int EPI>
-__device__ __forceinline__ void epilogue(int gi, float rate, const uint4 &pe, const uint4 &pc,
+__device__ __forceinline__ void epilogue(int gi, float rate, const uint4 &pe,
                                          const uint32_t *__restrict__ perm, const RateParams &prm,
                                          const EpiOut &out, Acc &acc)
 {
@@ -190,33 +193,50 @@ __device__ __forceinline__ void epilogue(int gi, float rate, const uint4 &pe, co
         q.w = __float_as_uint(fmaf(prm.dt, rate, __uint_as_float(pe.w)));
         out.Pout[gi] = q;
     } else {
-        // C^{l+1} = C^l + dt r^{l+1/2}, x^{l+1} = x^l + dt v, back to the caller's order
-        const float Cn = fmaf(prm.dt, rate, __uint_as_float(pc.w));
+        // C^{l+1} = C^l + dt r^{l+1/2}, x^{l+1} = x^l + dt v, in the caller's order.  x^l is the
+        // evaluation position minus the half-step drift (exact in fixed point); C^l is still in
+        // the caller's array, read just before this thread overwrites it.
         const uint32_t a = __ldg(perm + gi);
+        float Cn = 0.f;
         if (a < (uint32_t)prm.n) {
+            Cn = fmaf(prm.dt, rate, out.C[a]);
             out.C[a] = Cn;
-            out.xq[a] = pc.x + prm.inc[0];
-            out.xq[(size_t)prm.n + a] = pc.y + prm.inc[1];
-            if (DIM == 3) out.xq[2 * (size_t)prm.n + a] = pc.z + prm.inc[2];
+            out.xq[a] = pe.x - prm.back[0] + prm.inc[0];
+            out.xq[(size_t)prm.n + a] = pe.y - prm.back[1] + prm.inc[1];
+            if (DIM == 3) out.xq[2 * (size_t)prm.n + a] = pe.z - prm.back[2] + prm.inc[2];
         }
         if (!isfinite(Cn)) atomicOr(out.status, 1);
-        const double d = (double)Cn;
-        acc.s += d;
-        acc.mn = fmin(acc.mn, d);
-        acc.mx = fmax(acc.mx, d);
+        acc.s += (double)Cn;
+        acc.mn = fminf(acc.mn, Cn);
+        acc.mx = fmaxf(acc.mx, Cn);
     }
 }
 
-// Fixed-order reduction of nb partial triples {sum, min, max} by one block of NT threads.
+// Fixed-order reduction of nb partial triples {sum, min, max} by one block of NT threads.  Thread
+// t folds partials t, t + NT, t + 2 NT, ... in that order; the loads are issued 16 at a time so
+// that they are in flight together.
 template <int NT>
 __device__ void reduce_partials_last_block(const double *partials, int nb, double *stats)
 {
     __shared__ double sh[3][NT];
+    constexpr int U = 16;
     double a = 0.0, b = dinf(), c = -dinf();
-    for (int k = threadIdx.x; k < nb; k += NT) {
-        a += __ldcg(partials + 3 * (size_t)k + 0);
-        b = fmin(b, __ldcg(partials + 3 * (size_t)k + 1));
-        c = fmax(c, __ldcg(partials + 3 * (size_t)k + 2));
+    for (int k0 = threadIdx.x; k0 < nb; k0 += U * NT) {
+        double va[U], vb[U], vc[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = k0 + u * NT;
+            const bool ok = k < nb;
+            va[u] = ok ? __ldcg(partials + 3 * (size_t)k + 0) : 0.0;
+            vb[u] = ok ? __ldcg(partials + 3 * (size_t)k + 1) : dinf();
+            vc[u] = ok ? __ldcg(partials + 3 * (size_t)k + 2) : -dinf();
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            a += va[u];
+            b = fmin(b, vb[u]);
+            c = fmax(c, vc[u]);
+        }
     }
     sh[0][threadIdx.x] = a;
     sh[1][threadIdx.x] = b;
@@ -248,19 +268,26 @@ __device__ __forceinline__ void block_finish(Acc acc, const EpiOut &out)
         if ((threadIdx.x & 31) == 0 && c) atomicAdd(out.pairs, (unsigned long long)c);
     }
     if (EPI != EPI_CORRECT) return;
-    double s = acc.s, mn = acc.mn, mx = acc.mx;
+    // min and max: FP32 warp shuffles (exact).  Sum: FP64, added serially by one lane per warp in
+    // lane order (FP64 issue is scarce on this part; one lane does 32 adds instead of every lane
+    // doing 5 shuffled adds).
+    float mn = acc.mn, mx = acc.mx;
     for (int o = 16; o > 0; o >>= 1) {
-        s += __shfl_down_sync(0xffffffffu, s, o);
-        mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
-        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        mn = fminf(mn, __shfl_down_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
     }
+    __shared__ double lane_sum[NT];
     __shared__ double red[3][NT / 32];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    lane_sum[threadIdx.x] = acc.s;
+    __syncwarp();
     if (lane == 0) {
+        double s = 0.0;
+        for (int l = 0; l < 32; ++l) s += lane_sum[threadIdx.x + l];
         red[0][wid] = s;
-        red[1][wid] = mn;
-        red[2][wid] = mx;
+        red[1][wid] = (double)mn;
+        red[2][wid] = (double)mx;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -299,16 +326,16 @@ __global__ __launch_bounds__(kRateThreads) void k_rate(const uint4 *__restrict__
     const bool valid = i < prm.n;
     const int ii = valid ? i : prm.n - 1;
     const uint4 pa = __ldg(Pe + ii);
-    const uint4 pc = (Pe == Pc) ? pa : __ldg(Pc + ii);
-    const int cx = (int)__umulhi(pc.x, (uint32_t)prm.ncx);
-    const int cy = (int)__umulhi(pc.y, (uint32_t)prm.ncy);
-    const int cz = DIM == 3 ? (int)__umulhi(pc.z, (uint32_t)prm.ncz) : 0;
-    Acc acc{0.0, dinf(), -dinf(), 0u};
+    // cell of the cell build: evaluation position minus the drift since the build
+    const int cx = (int)__umulhi(pa.x - prm.back[0], (uint32_t)prm.ncx);
+    const int cy = (int)__umulhi(pa.y - prm.back[1], (uint32_t)prm.ncy);
+    const int cz = DIM == 3 ? (int)__umulhi(pa.z - prm.back[2], (uint32_t)prm.ncz) : 0;
+    Acc acc{0.0, __int_as_float(0x7f800000), __int_as_float(0xff800000), 0u};
     unsigned cnt = 0u;
     const float rate = rate_direct<DIM, KERNEL, ISO, COUNT>(Pe, cs, pa, cx, cy, cz, prm, cnt);
     if (valid) {
         acc.cnt = cnt;
-        epilogue<DIM, EPI>(i, rate, pa, pc, perm, prm, out, acc);
+        epilogue<DIM, EPI>(i, rate, pa, perm, prm, out, acc);
     }
     block_finish<EPI, COUNT, kRateThreads>(acc, out);
 }
@@ -445,17 +472,16 @@ __global__ __launch_bounds__(kTileThreads, 2) void k_rate_tiled(const uint4 *__r
     __syncthreads();
 
     // 4. targets: thread t takes targets t, t + NT, ... in (row, sorted) order
-    Acc acc{0.0, dinf(), -dinf(), 0u};
+    Acc acc{0.0, __int_as_float(0x7f800000), __int_as_float(0xff800000), 0u};
     int r = 0;
     for (int t = threadIdx.x; t < ntarget; t += kTileThreads) {
         while (tpre[r + 1] <= t) ++r;
         const int off = t - tpre[r];
         const int gi = tglb[r] + off;
         const uint4 pe = __ldg(Pe + gi);
-        const uint4 pc = (Pe == Pc) ? pe : __ldg(Pc + gi);
-        const int cx = (int)__umulhi(pc.x, (uint32_t)ncx);
-        const int cy = (int)__umulhi(pc.y, (uint32_t)ncy);
-        const int cz = DIM == 3 ? (int)__umulhi(pc.z, (uint32_t)ncz) : 0;
+        const int cx = (int)__umulhi(pe.x - prm.back[0], (uint32_t)ncx);
+        const int cy = (int)__umulhi(pe.y - prm.back[1], (uint32_t)ncy);
+        const int cz = DIM == 3 ? (int)__umulhi(pe.z - prm.back[2], (uint32_t)ncz) : 0;
         float rate;
         unsigned cnt = 0u;
         if (staged) {
@@ -489,7 +515,7 @@ __global__ __launch_bounds__(kTileThreads, 2) void k_rate_tiled(const uint4 *__r
             rate = rate_direct<DIM, KERNEL, true, COUNT>(Pe, cs, pe, cx, cy, cz, prm, cnt);
         }
         acc.cnt += cnt;
-        epilogue<DIM, EPI>(gi, rate, pe, pc, perm, prm, out, acc);
+        epilogue<DIM, EPI>(gi, rate, pe, perm, prm, out, acc);
     }
     block_finish<EPI, COUNT, kTileThreads>(acc, out);
 }
