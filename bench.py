@@ -39,6 +39,7 @@ WORKLOADS = {
     "ladder-256-n28-r10": lambda: inputs.ladder_2d(256, 10),
     "lattice-64-h1.3": inputs.lattice_2d_64,
     "cube-128-h2": inputs.cube_3d_128,
+    "batched-64": None,          # 64 uneven 2D plumes in one batch (inputs.batched_2d)
 }
 DEFAULT_WORKLOAD = "ladder-1024-n120-r10"
 METRIC = "particle-pair interactions/s"
@@ -165,9 +166,58 @@ def cpu_oracle_rate(plume, xq, C, sample, min_seconds, max_steps=None):
     return pairs / el, steps, el, int(sel.size)
 
 
+def cpu_oracle_batch(plumes, states, per_plume, min_seconds, max_steps=None):
+    """Oracle timing for a batch: Eq. 4 twice per step on a fixed sample of each plume."""
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(12345)
+    prepared = []
+    for p, (xq, C) in zip(plumes, states):
+        sel = np.sort(rng.choice(p.n, min(per_plume, p.n), replace=False))
+        args = (p.velocity, np.asarray(C, dtype=np.float64), p.mass, p.rho, p.boxv, p.kernel,
+                p.support, p.dim + 2.0, p.alpha_L, p.alpha_T, p.D_m)
+        prepared.append((sel, inputs.from_fixed(xq, p.boxv), args))
+    pairs = steps = 0
+    t0 = time.perf_counter()
+    while True:
+        for sel, x, args in prepared:
+            for _ in range(2):
+                pairs += oracle.rate_at(sel, x, *args)[1]
+        steps += 1
+        el = time.perf_counter() - t0
+        if (max_steps is not None and steps >= max_steps) or (max_steps is None and el >= min_seconds):
+            break
+    return pairs / el, steps, el, sum(int(p[0].size) for p in prepared)
+
+
+def batched_config(plumes):
+    return {"workload": "batched-2d-64-plumes-seed20210821", "plumes": len(plumes),
+            "particles": int(sum(p.n for p in plumes)), "dim": 2, "kernel": "wendland-c2",
+            "side_range": [min(p.side for p in plumes), max(p.side for p in plumes)],
+            "l2": "flushed (256 MiB write) before every timed step"}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
+        return 0
+    if args.workload == "batched-64":
+        plumes = inputs.batched_2d()
+        states = [p.initial_state() for p in plumes]
+        cpu_oracle_batch(plumes, states, args.cpu_sample // 64, 0.0, max_steps=args.warmup)
+        value, steps, secs, ns = cpu_oracle_batch(plumes, states, args.cpu_sample // 64, 0.0,
+                                                  max_steps=args.steps)
+        line = {
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": batched_config(plumes),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"Eq. 4 evaluated twice per step on {ns} particles sampled "
+                                       f"across the 64 plumes"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line))
         return 0
     plume = WORKLOADS[args.workload]()
     xq, C = plume.initial_state()
@@ -196,12 +246,141 @@ def workload_config(plume):
             "l2": "flushed (256 MiB write) before every timed step"}
 
 
+def run_batched(args):
+    """64 uneven plumes in one batch (autotuned, graph replay) against one context per plume."""
+    import torch
+
+    from paper_2108_09488_gb300 import ade
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = Dist(world, True)
+    plumes = inputs.batched_2d()
+    states = [p.initial_state() for p in plumes]
+    plist = [ade.params_for(p) for p in plumes]
+    b = ade.Batch(plist, [s[0] for s in states], [s[1] for s in states], device=device)
+    pairs = b.count_pairs()
+    tune_ms = b.autotune()
+    info0 = b.plume_info(0)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+    for _ in range(args.warmup):
+        flush.zero_()
+        b.step_timed()
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    phases = []
+    for _ in range(args.steps):
+        flush.zero_()
+        phases.append(b.step_timed())
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    total_ms = dist.max(sum(sum(p) for p in phases), device)
+    value = world * 2.0 * pairs * args.steps / (total_ms * 1e-3)
+
+    # the same plumes as 64 separate contexts (same cell subdivision), one graph launch each
+    sims = [ade.Simulation(ade.params_for(p, cell_subdiv=b.plume_info(i).cell_subdiv,
+                                          flags=ade.FLAG_DIRECT), *states[i], device=device)
+            for i, p in enumerate(plumes)]
+    stream = torch.cuda.current_stream(device)
+    for _ in range(args.warmup):
+        flush.zero_()
+        for sm in sims:
+            sm.run(1, stats=False)
+    torch.cuda.synchronize()
+    pp_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for sm in sims:
+            sm.run(1, stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pp_ms += e0.elapsed_time(e1)
+    pp_value = 2.0 * pairs * args.steps / (pp_ms * 1e-3)
+    for sm in sims:
+        sm.close()
+
+    rate_ms = [p[1] for p in phases] + [p[2] for p in phases]
+    rate_avg_ms = sum(rate_ms) / len(rate_ms)
+    props = torch.cuda.get_device_properties(device)
+    f_max = clk.get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * f_max * 1e6 / I_MIN[2] / 1e9
+    achieved = pairs / (rate_avg_ms * 1e-3) / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_rate_batch (predictor + corrector)",
+                "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                              f"{f_max:.0f} MHz / {I_MIN[2]} FP32-pipe instructions per pair",
+                "rate_kernel_ms": rate_avg_ms,
+                "phase_ms_per_step": {k: sum(p[i] for p in phases) / len(phases)
+                                      for i, k in enumerate(("cells", "predictor", "corrector"))}}
+
+    # end to end: H2D of every plume's x and C, one graph-replayed step, D2H of C
+    xq_pin = b.xq.cpu().pin_memory()
+    C_pin = b.C.cpu().pin_memory()
+    C_out = torch.empty_like(C_pin).pin_memory()
+    for _ in range(args.warmup):
+        b.xq.copy_(xq_pin, non_blocking=True)
+        b.C.copy_(C_pin, non_blocking=True)
+        b.run(1)
+        C_out.copy_(b.C, non_blocking=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        b.xq.copy_(xq_pin, non_blocking=True)
+        b.C.copy_(C_pin, non_blocking=True)
+        b.run(1)
+        C_out.copy_(b.C, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = dist.max(e0.elapsed_time(e1), device)
+    e2e = {"value": world * 2.0 * pairs * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": int(xq_pin.numel() * 4 + C_pin.numel() * 4),
+           "d2h_bytes_per_step": int(C_out.numel() * 4), "ms_per_step": e2e_ms / args.steps,
+           "path": "ade_batch_run (graph replay) via ctypes"}
+    ms_per_step = total_ms / args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": batched_config(plumes),
+        "batch": {"autotune_best_ms": tune_ms, "work_item_particles": info0.tile[0],
+                  "persistent_grid": info0.tile[1], "work_items": info0.tile[2],
+                  "cell_subdiv": [b.plume_info(i).cell_subdiv for i in range(len(plumes))]},
+        "per_plume_launches": {"value": pp_value, "ms_per_step": pp_ms / args.steps,
+                               "launches_per_step": 8 * len(plumes),
+                               "batched_speedup": value / pp_value},
+        "steps_per_s": 1e3 / ms_per_step * world, "interactions_per_step": 2 * pairs,
+        "roofline": roofline, "e2e": e2e, "clocks": clk,
+        "gpu_launches": b.launches_per_step() * args.steps,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, steps, secs, ns = cpu_oracle_batch(plumes, states, args.cpu_sample // 64, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"Eq. 4 evaluated twice per step on {ns} particles sampled "
+                                          f"across the 64 plumes; {steps} steps in {secs:.1f} s"}
+    b.close()
+    if rank == 0:
+        print(json.dumps(line))
+    dist.close()
+    return 0
+
+
 def run_ours(args):
     import torch
 
     from paper_2108_09488_gb300 import ade
 
     world, rank, local = dist_env()
+    if args.workload == "batched-64":
+        return run_batched(args)
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
     torch.cuda.set_device(local)

@@ -161,6 +161,59 @@ int ade_get_stats(ade_ctx *ctx, ade_stats *stats_host, void *stream);
 int ade_closed_form_error(ade_ctx *ctx, const double *x0_host, double w, double C0,
                           int nimg, double *out_host, void *stream);
 
+/* ---- Batched plumes -------------------------------------------------------------------------
+ * Many independent plumes (the convergence ladder and dispersivity sweep of Sec. 3-4 run side by
+ * side) stepped together: one cell build over all plumes (global cell keys offset per plume) and
+ * two persistent rate launches per step that take (plume, particle range) work items from an
+ * atomic counter, largest estimated cost first.  Each particle is evaluated by the same code as in
+ * a single-plume context, so a plume's results are bit-identical to ade_step on a context with the
+ * same parameters and cell subdivision (ade_batch_get_plume_info reports it).
+ * Layout: plume p owns caller particles [off_p, off_p + n_p), off_p = n_0 + ... + n_{p-1};
+ * xq_dev holds the plumes' [dim][n_p] position blocks back to back (plume p's block starts at
+ * element dim * off_p) and C_dev the concentrations back to back.  All plumes share dim, kernel and
+ * a cubic box side per plume; each has its own h, dispersivities, velocity and time step. */
+typedef struct ade_batch ade_batch;
+
+/* Workspace for a batch (bytes, 256-byte aligned); sized for every cell subdivision the autotuner
+ * may choose. */
+int ade_batch_workspace_bytes(int nplumes, const ade_params *p, const int *n, size_t *bytes);
+
+/* Create a batch bound to the caller's state and workspace; uploads the per-plume constants and
+ * the work list on `stream` and waits for that upload. */
+int ade_batch_init(ade_batch **out, int nplumes, const ade_params *p, const int *n, uint32_t *xq_dev,
+                   float *C_dev, void *workspace_dev, size_t workspace_bytes, void *stream);
+
+/* nsteps predictor-corrector steps (Eq. 8-9) of every plume, each with its own time step. */
+int ade_batch_step(ade_batch *b, int nsteps, void *stream);
+
+/* As ade_batch_step, replaying one captured CUDA graph per step; only enqueues. */
+int ade_batch_run(ade_batch *b, int nsteps, void *stream);
+
+/* FP64 per-plume mass, min and max (stats_host[nplumes]); waits for the stream. */
+int ade_batch_stats(ade_batch *b, ade_stats *stats_host, void *stream);
+
+/* Total ordered in-support pairs over all plumes (support decided in FP64); waits. */
+int ade_batch_count_pairs(ade_batch *b, long long *pairs_host, void *stream);
+
+/* Per-plume configuration: support, dt, D, grid and cell subdivision in use; tile[0..2] report the
+ * batch's work-item size, persistent grid size and number of work items. */
+int ade_batch_get_plume_info(const ade_batch *b, int plume, ade_info *info_host);
+
+/* Autotuner: times the cell build plus one evaluation of every plume for each cell-subdivision
+ * policy (per-plume cost model, or 1..4 cells per support radius), work-item size (64..512
+ * particles) and persistent grid size (4, 8, 16 blocks per SM), keeps the fastest and re-plans.
+ * Leaves the particle state unchanged; waits; best_ms_host (may be NULL) gets the best time. */
+int ade_batch_autotune(ade_batch *b, double *best_ms_host, void *stream);
+
+/* One batched step bracketed by CUDA events; waits; phase_ms_host[4] = {cell build, predictor,
+ * corrector, 0} in milliseconds. */
+int ade_batch_step_timed(ade_batch *b, double *phase_ms_host, void *stream);
+
+/* Kernel launches one batched step enqueues. */
+int ade_batch_launches_per_step(const ade_batch *b, int *launches);
+
+void ade_batch_destroy(ade_batch *b);
+
 /* Cell build that allocates nothing (no counterpart in the paper: it is a service for callers).
  * Some callers cannot call cudaMalloc or give the library a workspace -- plug-ins handed only
  * their input and output buffers, code whose device memory belongs to another allocator, loops

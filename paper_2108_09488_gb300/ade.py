@@ -31,7 +31,11 @@ DT_TRACE = 1
 EXPORTS = ("ade_workspace_bytes", "ade_init_particles", "ade_get_info", "ade_build_cells",
            "ade_get_cells", "ade_dispersion_rate", "ade_count_pairs", "ade_step", "ade_run",
            "ade_get_stats", "ade_closed_form_error", "ade_destroy", "ade_last_error",
-           "ade_step_timed", "ade_launches_per_step", "ade_build_cells_noalloc")
+           "ade_step_timed", "ade_launches_per_step", "ade_build_cells_noalloc",
+           "ade_batch_workspace_bytes", "ade_batch_init", "ade_batch_step", "ade_batch_run",
+           "ade_batch_stats", "ade_batch_count_pairs", "ade_batch_get_plume_info",
+           "ade_batch_autotune", "ade_batch_launches_per_step", "ade_batch_destroy",
+           "ade_batch_step_timed")
 NOALLOC_MAX_PARTICLES = 1 << 20
 NOALLOC_MAX_CELLS = 1 << 20
 
@@ -97,6 +101,17 @@ def load():
         "ade_step_timed": (I, [P, ctypes.POINTER(ctypes.c_double), V]),
         "ade_launches_per_step": (I, [P, ctypes.POINTER(I)]),
         "ade_build_cells_noalloc": (I, [I, I, P, P, ctypes.POINTER(I), P, P, P, V]),
+        "ade_batch_workspace_bytes": (I, [I, P, P, ctypes.POINTER(SZ)]),
+        "ade_batch_init": (I, [ctypes.POINTER(P), I, P, P, P, P, P, SZ, V]),
+        "ade_batch_step": (I, [P, I, V]),
+        "ade_batch_run": (I, [P, I, V]),
+        "ade_batch_stats": (I, [P, P, V]),
+        "ade_batch_count_pairs": (I, [P, ctypes.POINTER(LL), V]),
+        "ade_batch_get_plume_info": (I, [P, I, ctypes.POINTER(Info)]),
+        "ade_batch_autotune": (I, [P, ctypes.POINTER(ctypes.c_double), V]),
+        "ade_batch_launches_per_step": (I, [P, ctypes.POINTER(I)]),
+        "ade_batch_step_timed": (I, [P, ctypes.POINTER(ctypes.c_double), V]),
+        "ade_batch_destroy": (None, [P]),
         "ade_destroy": (None, [P]),
         "ade_last_error": (ctypes.c_char_p, []),
     }
@@ -297,6 +312,110 @@ class Simulation:
     def close(self):
         if self.ctx:
             destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- batched plumes ---------------------------------------------------------------------------
+def _params_array(plist):
+    arr = (Params * len(plist))()
+    for i, p in enumerate(plist):
+        arr[i] = p
+    return arr
+
+
+def batch_workspace_bytes(plist, ns):
+    arr = _params_array(plist)
+    nn = (ctypes.c_int * len(ns))(*[int(v) for v in ns])
+    out = ctypes.c_size_t(0)
+    _check(load().ade_batch_workspace_bytes(len(plist), arr, nn, ctypes.byref(out)))
+    return out.value
+
+
+class Batch:
+    """Many plumes stepped together through the ade_batch_* entry points.
+
+    ``xq_list[p]`` (uint32 [dim][n_p]) and ``C_list[p]`` (float32 [n_p]) are copied into one
+    concatenated device state (plume p's position block starts at element dim * off_p)."""
+
+    def __init__(self, plist, xq_list, C_list, device="cuda", stream=None):
+        import torch
+        self.torch = torch
+        self.P = len(plist)
+        self.dim = plist[0].dim
+        self.ns = [int(np.asarray(x).shape[1]) for x in xq_list]
+        self.offsets = np.concatenate([[0], np.cumsum(self.ns)]).astype(np.int64)
+        xq = np.concatenate([np.ascontiguousarray(x, dtype=np.uint32).ravel() for x in xq_list])
+        C = np.concatenate([np.asarray(c, dtype=np.float32).ravel() for c in C_list])
+        self.xq = torch.from_numpy(xq.view(np.int32)).to(device).contiguous()
+        self.C = torch.from_numpy(C).to(device).contiguous()
+        self._params = _params_array(plist)
+        self._n = (ctypes.c_int * self.P)(*self.ns)
+        nbytes = batch_workspace_bytes(plist, self.ns)
+        self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        self.ws_ptr = (self.ws.data_ptr() + 255) // 256 * 256
+        self.ctx = ctypes.c_void_p()
+        _check(load().ade_batch_init(ctypes.byref(self.ctx), self.P, self._params, self._n,
+                                     self.xq.data_ptr(), self.C.data_ptr(), self.ws_ptr, nbytes,
+                                     self.stream))
+
+    @property
+    def stream(self):
+        return ctypes.c_void_p(self.torch.cuda.current_stream().cuda_stream)
+
+    def step(self, nsteps=1):
+        _check(load().ade_batch_step(self.ctx, nsteps, self.stream))
+
+    def run(self, nsteps):
+        _check(load().ade_batch_run(self.ctx, nsteps, self.stream))
+
+    def stats(self):
+        st = (Stats * self.P)()
+        rc = load().ade_batch_stats(self.ctx, st, self.stream)
+        if rc not in (ADE_OK, -3):
+            _check(rc)
+        return list(st)
+
+    def count_pairs(self):
+        v = ctypes.c_longlong(0)
+        _check(load().ade_batch_count_pairs(self.ctx, ctypes.byref(v), self.stream))
+        return v.value
+
+    def plume_info(self, p):
+        info = Info()
+        _check(load().ade_batch_get_plume_info(self.ctx, p, ctypes.byref(info)))
+        return info
+
+    def autotune(self):
+        ms = ctypes.c_double(0.0)
+        _check(load().ade_batch_autotune(self.ctx, ctypes.byref(ms), self.stream))
+        return ms.value
+
+    def launches_per_step(self):
+        v = ctypes.c_int(0)
+        _check(load().ade_batch_launches_per_step(self.ctx, ctypes.byref(v)))
+        return v.value
+
+    def step_timed(self):
+        out = (ctypes.c_double * 4)()
+        _check(load().ade_batch_step_timed(self.ctx, out, self.stream))
+        return list(out)
+
+    def state(self, p):
+        """(xq uint32 [dim][n_p], C float32 [n_p]) of plume p, copied to the host."""
+        self.torch.cuda.synchronize()
+        lo, hi = int(self.offsets[p]), int(self.offsets[p + 1])
+        xq = self.xq[self.dim * lo:self.dim * hi].cpu().numpy().view(np.uint32).reshape(self.dim, hi - lo)
+        return xq, self.C[lo:hi].cpu().numpy()
+
+    def close(self):
+        if self.ctx:
+            load().ade_batch_destroy(self.ctx)
             self.ctx = None
 
     def __del__(self):

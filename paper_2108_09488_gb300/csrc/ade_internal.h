@@ -44,6 +44,14 @@ struct RateParams {
     int cap;         // staged-particle capacity of a tile
     double u[3];     // FP64 length of one fixed-point unit per axis (L_i / 2^32)
     double H2d;      // FP64 support radius squared (pair counting decides support in FP64)
+    int goff;        // batched plumes: first particle (caller and sorted order) of this plume
+    int coff;        // batched plumes: first cell of this plume in the global cell table
+};
+
+// One work item of the batched rate kernel: `count` sorted particles of plume `plume` starting
+// at plume-local sorted index `start`.
+struct BatchTile {
+    int plume, start, count, pad;
 };
 
 // Outputs of the fused epilogues.
@@ -87,6 +95,15 @@ int report_error(int code, const char *msg);
 int scan_blocks(int m);
 cudaError_t launch_build_cells(int dim, const uint32_t *xq, const float *C, int n, const int *nc,
                                int ncells, const Work &w, cudaStream_t s);
+// Batched plumes: keys are coff_p + local key; plume_of[i] gives the plume of caller particle i.
+cudaError_t launch_build_cells_batch(int dim, const uint32_t *xq, const float *C, int n, int ncells,
+                                     const RateParams *descs, const uint16_t *plume_of,
+                                     const Work &w, cudaStream_t s);
+cudaError_t launch_rate_batch(int dim, int kernel, int epi, const uint4 *Pe, const uint32_t *cell_start,
+                              const uint32_t *perm, const RateParams *descs, const BatchTile *tiles,
+                              int ntiles, unsigned *queue, int grid, const EpiOut &out, cudaStream_t s);
+cudaError_t launch_batch_stats(const float *C, const int *offsets, int nplumes, double *stats,
+                               cudaStream_t s);
 cudaError_t launch_rate(int dim, int kernel, bool iso, int epi, const uint4 *Pe, const uint4 *Pc,
                         const uint32_t *cell_start, const uint32_t *perm, const RateParams &prm,
                         const EpiOut &out, cudaStream_t s);

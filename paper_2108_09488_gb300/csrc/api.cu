@@ -383,6 +383,89 @@ int clear_status_once(ade_ctx *c, cudaStream_t s)
     return ADE_OK;
 }
 
+// Per-plume constants: Eq. 3 (D), the time step (Eq. 10 or the largest-eigenvalue rule), the
+// fixed-point drift per step and half step, and the interaction constants of Eq. 4-5 / Eq. 7 in
+// fixed-point units of the x axis.
+int plume_constants(const ade_params *p, int n, const Derived &d, double *D, double *dt_out,
+                    uint32_t *inc, uint32_t *inc_half, ade::RateParams *rp_out, bool *iso)
+{
+    // Eq. 3 and the time step
+    dispersion_tensor(p->dim, p->v, p->alpha_L, p->alpha_T, p->D_m, D);
+    double dt = p->dt;
+    if (!(dt > 0.0)) {
+        double coef = p->dt_coef > 0.0 ? p->dt_coef : 0.1;
+        double den;
+        if (p->dt_rule == ADE_DT_TRACE) {
+            den = 0.0;
+            for (int i = 0; i < p->dim; ++i) den += D[i * p->dim + i];
+        } else {
+            den = lambda_max(p->dim, D);
+        }
+        if (!(den > 0.0)) return fail(ADE_ERR_ARG, "dispersion tensor is zero: give dt explicitly");
+        dt = coef * p->h * p->h / den;
+    }
+    *dt_out = dt;
+    for (int i = 0; i < 3; ++i) {
+        double L = i < p->dim ? p->box[i] : 1.0;
+        double vi = i < p->dim ? p->v[i] : 0.0;
+        inc[i] = fixed_increment(vi, dt, L);
+        inc_half[i] = fixed_increment(vi, 0.5 * dt, L);
+    }
+
+    // Rate constants, lengths in fixed-point units of the x axis.
+    ade::RateParams &rp = *rp_out;
+    memset(&rp, 0, sizeof(rp));
+    rp.n = n;
+    rp.ncx = d.g.nc[0];
+    rp.ncy = d.g.nc[1];
+    rp.ncz = d.g.nc[2];
+    rp.nrows = d.g.nrows;
+    for (int r = 0; r < d.g.nrows; ++r) rp.rows[r] = d.g.rows[r];
+    const double u = p->box[0] / kTwo32;
+    const double Hu = d.H / u;
+    rp.H2 = (float)(Hu * Hu);
+    for (int i = 0; i < 3; ++i) rp.u[i] = (i < p->dim ? p->box[i] : 1.0) / kTwo32;
+    rp.H2d = d.H * d.H;
+    rp.invH = (float)(1.0 / Hu);
+    rp.sy = (float)(p->box[1] / p->box[0]);
+    rp.sz = p->dim == 3 ? (float)(p->box[2] / p->box[0]) : 1.0f;
+    *iso = p->box[1] == p->box[0] && (p->dim == 2 || p->box[2] == p->box[0]);
+    const double gamma = p->gamma > 0.0 ? p->gamma : p->dim + 2.0;
+    const int dm = p->dim;
+    auto K = [&](int i, int j) { return 2.0 * D[i * dm + j]; };  // harmonic mean of equal D
+    // Gamma x^T K x / r^2 - tr K = x^T Gamma (K - K_last I) x / r^2 + (Gamma K_last - tr K)
+    const double Klast = K(dm - 1, dm - 1);
+    double trK = 0.0;
+    for (int i = 0; i < dm; ++i) trK += K(i, i);
+    rp.Kc[0] = (float)(gamma * (K(0, 0) - Klast));
+    rp.Kc[1] = dm == 3 ? (float)(gamma * (K(1, 1) - Klast)) : 0.0f;
+    rp.Kc[2] = 0.0f;
+    rp.Kc[3] = (float)(2.0 * gamma * K(0, 1));
+    rp.Kc[4] = dm == 3 ? (float)(2.0 * gamma * K(0, 2)) : 0.0f;
+    rp.Kc[5] = dm == 3 ? (float)(2.0 * gamma * K(1, 2)) : 0.0f;
+    rp.c0 = (float)(gamma * Klast - trK);
+    const double H = d.H;
+    double B, kc;
+    if (p->kernel == ADE_WENDLAND_C2) {
+        B = dm == 2 ? 7.0 / (kPi * H * H) : 21.0 / (2.0 * kPi * H * H * H);
+        kc = -20.0 * B / (H * H);
+    } else {
+        B = dm == 2 ? 9.0 / (kPi * H * H) : 495.0 / (32.0 * kPi * H * H * H);
+        kc = -(56.0 / 3.0) * B / (H * H);
+    }
+    rp.pf = (float)(0.5 * (p->mass / p->rho) * kc);
+    rp.variant = d.tiles.variant;
+    rp.k = d.tiles.k;
+    rp.tx = d.tiles.tx;
+    rp.ty = d.tiles.ty;
+    rp.tz = d.tiles.tz;
+    rp.ntx = d.tiles.ntx;
+    rp.nty = d.tiles.nty;
+    rp.ntz = d.tiles.ntz;
+    rp.cap = d.tiles.cap;
+    return ADE_OK;
+}
+
 template <typename T>
 T *at(void *base, size_t off)
 {
@@ -451,83 +534,11 @@ int ade_init_particles(ade_ctx **out, const ade_params *p, int n, uint32_t *xq_d
     c->w.done = at<unsigned>(workspace_dev, d.L.done);
     c->w.pairs = at<unsigned long long>(workspace_dev, d.L.pairs);
 
-    // Eq. 3 and the time step
-    dispersion_tensor(p->dim, p->v, p->alpha_L, p->alpha_T, p->D_m, c->D);
-    double dt = p->dt;
-    if (!(dt > 0.0)) {
-        double coef = p->dt_coef > 0.0 ? p->dt_coef : 0.1;
-        double den;
-        if (p->dt_rule == ADE_DT_TRACE) {
-            den = 0.0;
-            for (int i = 0; i < p->dim; ++i) den += c->D[i * p->dim + i];
-        } else {
-            den = lambda_max(p->dim, c->D);
-        }
-        if (!(den > 0.0)) {
-            delete c;
-            return fail(ADE_ERR_ARG, "dispersion tensor is zero: give dt explicitly");
-        }
-        dt = coef * p->h * p->h / den;
+    rc = plume_constants(p, n, d, c->D, &c->dt, c->inc, c->inc_half, &c->rp, &c->iso);
+    if (rc) {
+        delete c;
+        return rc;
     }
-    c->dt = dt;
-    for (int i = 0; i < 3; ++i) {
-        double L = i < p->dim ? p->box[i] : 1.0;
-        double vi = i < p->dim ? p->v[i] : 0.0;
-        c->inc[i] = fixed_increment(vi, dt, L);
-        c->inc_half[i] = fixed_increment(vi, 0.5 * dt, L);
-    }
-
-    // Rate constants, lengths in fixed-point units of the x axis.
-    ade::RateParams &rp = c->rp;
-    memset(&rp, 0, sizeof(rp));
-    rp.n = n;
-    rp.ncx = d.g.nc[0];
-    rp.ncy = d.g.nc[1];
-    rp.ncz = d.g.nc[2];
-    rp.nrows = d.g.nrows;
-    for (int r = 0; r < d.g.nrows; ++r) rp.rows[r] = d.g.rows[r];
-    const double u = p->box[0] / kTwo32;
-    const double Hu = d.H / u;
-    rp.H2 = (float)(Hu * Hu);
-    for (int i = 0; i < 3; ++i) rp.u[i] = (i < p->dim ? p->box[i] : 1.0) / kTwo32;
-    rp.H2d = d.H * d.H;
-    rp.invH = (float)(1.0 / Hu);
-    rp.sy = (float)(p->box[1] / p->box[0]);
-    rp.sz = p->dim == 3 ? (float)(p->box[2] / p->box[0]) : 1.0f;
-    c->iso = p->box[1] == p->box[0] && (p->dim == 2 || p->box[2] == p->box[0]);
-    const double gamma = p->gamma > 0.0 ? p->gamma : p->dim + 2.0;
-    const int dm = p->dim;
-    auto K = [&](int i, int j) { return 2.0 * c->D[i * dm + j]; };  // harmonic mean of equal D
-    // Gamma x^T K x / r^2 - tr K = x^T Gamma (K - K_last I) x / r^2 + (Gamma K_last - tr K)
-    const double Klast = K(dm - 1, dm - 1);
-    double trK = 0.0;
-    for (int i = 0; i < dm; ++i) trK += K(i, i);
-    rp.Kc[0] = (float)(gamma * (K(0, 0) - Klast));
-    rp.Kc[1] = dm == 3 ? (float)(gamma * (K(1, 1) - Klast)) : 0.0f;
-    rp.Kc[2] = 0.0f;
-    rp.Kc[3] = (float)(2.0 * gamma * K(0, 1));
-    rp.Kc[4] = dm == 3 ? (float)(2.0 * gamma * K(0, 2)) : 0.0f;
-    rp.Kc[5] = dm == 3 ? (float)(2.0 * gamma * K(1, 2)) : 0.0f;
-    rp.c0 = (float)(gamma * Klast - trK);
-    const double H = d.H;
-    double B, kc;
-    if (p->kernel == ADE_WENDLAND_C2) {
-        B = dm == 2 ? 7.0 / (kPi * H * H) : 21.0 / (2.0 * kPi * H * H * H);
-        kc = -20.0 * B / (H * H);
-    } else {
-        B = dm == 2 ? 9.0 / (kPi * H * H) : 495.0 / (32.0 * kPi * H * H * H);
-        kc = -(56.0 / 3.0) * B / (H * H);
-    }
-    rp.pf = (float)(0.5 * (p->mass / p->rho) * kc);
-    rp.variant = d.tiles.variant;
-    rp.k = d.tiles.k;
-    rp.tx = d.tiles.tx;
-    rp.ty = d.tiles.ty;
-    rp.tz = d.tiles.tz;
-    rp.ntx = d.tiles.ntx;
-    rp.nty = d.tiles.nty;
-    rp.ntz = d.tiles.ntz;
-    rp.cap = d.tiles.cap;
     *out = c;
     return ADE_OK;
 }
@@ -798,6 +809,592 @@ void ade_destroy(ade_ctx *c)
     if (c->ev_ready)
         for (int k = 0; k < 5; ++k) cudaEventDestroy(c->ev[k]);
     delete c;
+}
+
+}  // extern "C"
+
+// =============================================================================================
+// Batched plumes: many independent plumes stepped together (one cell build, two persistent rate
+// launches per step for the whole batch).
+// =============================================================================================
+#include <algorithm>
+#include <vector>
+
+struct ade_batch {
+    int P = 0, dim = 0, kernel = 0, N = 0;
+    std::vector<ade_params> params;
+    std::vector<int> n, offsets;          // caller offsets (offsets[P] = N)
+    std::vector<int> subdiv_choice;       // per-plume cell subdivision in use
+    std::vector<ade::RateParams> pred, corr;  // per-plume constants for the two evaluations
+    std::vector<double> dt, D;            // per-plume time step and tensor (9 each)
+    std::vector<int> ncells;
+    int NC = 0, NC_max = 0;
+    int tile_size = ade::kRateThreads, grid = 0, sms = 0;
+    int subdiv_mode = 0;                  // 0 = per-plume cost model, 1..4 forced where valid
+    std::vector<ade::BatchTile> tiles;
+    uint32_t *xq = nullptr;
+    float *C = nullptr;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    ade::Work w;
+    ade::RateParams *d_pred = nullptr, *d_corr = nullptr;
+    ade::BatchTile *d_tiles = nullptr;
+    unsigned *queue = nullptr;
+    uint16_t *plume_of = nullptr;
+    int *d_offsets = nullptr;
+    double *d_stats = nullptr;
+    int max_tiles = 0;
+    long long step = 0;
+    bool status_cleared = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+};
+
+namespace {
+
+struct BatchLayout {
+    size_t keys, rank, count, block_sums, perm_tmp, perm, cell_start, P0, P1, pred, corr, tiles,
+        queue, plume_of, offsets, stats, status, pairs, total;
+};
+
+BatchLayout batch_layout(int P, int N, int NC_max, int max_tiles)
+{
+    BatchLayout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align256(bytes > 0 ? bytes : 1);
+        return o;
+    };
+    L.keys = take((size_t)N * 4);
+    L.rank = take((size_t)N * 4);
+    L.count = take((size_t)NC_max * 4);
+    L.block_sums = take((size_t)ade::scan_blocks(NC_max) * 4);
+    L.perm_tmp = take((size_t)N * 4);
+    L.perm = take((size_t)N * 4);
+    L.cell_start = take(((size_t)NC_max + 1) * 4);
+    L.P0 = take((size_t)N * 16);
+    L.P1 = take((size_t)N * 16);
+    L.pred = take((size_t)P * sizeof(ade::RateParams));
+    L.corr = take((size_t)P * sizeof(ade::RateParams));
+    L.tiles = take((size_t)max_tiles * sizeof(ade::BatchTile));
+    L.queue = take(64);
+    L.plume_of = take((size_t)N * 2);
+    L.offsets = take(((size_t)P + 1) * 4);
+    L.stats = take((size_t)P * 3 * 8);
+    L.status = take(64);
+    L.pairs = take(64);
+    L.total = off;
+    return L;
+}
+
+constexpr int kMinTile = 32;
+
+int batch_validate(int P, const ade_params *p, const int *n)
+{
+    if (P < 1 || P > 65535) return fail(ADE_ERR_ARG, "nplumes must be in 1..65535");
+    if (!p || !n) return fail(ADE_ERR_ARG, "NULL argument");
+    long long N = 0;
+    for (int i = 0; i < P; ++i) {
+        int rc = validate(p + i, n[i]);
+        if (rc) return rc;
+        if (p[i].dim != p[0].dim || p[i].kernel != p[0].kernel)
+            return fail(ADE_ERR_ARG, "all plumes of a batch need the same dim and kernel");
+        if (!(p[i].box[1] == p[i].box[0] && (p[i].dim == 2 || p[i].box[2] == p[i].box[0])))
+            return fail(ADE_ERR_ARG, "batched plumes need a cubic box (equal sides)");
+        N += n[i];
+    }
+    if (N > (1ll << 28)) return fail(ADE_ERR_ARG, "total particles exceed 2^28");
+    return ADE_OK;
+}
+
+// Worst-case total cells over every subdivision a plume may be given.
+int batch_max_cells(int P, const ade_params *p, const int *n, long long *nc_max)
+{
+    long long tot = 0;
+    for (int i = 0; i < P; ++i) {
+        const double H = p[i].kernel == ADE_WENDLAND_C2 ? 2.0 * p[i].h : p[i].h;
+        long long m = 0;
+        for (int k = 1; k <= ade::kMaxSubdiv; ++k) {
+            Grid g;
+            if (make_grid(p[i], H, k, &g)) m = std::max<long long>(m, g.ncells);
+        }
+        if (m == 0) return fail(ADE_ERR_ARG, "plume %d: box too small for the support radius", i);
+        tot += m;
+    }
+    if (tot > (1ll << ade::kMaxCellBits)) return fail(ADE_ERR_ARG, "batch exceeds 2^24 cells");
+    *nc_max = tot;
+    return ADE_OK;
+}
+
+int batch_max_tiles(int P, const int *n)
+{
+    long long t = 0;
+    for (int i = 0; i < P; ++i) t += (n[i] + kMinTile - 1) / kMinTile;
+    return (int)t;
+}
+
+// Plan the batch for the current subdivision mode and tile size: per-plume constants, global
+// cell offsets and the work list, ordered by decreasing estimated cost (candidates per item).
+int batch_plan(ade_batch *b)
+{
+    b->NC = 0;
+    std::vector<std::pair<double, ade::BatchTile>> items;
+    for (int i = 0; i < b->P; ++i) {
+        ade_params pp = b->params[i];
+        if (b->subdiv_mode > 0) {
+            const double H = pp.kernel == ADE_WENDLAND_C2 ? 2.0 * pp.h : pp.h;
+            Grid g;
+            if (make_grid(pp, H, b->subdiv_mode, &g)) pp.cell_subdiv = b->subdiv_mode;
+        }
+        pp.flags = ADE_FLAG_DIRECT;
+        Derived d;
+        int rc = derive(&pp, b->n[i], &d);
+        if (rc) return rc;
+        ade::RateParams rp;
+        bool iso = true;
+        uint32_t inc[3], inc_half[3];
+        rc = plume_constants(&pp, b->n[i], d, &b->D[9 * i], &b->dt[i], inc, inc_half, &rp, &iso);
+        if (rc) return rc;
+        rp.goff = b->offsets[i];
+        rp.coff = b->NC;
+        b->ncells[i] = d.g.ncells;
+        b->subdiv_choice[i] = d.g.subdiv;
+        b->NC += d.g.ncells;
+        ade::RateParams pr = rp, co = rp;
+        pr.dt = (float)(0.5 * b->dt[i]);
+        co.dt = (float)b->dt[i];
+        for (int a = 0; a < 3; ++a) {
+            pr.inc[a] = inc_half[a];
+            pr.back[a] = 0u;
+            co.inc[a] = inc[a];
+            co.back[a] = inc_half[a];
+        }
+        b->pred[i] = pr;
+        b->corr[i] = co;
+        // work items and their estimated cost: candidates per particle x particles
+        const double ppc = (double)b->n[i] / d.g.ncells;
+        double cand = 0.0;
+        for (int r = 0; r < d.g.nrows; ++r) cand += (2 * d.g.rows[r].w + 1) * ppc;
+        for (int s0 = 0; s0 < b->n[i]; s0 += b->tile_size) {
+            ade::BatchTile t;
+            t.plume = i;
+            t.start = s0;
+            t.count = std::min(b->tile_size, b->n[i] - s0);
+            t.pad = 0;
+            items.push_back({(cand + 4.0 * d.g.nrows) * t.count, t});
+        }
+    }
+    if (b->NC > b->NC_max) return fail(ADE_ERR_CAPACITY, "batch cell table exceeds the workspace");
+    std::stable_sort(items.begin(), items.end(),
+                     [](const std::pair<double, ade::BatchTile> &x, const std::pair<double, ade::BatchTile> &y) {
+                         return x.first > y.first;
+                     });
+    if ((int)items.size() > b->max_tiles) return fail(ADE_ERR_CAPACITY, "too many work items");
+    b->tiles.clear();
+    for (auto &it : items) b->tiles.push_back(it.second);
+    return ADE_OK;
+}
+
+int batch_upload(ade_batch *b, cudaStream_t s)
+{
+    ADE_CK(cudaMemcpyAsync(b->d_pred, b->pred.data(), b->P * sizeof(ade::RateParams), cudaMemcpyHostToDevice, s));
+    ADE_CK(cudaMemcpyAsync(b->d_corr, b->corr.data(), b->P * sizeof(ade::RateParams), cudaMemcpyHostToDevice, s));
+    if (!b->tiles.empty())
+        ADE_CK(cudaMemcpyAsync(b->d_tiles, b->tiles.data(), b->tiles.size() * sizeof(ade::BatchTile),
+                               cudaMemcpyHostToDevice, s));
+    ADE_CK(cudaStreamSynchronize(s));   // the host vectors may change before the next call
+    if (b->graph_exec) {
+        cudaGraphExecDestroy(b->graph_exec);
+        b->graph_exec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return ADE_OK;
+}
+
+int batch_cells(ade_batch *b, cudaStream_t s)
+{
+    ADE_CK(ade::launch_build_cells_batch(b->dim, b->xq, b->C, b->N, b->NC, b->d_pred, b->plume_of, b->w, s));
+    return ADE_OK;
+}
+
+int batch_enqueue_step(ade_batch *b, cudaStream_t s)
+{
+    int rc = batch_cells(b, s);
+    if (rc) return rc;
+    ade::EpiOut out = epi_none();
+    out.Pout = b->w.P1;
+    ADE_CK(ade::launch_rate_batch(b->dim, b->kernel, ade::EPI_PREDICT, b->w.P0, b->w.cell_start, b->w.perm,
+                                  b->d_pred, b->d_tiles, (int)b->tiles.size(), b->queue, b->grid, out, s));
+    out = epi_none();
+    out.xq = b->xq;
+    out.C = b->C;
+    out.status = b->w.status;
+    ADE_CK(ade::launch_rate_batch(b->dim, b->kernel, ade::EPI_CORRECT, b->w.P1, b->w.cell_start, b->w.perm,
+                                  b->d_corr, b->d_tiles, (int)b->tiles.size(), b->queue, b->grid, out, s));
+    return ADE_OK;
+}
+
+int batch_clear_status_once(ade_batch *b, cudaStream_t s)
+{
+    if (!b->status_cleared) {
+        ADE_CK(cudaMemsetAsync(b->w.status, 0, sizeof(int), s));
+        b->status_cleared = true;
+    }
+    return ADE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ade_batch_workspace_bytes(int nplumes, const ade_params *p, const int *n, size_t *bytes)
+{
+    if (!bytes) return fail(ADE_ERR_ARG, "bytes is NULL");
+    int rc = batch_validate(nplumes, p, n);
+    if (rc) return rc;
+    long long ncm = 0;
+    rc = batch_max_cells(nplumes, p, n, &ncm);
+    if (rc) return rc;
+    long long N = 0;
+    for (int i = 0; i < nplumes; ++i) N += n[i];
+    *bytes = batch_layout(nplumes, (int)N, (int)ncm, batch_max_tiles(nplumes, n)).total;
+    return ADE_OK;
+}
+
+int ade_batch_init(ade_batch **out, int nplumes, const ade_params *p, const int *n, uint32_t *xq_dev,
+                   float *C_dev, void *workspace_dev, size_t workspace_bytes, void *stream)
+{
+    if (!out) return fail(ADE_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = batch_validate(nplumes, p, n);
+    if (rc) return rc;
+    long long ncm = 0;
+    rc = batch_max_cells(nplumes, p, n, &ncm);
+    if (rc) return rc;
+    ade_batch *b = new (std::nothrow) ade_batch;
+    if (!b) return fail(ADE_ERR_CAPACITY, "out of host memory");
+    b->P = nplumes;
+    b->dim = p[0].dim;
+    b->kernel = p[0].kernel;
+    b->params.assign(p, p + nplumes);
+    b->n.assign(n, n + nplumes);
+    b->offsets.assign(nplumes + 1, 0);
+    for (int i = 0; i < nplumes; ++i) b->offsets[i + 1] = b->offsets[i] + n[i];
+    b->N = b->offsets[nplumes];
+    b->NC_max = (int)ncm;
+    b->max_tiles = batch_max_tiles(nplumes, n);
+    b->subdiv_choice.assign(nplumes, 0);
+    b->ncells.assign(nplumes, 0);
+    b->pred.resize(nplumes);
+    b->corr.resize(nplumes);
+    b->dt.assign(nplumes, 0.0);
+    b->D.assign(9 * (size_t)nplumes, 0.0);
+    const BatchLayout L = batch_layout(nplumes, b->N, b->NC_max, b->max_tiles);
+    if (b->N > 0 && (!xq_dev || !C_dev)) {
+        delete b;
+        return fail(ADE_ERR_ARG, "xq_dev and C_dev must be non-NULL");
+    }
+    if (!workspace_dev || ((uintptr_t)workspace_dev & 255u) != 0u) {
+        delete b;
+        return fail(ADE_ERR_ARG, "workspace must be non-NULL and 256-byte aligned");
+    }
+    if (workspace_bytes < L.total) {
+        delete b;
+        return fail(ADE_ERR_CAPACITY, "workspace too small: %zu < %zu bytes", workspace_bytes, L.total);
+    }
+    b->xq = xq_dev;
+    b->C = C_dev;
+    b->ws = workspace_dev;
+    b->ws_bytes = workspace_bytes;
+    memset(&b->w, 0, sizeof(b->w));
+    b->w.keys = at<uint32_t>(workspace_dev, L.keys);
+    b->w.rank = at<uint32_t>(workspace_dev, L.rank);
+    b->w.count = at<uint32_t>(workspace_dev, L.count);
+    b->w.block_sums = at<uint32_t>(workspace_dev, L.block_sums);
+    b->w.perm_tmp = at<uint32_t>(workspace_dev, L.perm_tmp);
+    b->w.perm = at<uint32_t>(workspace_dev, L.perm);
+    b->w.cell_start = at<uint32_t>(workspace_dev, L.cell_start);
+    b->w.P0 = at<uint4>(workspace_dev, L.P0);
+    b->w.P1 = at<uint4>(workspace_dev, L.P1);
+    b->w.status = at<int>(workspace_dev, L.status);
+    b->w.pairs = at<unsigned long long>(workspace_dev, L.pairs);
+    b->d_pred = at<ade::RateParams>(workspace_dev, L.pred);
+    b->d_corr = at<ade::RateParams>(workspace_dev, L.corr);
+    b->d_tiles = at<ade::BatchTile>(workspace_dev, L.tiles);
+    b->queue = at<unsigned>(workspace_dev, L.queue);
+    b->plume_of = at<uint16_t>(workspace_dev, L.plume_of);
+    b->d_offsets = at<int>(workspace_dev, L.offsets);
+    b->d_stats = at<double>(workspace_dev, L.stats);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        delete b;
+        return fail(ADE_ERR_CUDA, "device query: %s", cudaGetErrorString(e));
+    }
+    b->grid = b->sms * 8;
+    rc = batch_plan(b);
+    if (rc) {
+        delete b;
+        return rc;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<uint16_t> pid((size_t)b->N);
+    for (int i = 0; i < nplumes; ++i)
+        std::fill(pid.begin() + b->offsets[i], pid.begin() + b->offsets[i + 1], (uint16_t)i);
+    e = cudaSuccess;
+    if (b->N > 0) e = cudaMemcpyAsync(b->plume_of, pid.data(), pid.size() * 2, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_offsets, b->offsets.data(), b->offsets.size() * 4, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        delete b;
+        return fail(ADE_ERR_CUDA, "upload: %s", cudaGetErrorString(e));
+    }
+    rc = batch_upload(b, s);
+    if (rc) {
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return ADE_OK;
+}
+
+int ade_batch_step(ade_batch *b, int nsteps, void *stream)
+{
+    if (!b || nsteps < 0) return fail(ADE_ERR_ARG, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = batch_clear_status_once(b, s);
+    for (int k = 0; rc == ADE_OK && k < nsteps; ++k) rc = batch_enqueue_step(b, s);
+    if (rc) return rc;
+    b->step += nsteps;
+    return ADE_OK;
+}
+
+int ade_batch_run(ade_batch *b, int nsteps, void *stream)
+{
+    if (!b || nsteps < 0) return fail(ADE_ERR_ARG, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = batch_clear_status_once(b, s);
+    if (rc) return rc;
+    if (!b->graph_exec && nsteps > 0) {
+        if (!b->cap_stream) ADE_CK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+        ADE_CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+        rc = batch_enqueue_step(b, b->cap_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        ADE_CK(e);
+        cudaError_t ei = cudaGraphInstantiate(&b->graph_exec, g, 0);
+        if (ei != cudaSuccess) {
+            cudaGraphDestroy(g);
+            b->graph_exec = nullptr;
+            return fail(ADE_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ei));
+        }
+        b->graph = g;
+    }
+    for (int k = 0; k < nsteps; ++k) ADE_CK(cudaGraphLaunch(b->graph_exec, s));
+    b->step += nsteps;
+    return ADE_OK;
+}
+
+int ade_batch_stats(ade_batch *b, ade_stats *st, void *stream)
+{
+    if (!b || !st) return fail(ADE_ERR_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = batch_clear_status_once(b, s);
+    if (rc) return rc;
+    ADE_CK(ade::launch_batch_stats(b->C, b->d_offsets, b->P, b->d_stats, s));
+    std::vector<double> h(3 * (size_t)b->P);
+    int status = 0;
+    ADE_CK(cudaMemcpyAsync(h.data(), b->d_stats, h.size() * 8, cudaMemcpyDeviceToHost, s));
+    ADE_CK(cudaMemcpyAsync(&status, b->w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ADE_CK(cudaStreamSynchronize(s));
+    for (int i = 0; i < b->P; ++i) {
+        st[i].mass = h[3 * i] * b->params[i].mass;
+        st[i].c_min = b->n[i] > 0 ? h[3 * i + 1] : 0.0;
+        st[i].c_max = b->n[i] > 0 ? h[3 * i + 2] : 0.0;
+        st[i].t = b->step * b->dt[i];
+        st[i].step = b->step;
+        st[i].pairs = 0;
+        st[i].status = status ? ADE_ERR_NUMERIC : ADE_OK;
+    }
+    return status ? fail(ADE_ERR_NUMERIC, "non-finite concentration produced") : ADE_OK;
+}
+
+int ade_batch_count_pairs(ade_batch *b, long long *pairs_host, void *stream)
+{
+    if (!b || !pairs_host) return fail(ADE_ERR_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = batch_cells(b, s);
+    if (rc) return rc;
+    ADE_CK(cudaMemsetAsync(b->w.pairs, 0, 8, s));
+    ade::EpiOut out = epi_none();
+    out.pairs = b->w.pairs;
+    ADE_CK(ade::launch_rate_batch(b->dim, b->kernel, ade::EPI_RATE, b->w.P0, b->w.cell_start, b->w.perm,
+                                  b->d_pred, b->d_tiles, (int)b->tiles.size(), b->queue, b->grid, out, s));
+    unsigned long long v = 0;
+    ADE_CK(cudaMemcpyAsync(&v, b->w.pairs, 8, cudaMemcpyDeviceToHost, s));
+    ADE_CK(cudaStreamSynchronize(s));
+    *pairs_host = (long long)v;
+    return ADE_OK;
+}
+
+int ade_batch_get_plume_info(const ade_batch *b, int plume, ade_info *info)
+{
+    if (!b || !info || plume < 0 || plume >= b->P) return fail(ADE_ERR_ARG, "bad argument");
+    memset(info, 0, sizeof(*info));
+    const ade::RateParams &rp = b->pred[plume];
+    const ade_params &p = b->params[plume];
+    info->support = p.kernel == ADE_WENDLAND_C2 ? 2.0 * p.h : p.h;
+    info->dt = b->dt[plume];
+    for (int i = 0; i < 9; ++i) info->D[i] = b->D[9 * plume + i];
+    info->nc[0] = rp.ncx;
+    info->nc[1] = rp.ncy;
+    info->nc[2] = rp.ncz;
+    info->ncells = b->ncells[plume];
+    info->cell_subdiv = b->subdiv_choice[plume];
+    info->stencil_rows = rp.nrows;
+    info->sort_passes = 1;
+    info->variant = 0;
+    info->tile[0] = b->tile_size;
+    info->tile[1] = b->grid;
+    info->tile[2] = (int)b->tiles.size();
+    info->workspace_bytes = b->ws_bytes;
+    return ADE_OK;
+}
+
+int ade_batch_autotune(ade_batch *b, double *best_ms_host, void *stream)
+{
+    if (!b) return fail(ADE_ERR_ARG, "batch is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    ADE_CK(cudaEventCreate(&e0));
+    ADE_CK(cudaEventCreate(&e1));
+    // one candidate: cell build + one evaluation of every plume (no output), best of two
+    auto time_cfg = [&](double *ms) -> int {
+        int rc = batch_plan(b);
+        if (rc) return rc;
+        rc = batch_upload(b, s);
+        if (rc) return rc;
+        double best = 1e30;
+        for (int rep = 0; rep < 2; ++rep) {
+            ADE_CK(cudaEventRecord(e0, s));
+            rc = batch_cells(b, s);
+            if (rc) return rc;
+            ade::EpiOut out = epi_none();
+            ADE_CK(ade::launch_rate_batch(b->dim, b->kernel, ade::EPI_RATE, b->w.P0, b->w.cell_start,
+                                          b->w.perm, b->d_pred, b->d_tiles, (int)b->tiles.size(), b->queue,
+                                          b->grid, out, s));
+            ADE_CK(cudaEventRecord(e1, s));
+            ADE_CK(cudaEventSynchronize(e1));
+            float f = 0.f;
+            ADE_CK(cudaEventElapsedTime(&f, e0, e1));
+            best = std::min(best, (double)f);
+        }
+        *ms = best;
+        return ADE_OK;
+    };
+    int rc = ADE_OK;
+    double best = 1e30, ms = 0.0;
+    int best_mode = b->subdiv_mode, best_tile = b->tile_size, best_grid = b->grid;
+    for (int mode = 0; rc == ADE_OK && mode <= ade::kMaxSubdiv; ++mode) {
+        b->subdiv_mode = mode;
+        rc = time_cfg(&ms);
+        if (rc == ADE_OK && ms < best) {
+            best = ms;
+            best_mode = mode;
+        }
+    }
+    b->subdiv_mode = best_mode;
+    const int tile_sizes[] = {64, 128, 256, 512};
+    for (int ti = 0; rc == ADE_OK && ti < 4; ++ti) {
+        b->tile_size = tile_sizes[ti];
+        rc = time_cfg(&ms);
+        if (rc == ADE_OK && ms < best) {
+            best = ms;
+            best_tile = tile_sizes[ti];
+        }
+    }
+    b->tile_size = best_tile;
+    const int per_sm[] = {4, 8, 16};
+    for (int gi = 0; rc == ADE_OK && gi < 3; ++gi) {
+        b->grid = b->sms * per_sm[gi];
+        rc = time_cfg(&ms);
+        if (rc == ADE_OK && ms < best) {
+            best = ms;
+            best_grid = b->grid;
+        }
+    }
+    b->grid = best_grid;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    rc = batch_plan(b);
+    if (rc) return rc;
+    rc = batch_upload(b, s);
+    if (rc) return rc;
+    if (best_ms_host) *best_ms_host = best;
+    return ADE_OK;
+}
+
+int ade_batch_step_timed(ade_batch *b, double *phase_ms, void *stream)
+{
+    if (!b || !phase_ms) return fail(ADE_ERR_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = batch_clear_status_once(b, s);
+    if (rc) return rc;
+    cudaEvent_t ev[4];
+    for (int k = 0; k < 4; ++k) ADE_CK(cudaEventCreate(&ev[k]));
+    ADE_CK(cudaEventRecord(ev[0], s));
+    rc = batch_cells(b, s);
+    if (rc) return rc;
+    ADE_CK(cudaEventRecord(ev[1], s));
+    ade::EpiOut out = epi_none();
+    out.Pout = b->w.P1;
+    ADE_CK(ade::launch_rate_batch(b->dim, b->kernel, ade::EPI_PREDICT, b->w.P0, b->w.cell_start, b->w.perm,
+                                  b->d_pred, b->d_tiles, (int)b->tiles.size(), b->queue, b->grid, out, s));
+    ADE_CK(cudaEventRecord(ev[2], s));
+    out = epi_none();
+    out.xq = b->xq;
+    out.C = b->C;
+    out.status = b->w.status;
+    ADE_CK(ade::launch_rate_batch(b->dim, b->kernel, ade::EPI_CORRECT, b->w.P1, b->w.cell_start, b->w.perm,
+                                  b->d_corr, b->d_tiles, (int)b->tiles.size(), b->queue, b->grid, out, s));
+    ADE_CK(cudaEventRecord(ev[3], s));
+    ADE_CK(cudaEventSynchronize(ev[3]));
+    for (int k = 0; k < 3; ++k) {
+        float ms = 0.f;
+        ADE_CK(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+        phase_ms[k] = ms;
+    }
+    phase_ms[3] = 0.0;
+    for (int k = 0; k < 4; ++k) cudaEventDestroy(ev[k]);
+    b->step += 1;
+    return ADE_OK;
+}
+
+int ade_batch_launches_per_step(const ade_batch *b, int *launches)
+{
+    if (!b || !launches) return fail(ADE_ERR_ARG, "NULL argument");
+    *launches = 8;  // count, 3 scan launches, place, order, predictor, corrector
+    return ADE_OK;
+}
+
+void ade_batch_destroy(ade_batch *b)
+{
+    if (!b) return;
+    if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    delete b;
 }
 
 }  // extern "C"

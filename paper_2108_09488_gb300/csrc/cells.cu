@@ -191,9 +191,84 @@ __global__ __launch_bounds__(kThreads) void k_order(const uint32_t *__restrict__
     }
 }
 
+// Batched plumes: caller particle i belongs to plume p = plume_of[i], whose positions are the
+// [dim][n_p] block starting at xq + dim * goff_p; its key is coff_p + the plume-local key.
+__global__ __launch_bounds__(kThreads) void k_count_batch(const uint32_t *__restrict__ xq, int n, int dim,
+                                                          const RateParams *__restrict__ descs,
+                                                          const uint16_t *__restrict__ plume_of,
+                                                          uint32_t *__restrict__ keys,
+                                                          uint32_t *__restrict__ rank,
+                                                          uint32_t *__restrict__ count)
+{
+    const int i = blockIdx.x * kThreads + threadIdx.x;
+    if (i >= n) return;
+    const RateParams &d = descs[__ldg(plume_of + i)];
+    const int np = d.n, goff = d.goff;
+    const uint32_t key = (uint32_t)d.coff + cell_key(xq + (size_t)dim * goff, np, i - goff, dim, d.ncx, d.ncy, d.ncz);
+    keys[i] = key;
+    rank[i] = atomicAdd(count + key, 1u);
+}
+
+__global__ __launch_bounds__(kThreads) void k_order_batch(const uint32_t *__restrict__ start, int ncells,
+                                                          const uint32_t *__restrict__ perm_tmp,
+                                                          const uint32_t *__restrict__ xq,
+                                                          const float *__restrict__ C, int n, int dim,
+                                                          const RateParams *__restrict__ descs,
+                                                          const uint16_t *__restrict__ plume_of,
+                                                          uint32_t *__restrict__ perm,
+                                                          uint4 *__restrict__ P)
+{
+    const int c = blockIdx.x * kThreads + threadIdx.x;
+    if (c >= ncells) return;
+    const uint32_t s = __ldg(start + c), e = __ldg(start + c + 1);
+    if (e <= s || e > (uint32_t)n) return;
+    for (uint32_t k = s; k < e; ++k) {
+        uint32_t v = __ldg(perm_tmp + k);
+        uint32_t j = k;
+        while (j > s && perm[j - 1] > v) {
+            perm[j] = perm[j - 1];
+            --j;
+        }
+        perm[j] = v;
+    }
+    for (uint32_t k = s; k < e; ++k) {
+        const uint32_t a = perm[k];
+        const RateParams &d = descs[__ldg(plume_of + a)];
+        const uint32_t *xp = xq + (size_t)dim * d.goff;
+        const uint32_t l = a - (uint32_t)d.goff, np = (uint32_t)d.n;
+        uint4 p;
+        p.x = __ldg(xp + l);
+        p.y = __ldg(xp + np + l);
+        p.z = dim == 3 ? __ldg(xp + 2 * (size_t)np + l) : 0u;
+        p.w = __float_as_uint(__ldg(C + a));
+        P[k] = p;
+    }
+}
+
 }  // namespace
 
 int scan_blocks(int m) { return (m + kScanTile - 1) / kScanTile; }
+
+cudaError_t launch_build_cells_batch(int dim, const uint32_t *xq, const float *C, int n, int ncells,
+                                     const RateParams *descs, const uint16_t *plume_of,
+                                     const Work &w, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(w.count, 0, (size_t)ncells * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    const int nb = (n + kThreads - 1) / kThreads;
+    if (nb > 0)
+        k_count_batch<<<nb, kThreads, 0, s>>>(xq, n, dim, descs, plume_of, w.keys, w.rank, w.count);
+    const int sb = scan_blocks(ncells);
+    k_scan_blocks<<<sb, kThreads, 0, s>>>(w.count, ncells, w.block_sums);
+    k_scan_top<<<1, kThreads, 0, s>>>(w.block_sums, sb);
+    k_scan_apply<<<sb, kThreads, 0, s>>>(w.count, ncells, w.block_sums, w.cell_start);
+    if (nb > 0) {
+        k_place<<<nb, kThreads, 0, s>>>(w.keys, w.rank, n, w.cell_start, w.perm_tmp);
+        k_order_batch<<<(ncells + kThreads - 1) / kThreads, kThreads, 0, s>>>(
+            w.cell_start, ncells, w.perm_tmp, xq, C, n, dim, descs, plume_of, w.perm, w.P0);
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_build_cells(int dim, const uint32_t *xq, const float *C, int n, const int *nc,
                                int ncells, const Work &w, cudaStream_t s)

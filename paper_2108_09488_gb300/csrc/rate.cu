@@ -182,7 +182,7 @@ __device__ __forceinline__ void epilogue(int gi, float rate, const uint4 &pe,
     if (EPI == EPI_RATE) {
         if (out.rate) {
             const uint32_t a = __ldg(perm + gi);
-            if (a < (uint32_t)prm.n) out.rate[a] = rate;
+            if (a - (uint32_t)prm.goff < (uint32_t)prm.n) out.rate[a] = rate;
         }
     } else if (EPI == EPI_PREDICT) {
         // C^{l+1/2} = C^l + dt/2 r^l, x^{l+1/2} = x^l + dt/2 v
@@ -198,7 +198,7 @@ __device__ __forceinline__ void epilogue(int gi, float rate, const uint4 &pe,
         // the caller's array, read just before this thread overwrites it.
         const uint32_t a = __ldg(perm + gi);
         float Cn = 0.f;
-        if (a < (uint32_t)prm.n) {
+        if (a - (uint32_t)prm.goff < (uint32_t)prm.n) {
             Cn = fmaf(prm.dt, rate, out.C[a]);
             out.C[a] = Cn;
             out.xq[a] = pe.x - prm.back[0] + prm.inc[0];
@@ -521,6 +521,83 @@ __global__ __launch_bounds__(kTileThreads, 2) void k_rate_tiled(const uint4 *__r
 }
 
 // ---------------------------------------------------------------------------------------------
+// batched plumes: persistent kernel over a queue of (plume, range) work items
+// ---------------------------------------------------------------------------------------------
+// Every CTA takes work items from an atomic counter until the list is exhausted (no CTA waits on
+// another).  An item is a range of one plume's cell-sorted particles; the plume's constants are
+// copied to shared memory once per item and each particle is evaluated with the same code as the
+// single-plume direct kernel (rate_direct + epilogue), so a plume gives bit-identical results
+// whether it runs alone or in a batch.  Items are ordered by decreasing estimated cost.
+template <int DIM, int KERNEL, int EPI, bool COUNT>
+__global__ __launch_bounds__(kRateThreads) void k_rate_batch(const uint4 *__restrict__ Pe,
+                                                             const uint32_t *__restrict__ cs,
+                                                             const uint32_t *__restrict__ perm,
+                                                             const RateParams *__restrict__ descs,
+                                                             const BatchTile *__restrict__ tiles,
+                                                             int ntiles, unsigned *queue,
+                                                             const EpiOut out)
+{
+    __shared__ RateParams sp;
+    __shared__ int s_item;
+    constexpr int kWords = (int)(sizeof(RateParams) / sizeof(int));
+    static_assert(sizeof(RateParams) % sizeof(int) == 0, "RateParams is copied word by word");
+    int cur = -1;
+    unsigned cnt = 0u;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(queue, 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= ntiles) break;
+        const BatchTile t = tiles[item];
+        if (t.plume != cur) {
+            const int *src = reinterpret_cast<const int *>(descs + t.plume);
+            int *dst = reinterpret_cast<int *>(&sp);
+            for (int w = threadIdx.x; w < kWords; w += kRateThreads) dst[w] = __ldg(src + w);
+            cur = t.plume;
+        }
+        __syncthreads();
+        const RateParams &prm = sp;
+        EpiOut o = out;
+        if (EPI == EPI_CORRECT) o.xq = out.xq + (size_t)prm.goff * (DIM - 1);
+        for (int k = threadIdx.x; k < t.count; k += kRateThreads) {
+            const int gi = prm.goff + t.start + k;
+            const uint4 pa = __ldg(Pe + gi);
+            const int cx = (int)__umulhi(pa.x - prm.back[0], (uint32_t)prm.ncx);
+            const int cy = (int)__umulhi(pa.y - prm.back[1], (uint32_t)prm.ncy);
+            const int cz = DIM == 3 ? (int)__umulhi(pa.z - prm.back[2], (uint32_t)prm.ncz) : 0;
+            unsigned c = 0u;
+            const float rate = rate_direct<DIM, KERNEL, true, COUNT>(Pe, cs + prm.coff, pa, cx, cy, cz, prm, c);
+            cnt += c;
+            Acc acc{0.0, 0.f, 0.f, 0u};
+            epilogue<DIM, EPI>(gi, rate, pa, perm, prm, o, acc);
+        }
+        __syncthreads();   // sp and s_item are rewritten by the next item
+    }
+    if (COUNT) {
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+        if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out.pairs, (unsigned long long)cnt);
+    }
+}
+
+template <int DIM, int KERNEL, bool COUNT>
+void launch_batch_epi(int epi, int grid, const uint4 *Pe, const uint32_t *cs, const uint32_t *perm,
+                      const RateParams *descs, const BatchTile *tiles, int ntiles, unsigned *queue,
+                      const EpiOut &out, cudaStream_t s)
+{
+    switch (epi) {
+    case EPI_RATE:
+        k_rate_batch<DIM, KERNEL, EPI_RATE, COUNT><<<grid, kRateThreads, 0, s>>>(Pe, cs, perm, descs, tiles, ntiles, queue, out);
+        break;
+    case EPI_PREDICT:
+        k_rate_batch<DIM, KERNEL, EPI_PREDICT, COUNT><<<grid, kRateThreads, 0, s>>>(Pe, cs, perm, descs, tiles, ntiles, queue, out);
+        break;
+    default:
+        k_rate_batch<DIM, KERNEL, EPI_CORRECT, COUNT><<<grid, kRateThreads, 0, s>>>(Pe, cs, perm, descs, tiles, ntiles, queue, out);
+        break;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------------------
 template <int DIM, int KERNEL, int EPI, bool COUNT>
@@ -580,6 +657,31 @@ size_t tiled_smem_bytes(int dim, const RateParams &prm)
     const int HX = prm.tx + 2 * k, HY = prm.ty + 2 * k, HZ = dim == 3 ? prm.tz + 2 * k : 1;
     const int tr = prm.ty * (dim == 3 ? prm.tz : 1);
     return (size_t)prm.cap * 16 + (size_t)HY * HZ * (HX + 1) * 4 + (size_t)3 * (tr + 1) * 4;
+}
+
+cudaError_t launch_rate_batch(int dim, int kernel, int epi, const uint4 *Pe, const uint32_t *cell_start,
+                              const uint32_t *perm, const RateParams *descs, const BatchTile *tiles,
+                              int ntiles, unsigned *queue, int grid, const EpiOut &out, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess || ntiles == 0) return e;
+    const bool count = out.pairs != nullptr;
+    if (dim == 2) {
+        if (kernel == ADE_WENDLAND_C2)
+            count ? launch_batch_epi<2, ADE_WENDLAND_C2, true>(epi, grid, Pe, cell_start, perm, descs, tiles, ntiles, queue, out, s)
+                  : launch_batch_epi<2, ADE_WENDLAND_C2, false>(epi, grid, Pe, cell_start, perm, descs, tiles, ntiles, queue, out, s);
+        else
+            count ? launch_batch_epi<2, ADE_WENDLAND_C4, true>(epi, grid, Pe, cell_start, perm, descs, tiles, ntiles, queue, out, s)
+                  : launch_batch_epi<2, ADE_WENDLAND_C4, false>(epi, grid, Pe, cell_start, perm, descs, tiles, ntiles, queue, out, s);
+    } else {
+        if (kernel == ADE_WENDLAND_C2)
+            count ? launch_batch_epi<3, ADE_WENDLAND_C2, true>(epi, grid, Pe, cell_start, perm, descs, tiles, ntiles, queue, out, s)
+                  : launch_batch_epi<3, ADE_WENDLAND_C2, false>(epi, grid, Pe, cell_start, perm, descs, tiles, ntiles, queue, out, s);
+        else
+            count ? launch_batch_epi<3, ADE_WENDLAND_C4, true>(epi, grid, Pe, cell_start, perm, descs, tiles, ntiles, queue, out, s)
+                  : launch_batch_epi<3, ADE_WENDLAND_C4, false>(epi, grid, Pe, cell_start, perm, descs, tiles, ntiles, queue, out, s);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_rate(int dim, int kernel, bool iso, int epi, const uint4 *Pe, const uint4 *Pc,

@@ -155,7 +155,48 @@ __global__ __launch_bounds__(kRedThreads) void k_state_partials(const float *__r
     }
 }
 
+// One block per plume: FP64 {sum C, min C, max C} over the plume's caller range, fixed order.
+__global__ __launch_bounds__(kRedThreads) void k_batch_stats(const float *__restrict__ C,
+                                                             const int *__restrict__ offsets,
+                                                             double *__restrict__ stats)
+{
+    const int p = blockIdx.x;
+    const int lo = offsets[p], hi = offsets[p + 1];
+    double s = 0.0, mn = dinf(), mx = -dinf();
+    for (int i = lo + threadIdx.x; i < hi; i += kRedThreads) {
+        const double v = (double)C[i];
+        s += v;
+        mn = fmin(mn, v);
+        mx = fmax(mx, v);
+    }
+    __shared__ double sh[3][kRedThreads];
+    sh[0][threadIdx.x] = s;
+    sh[1][threadIdx.x] = mn;
+    sh[2][threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+            sh[1][threadIdx.x] = fmin(sh[1][threadIdx.x], sh[1][threadIdx.x + o]);
+            sh[2][threadIdx.x] = fmax(sh[2][threadIdx.x], sh[2][threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        stats[3 * p + 0] = sh[0][0];
+        stats[3 * p + 1] = sh[1][0];
+        stats[3 * p + 2] = sh[2][0];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_batch_stats(const float *C, const int *offsets, int nplumes, double *stats,
+                               cudaStream_t s)
+{
+    if (nplumes > 0) k_batch_stats<<<nplumes, kRedThreads, 0, s>>>(C, offsets, stats);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_state_stats(const float *C, int n, double *partials, double *stats, cudaStream_t s)
 {

@@ -122,3 +122,15 @@ def test_empty_particle_set_is_valid(adelib):
     ctx, nbytes = _ctx(adelib, p, 0)
     assert nbytes > 0
     adelib.destroy(ctx)
+
+
+def test_batch_workspace_and_validation(adelib):
+    plumes = inputs.batched_2d(nplumes=5, side_lo=16, side_hi=64)
+    plist = [adelib.params_for(p) for p in plumes]
+    ns = [p.n for p in plumes]
+    assert adelib.batch_workspace_bytes(plist, ns) > 16 * sum(ns)
+    bad = list(plist)
+    bad[2] = adelib.params_for(inputs.cube_3d_128(side=16))
+    with pytest.raises(adelib.AdeError) as e:
+        adelib.batch_workspace_bytes(bad, ns[:2] + [16 ** 3] + ns[3:])
+    assert e.value.code == -1
