@@ -161,6 +161,30 @@ int ade_get_stats(ade_ctx *ctx, ade_stats *stats_host, void *stream);
 int ade_closed_form_error(ade_ctx *ctx, const double *x0_host, double w, double C0,
                           int nimg, double *out_host, void *stream);
 
+/* Change alpha_L, alpha_T and D_m (Eq. 3) of a context, keeping its time step, grid and state. */
+int ade_set_dispersivity(ade_ctx *ctx, double alpha_L, double alpha_T, double D_m);
+
+/* ---- Adjoint (dispersivity inversion) ---------------------------------------------------------
+ * The paper has no adjoint; it is derived from Eq. 3-5 and Eq. 8-9 for the uniform-velocity case.
+ * With the rate r = L(theta) C linear in C, theta = (alpha_L, alpha_T, D_m), L symmetric and the
+ * same at every step (uniform drift), one step is C^{l+1} = S C^l, S = I + dt L + dt^2 L^2 / 2.
+ * For J = 1/2 sum_a (C_a^N - C*_a)^2 with dt fixed:
+ *   dJ/dC^0 = S^N (C^N - C*)  and  dJ/dtheta_k = sum_l lambda^{l+1} . (dS/dtheta_k) C^l,
+ *   lambda^N = C^N - C*, lambda^l = S lambda^{l+1}.
+ * The forward run starts from the context's current state (which is not modified), uses one cell
+ * list built at the current positions, and keeps C every ckpt_every steps; segments are recomputed
+ * on the way back.  Pair arithmetic is FP32; J and the dot products are FP64. */
+
+/* Device workspace of ade_adjoint for nsteps steps with checkpoints every ckpt_every steps. */
+int ade_adjoint_workspace_bytes(const ade_ctx *ctx, int nsteps, int ckpt_every, size_t *bytes);
+
+/* C_target_dev [n] (caller order): the target field C*.  Outputs: dJdC0_dev [n] (caller order, may
+ * be NULL), dJdtheta_host[3] = dJ/d(alpha_L, alpha_T, D_m) (may be NULL), J_host (may be NULL),
+ * C_final_dev [n] = C^N (caller order, may be NULL).  Waits for the stream. */
+int ade_adjoint(ade_ctx *ctx, const float *C_target_dev, int nsteps, int ckpt_every,
+                void *adjoint_workspace_dev, size_t adjoint_workspace_bytes, float *dJdC0_dev,
+                double *dJdtheta_host, double *J_host, float *C_final_dev, void *stream);
+
 /* ---- Batched plumes -------------------------------------------------------------------------
  * Many independent plumes (the convergence ladder and dispersivity sweep of Sec. 3-4 run side by
  * side) stepped together: one cell build over all plumes (global cell keys offset per plume) and

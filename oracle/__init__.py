@@ -317,3 +317,46 @@ def stats(C, m, C_ref=None, C0=1.0, vol=None):
         out["linf"] = float(np.max(np.abs(e)))
         out["rmse"] = float(np.sqrt(np.mean((e / C0) ** 2)))
     return out
+
+
+# --------------------------------------------------------------------------------------------
+# Misfit and its gradient (checks for the adjoint; FP64)
+# --------------------------------------------------------------------------------------------
+def _R(x, v, C, m, rho, box, kind, H, gamma, theta):
+    """Eq. 4 with theta = (alpha_L, alpha_T, D_m) at fixed positions."""
+    return rate(x, v, C, m, rho, box, kind, H, gamma, theta[0], theta[1], theta[2])[0]
+
+
+def misfit(x, v, C0, m, rho, box, kind, H, gamma, theta, dt, nsteps, target):
+    """J = 1/2 sum (C^N - C*)^2 for nsteps of Eq. 8-9 at fixed positions (a uniform drift leaves
+    every separation, hence the rate, unchanged), dt fixed.  Returns (J, C^N)."""
+    C = np.asarray(C0, dtype=np.float64).copy()
+    for _ in range(nsteps):
+        a = _R(x, v, C, m, rho, box, kind, H, gamma, theta)
+        C = C + dt * _R(x, v, C + 0.5 * dt * a, m, rho, box, kind, H, gamma, theta)
+    e = C - np.asarray(target, dtype=np.float64)
+    return 0.5 * float(np.dot(e, e)), C
+
+
+def misfit_gradient_tlm(x, v, C0, m, rho, box, kind, H, gamma, theta, dt, nsteps, target):
+    """dJ/dtheta by the tangent-linear model: with S(theta) C = C + dt R(C + dt/2 R(C)),
+    dC^{l+1}/dtheta_k = S dC^l/dtheta_k + (dS/dtheta_k) C^l, where (dS/dtheta_k) C =
+    dt R_k(C) + dt^2/2 (R_k(R(C)) + R(R_k(C))) and R_k is Eq. 4 with theta = e_k (D of Eq. 3 is
+    linear in theta).  Returns (J, gradient[3])."""
+    ek = [np.eye(3)[k] for k in range(3)]
+    args = (x, v)
+    kw = (m, rho, box, kind, H, gamma)
+    R = lambda C, th: _R(*args, C, *kw, th)
+    C = np.asarray(C0, dtype=np.float64).copy()
+    dC = [np.zeros_like(C) for _ in range(3)]
+    for _ in range(nsteps):
+        RC = R(C, theta)
+        for k in range(3):
+            Rk = R(C, ek[k])
+            dSk = dt * Rk + 0.5 * dt * dt * (R(RC, ek[k]) + R(Rk, theta))
+            d = dC[k]
+            Sd = d + dt * R(d + 0.5 * dt * R(d, theta), theta)
+            dC[k] = Sd + dSk
+        C = C + dt * R(C + 0.5 * dt * RC, theta)
+    e = C - np.asarray(target, dtype=np.float64)
+    return 0.5 * float(np.dot(e, e)), np.array([float(np.dot(e, dC[k])) for k in range(3)])

@@ -35,7 +35,8 @@ EXPORTS = ("ade_workspace_bytes", "ade_init_particles", "ade_get_info", "ade_bui
            "ade_batch_workspace_bytes", "ade_batch_init", "ade_batch_step", "ade_batch_run",
            "ade_batch_stats", "ade_batch_count_pairs", "ade_batch_get_plume_info",
            "ade_batch_autotune", "ade_batch_launches_per_step", "ade_batch_destroy",
-           "ade_batch_step_timed")
+           "ade_batch_step_timed", "ade_set_dispersivity", "ade_adjoint_workspace_bytes",
+           "ade_adjoint")
 NOALLOC_MAX_PARTICLES = 1 << 20
 NOALLOC_MAX_CELLS = 1 << 20
 
@@ -111,6 +112,10 @@ def load():
         "ade_batch_autotune": (I, [P, ctypes.POINTER(ctypes.c_double), V]),
         "ade_batch_launches_per_step": (I, [P, ctypes.POINTER(I)]),
         "ade_batch_step_timed": (I, [P, ctypes.POINTER(ctypes.c_double), V]),
+        "ade_set_dispersivity": (I, [P, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+        "ade_adjoint_workspace_bytes": (I, [P, I, I, ctypes.POINTER(SZ)]),
+        "ade_adjoint": (I, [P, P, I, I, P, SZ, P, ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(ctypes.c_double), P, V]),
         "ade_batch_destroy": (None, [P]),
         "ade_destroy": (None, [P]),
         "ade_last_error": (ctypes.c_char_p, []),
@@ -303,6 +308,29 @@ class Simulation:
 
     def closed_form_error(self, x0, w, C0=1.0, nimg=2):
         return closed_form_error(self.ctx, x0, w, C0, nimg, self.stream)
+
+    def set_dispersivity(self, alpha_L, alpha_T, D_m):
+        _check(load().ade_set_dispersivity(self.ctx, alpha_L, alpha_T, D_m))
+
+    def adjoint(self, C_target, nsteps, ckpt_every=40, want_dC0=True, want_final=False):
+        """Misfit J = 1/2 |C^N - C*|^2 and its gradients (adjoint of Eq. 8-9, see ade_adjoint).
+        Returns (J, dJ/d(alpha_L, alpha_T, D_m) as a numpy array, dJ/dC0 tensor or None,
+        C^N tensor or None)."""
+        t = self.torch
+        tgt = t.as_tensor(C_target, dtype=t.float32, device=self.C.device).contiguous()
+        nbytes = ctypes.c_size_t(0)
+        _check(load().ade_adjoint_workspace_bytes(self.ctx, nsteps, ckpt_every, ctypes.byref(nbytes)))
+        aws = t.empty(nbytes.value + 256, dtype=t.uint8, device=self.C.device)
+        aws_ptr = (aws.data_ptr() + 255) // 256 * 256
+        dC0 = t.empty(max(self.n, 1), dtype=t.float32, device=self.C.device) if want_dC0 else None
+        fin = t.empty(max(self.n, 1), dtype=t.float32, device=self.C.device) if want_final else None
+        g = (ctypes.c_double * 3)()
+        J = ctypes.c_double(0.0)
+        _check(load().ade_adjoint(self.ctx, tgt.data_ptr(), nsteps, ckpt_every, aws_ptr, nbytes.value,
+                                  dC0.data_ptr() if dC0 is not None else None, g, ctypes.byref(J),
+                                  fin.data_ptr() if fin is not None else None, self.stream))
+        return (J.value, np.array(list(g)), dC0[: self.n] if dC0 is not None else None,
+                fin[: self.n] if fin is not None else None)
 
     def state(self):
         """(xq uint32 [dim][n], C float32 [n]) copied to the host."""

@@ -91,6 +91,9 @@ struct Work {
 // Records msg as the calling thread's last error (read by ade_last_error) and returns code.
 int report_error(int code, const char *msg);
 
+// Pair-factor constants Kc[6], c0 of a uniform dispersion tensor D (dim x dim, Eq. 5, K = 2D).
+void pair_coeffs(int dim, double gamma, const double *D, float *Kc, float *c0);
+
 // Launchers (cells.cu, rate.cu, reduce.cu).  All return cudaGetLastError() of the launches.
 int scan_blocks(int m);
 cudaError_t launch_build_cells(int dim, const uint32_t *xq, const float *C, int n, const int *nc,

@@ -14,6 +14,9 @@
 
 #include "ade_internal.h"
 
+#include <algorithm>
+#include <vector>
+
 namespace {
 
 thread_local char g_err[512] = "";
@@ -432,18 +435,7 @@ int plume_constants(const ade_params *p, int n, const Derived &d, double *D, dou
     *iso = p->box[1] == p->box[0] && (p->dim == 2 || p->box[2] == p->box[0]);
     const double gamma = p->gamma > 0.0 ? p->gamma : p->dim + 2.0;
     const int dm = p->dim;
-    auto K = [&](int i, int j) { return 2.0 * D[i * dm + j]; };  // harmonic mean of equal D
-    // Gamma x^T K x / r^2 - tr K = x^T Gamma (K - K_last I) x / r^2 + (Gamma K_last - tr K)
-    const double Klast = K(dm - 1, dm - 1);
-    double trK = 0.0;
-    for (int i = 0; i < dm; ++i) trK += K(i, i);
-    rp.Kc[0] = (float)(gamma * (K(0, 0) - Klast));
-    rp.Kc[1] = dm == 3 ? (float)(gamma * (K(1, 1) - Klast)) : 0.0f;
-    rp.Kc[2] = 0.0f;
-    rp.Kc[3] = (float)(2.0 * gamma * K(0, 1));
-    rp.Kc[4] = dm == 3 ? (float)(2.0 * gamma * K(0, 2)) : 0.0f;
-    rp.Kc[5] = dm == 3 ? (float)(2.0 * gamma * K(1, 2)) : 0.0f;
-    rp.c0 = (float)(gamma * Klast - trK);
+    ade::pair_coeffs(dm, gamma, D, rp.Kc, &rp.c0);
     const double H = d.H;
     double B, kc;
     if (p->kernel == ADE_WENDLAND_C2) {
@@ -473,6 +465,23 @@ T *at(void *base, size_t off)
 }
 
 }  // namespace
+
+// Pair-factor constants for a uniform tensor D (Eq. 5 with K = 2D):
+// Gamma x^T K x / r^2 - tr K = x^T Gamma (K - K_last I) x / r^2 + (Gamma K_last - tr K).
+void ade::pair_coeffs(int dm, double gamma, const double *D, float *Kc, float *c0)
+{
+    auto K = [&](int i, int j) { return 2.0 * D[i * dm + j]; };  // harmonic mean of equal D
+    const double Klast = K(dm - 1, dm - 1);
+    double trK = 0.0;
+    for (int i = 0; i < dm; ++i) trK += K(i, i);
+    Kc[0] = (float)(gamma * (K(0, 0) - Klast));
+    Kc[1] = dm == 3 ? (float)(gamma * (K(1, 1) - Klast)) : 0.0f;
+    Kc[2] = 0.0f;
+    Kc[3] = (float)(2.0 * gamma * K(0, 1));
+    Kc[4] = dm == 3 ? (float)(2.0 * gamma * K(0, 2)) : 0.0f;
+    Kc[5] = dm == 3 ? (float)(2.0 * gamma * K(1, 2)) : 0.0f;
+    *c0 = (float)(gamma * Klast - trK);
+}
 
 int ade::report_error(int code, const char *msg) { return fail(code, "%s", msg); }
 
@@ -540,6 +549,29 @@ int ade_init_particles(ade_ctx **out, const ade_params *p, int n, uint32_t *xq_d
         return rc;
     }
     *out = c;
+    return ADE_OK;
+}
+
+int ade_set_dispersivity(ade_ctx *c, double alpha_L, double alpha_T, double D_m)
+{
+    if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
+    if (!(alpha_L >= 0.0) || !(alpha_T >= 0.0) || !(D_m >= 0.0) || !isfinite(alpha_L) ||
+        !isfinite(alpha_T) || !isfinite(D_m))
+        return fail(ADE_ERR_ARG, "alpha_L, alpha_T, D_m must be finite and >= 0");
+    c->p.alpha_L = alpha_L;
+    c->p.alpha_T = alpha_T;
+    c->p.D_m = D_m;
+    dispersion_tensor(c->dim, c->p.v, alpha_L, alpha_T, D_m, c->D);
+    const double gamma = c->p.gamma > 0.0 ? c->p.gamma : c->dim + 2.0;
+    ade::pair_coeffs(c->dim, gamma, c->D, c->rp.Kc, &c->rp.c0);
+    if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+    }
+    if (c->graph) {
+        cudaGraphDestroy(c->graph);
+        c->graph = nullptr;
+    }
     return ADE_OK;
 }
 
@@ -817,8 +849,6 @@ void ade_destroy(ade_ctx *c)
 // Batched plumes: many independent plumes stepped together (one cell build, two persistent rate
 // launches per step for the whole batch).
 // =============================================================================================
-#include <algorithm>
-#include <vector>
 
 struct ade_batch {
     int P = 0, dim = 0, kernel = 0, N = 0;
