@@ -40,7 +40,16 @@ WORKLOADS = {
     "lattice-64-h1.3": inputs.lattice_2d_64,
     "cube-128-h2": inputs.cube_3d_128,
     "batched-64": None,          # 64 uneven 2D plumes in one batch (inputs.batched_2d)
+    "adjoint-512": None,         # gradient of the misfit: 512^2, 400 steps, checkpoints every 40
 }
+ADJ_THETA = (1e-2, 1e-3, 1e-6)
+ADJ_THETA_STAR = (2e-2, 2e-3, 1e-6)
+ADJ_STEPS, ADJ_CKPT = 400, 40
+
+
+def adjoint_plume():
+    return inputs.Plume(dim=2, side=512, h_over_dx=1.3, alpha_L=ADJ_THETA[0], alpha_T=ADJ_THETA[1],
+                        D_m=ADJ_THETA[2], name="2d-512^2-h1.3dx-adjoint-400steps")
 DEFAULT_WORKLOAD = "ladder-1024-n120-r10"
 METRIC = "particle-pair interactions/s"
 UNIT = "interactions/s"
@@ -49,6 +58,11 @@ UNIT = "interactions/s"
 # (2D: 16, 3D: 22); the derivation is in the design doc.  The ALU roof is
 # SMs x 128 FP32 lanes x clock / I_MIN pairs per second.
 I_MIN = {2: 16, 3: 22}
+
+# DRAM bytes per rate launch (read + write, mean of predictor and corrector) from one ncu capture
+# of the current kernels (profiles/k_rate_ladder1024.md, profiles/k_rate_batch_batched64.md).
+# Set an entry to None whenever the kernel changes until it is captured again.
+TRAFFIC_PER_LAUNCH = {"ladder-1024-n120-r10": 22.81e6, "batched-64": 45.16e6}
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
 
@@ -219,7 +233,7 @@ def run_reference(args):
         }
         print(json.dumps(line))
         return 0
-    plume = WORKLOADS[args.workload]()
+    plume = adjoint_plume() if args.workload == "adjoint-512" else WORKLOADS[args.workload]()
     xq, C = plume.initial_state()
     sample = args.cpu_sample
     cpu_oracle_rate(plume, xq, C, sample, 0.0, max_steps=args.warmup) if args.warmup else None
@@ -313,7 +327,9 @@ def run_batched(args):
     peak = props.multi_processor_count * FP32_LANES_PER_SM * f_max * 1e6 / I_MIN[2] / 1e9
     achieved = pairs / (rate_avg_ms * 1e-3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_rate_batch (predictor + corrector)",
+                "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get("batched-64"),
+                "traffic_unit": "bytes per launch (ncu dram read + write)",
+                "kernel": "k_rate_batch (predictor + corrector)",
                 "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                               f"{f_max:.0f} MHz / {I_MIN[2]} FP32-pipe instructions per pair",
                 "rate_kernel_ms": rate_avg_ms,
@@ -373,6 +389,69 @@ def run_batched(args):
     return 0
 
 
+def run_adjoint(args):
+    """One bench step = one gradient evaluation: the 400-step forward run with checkpoints and the
+    adjoint sweep (ade_adjoint).  Interactions counted: pair evaluations of every operator
+    application (forward 2 per step, recomputation 2 per step except each segment's last, backward
+    2 three-output and 2 single applications per step)."""
+    import torch
+
+    from paper_2108_09488_gb300 import ade
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = Dist(world, True)
+    p = adjoint_plume()
+    xq, C = p.initial_state()
+    sim = ade.Simulation(ade.params_for(p), xq, C, device=device)
+    pairs = sim.count_pairs()
+    # target: the same run with theta* (generated here on the GPU; the tests generate it with the
+    # oracle at smaller sizes)
+    sim.set_dispersivity(*ADJ_THETA_STAR)
+    _, _, _, target = sim.adjoint(np.zeros(p.n, np.float32), ADJ_STEPS, ADJ_CKPT, want_dC0=False,
+                                  want_final=True)
+    target = target.clone()
+    sim.set_dispersivity(*ADJ_THETA)
+    passes = 2 * ADJ_STEPS + 2 * (ADJ_STEPS - ADJ_STEPS // ADJ_CKPT) + 4 * ADJ_STEPS
+    for _ in range(args.warmup):
+        sim.adjoint(target, ADJ_STEPS, ADJ_CKPT)
+    torch.cuda.synchronize()
+    dist.barrier()
+    stream = torch.cuda.current_stream(device)
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        J, g, _, _ = sim.adjoint(target, ADJ_STEPS, ADJ_CKPT)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    ms = dist.max(e0.elapsed_time(e1), device) / args.steps
+    value = world * passes * pairs / (ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": p.name, "particles": p.n, "time_steps": ADJ_STEPS,
+                   "checkpoint_every": ADJ_CKPT, "theta": ADJ_THETA, "theta_star": ADJ_THETA_STAR,
+                   "step": "one gradient evaluation (forward + adjoint)"},
+        "gradient": {"J": J, "dJ_dalpha_L": g[0], "dJ_dalpha_T": g[1], "dJ_dD_m": g[2]},
+        "interactions_per_step": passes * pairs, "clocks": clk,
+        # cell build (6) and set-up gathers (3); forward 2 per step; recomputation 2 per step but
+        # each segment's last; backward 4 applications and 1 dot-product kernel per step
+        "gpu_launches": args.steps * (9 + 2 * ADJ_STEPS + 2 * (ADJ_STEPS - ADJ_STEPS // ADJ_CKPT)
+                                      + 5 * ADJ_STEPS),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    dist.close()
+    return 0
+
+
 def run_ours(args):
     import torch
 
@@ -381,6 +460,8 @@ def run_ours(args):
     world, rank, local = dist_env()
     if args.workload == "batched-64":
         return run_batched(args)
+    if args.workload == "adjoint-512":
+        return run_adjoint(args)
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
     torch.cuda.set_device(local)
@@ -423,7 +504,9 @@ def run_ours(args):
     peak = sms * FP32_LANES_PER_SM * f_max * 1e6 / I_MIN[plume.dim] / 1e9
     achieved = pairs / (rate_avg_ms * 1e-3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_rate (predictor + corrector)",
+                "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(args.workload),
+                "traffic_unit": "bytes per launch (ncu dram read + write)",
+                "kernel": "k_rate (predictor + corrector)",
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {f_max:.0f} MHz / "
                               f"{I_MIN[plume.dim]} FP32-pipe instructions per pair",
                 "rate_kernel_ms": rate_avg_ms,

@@ -71,19 +71,32 @@ __device__ __forceinline__ unsigned in_support_fp64(int ix, int iy, int iz, cons
     return (r2 > 0.0 && r2 < prm.H2d) ? 1u : 0u;
 }
 
+// Per-pair constants, copied into registers once per particle (the parameter block may live in
+// shared or constant memory).
+struct PairConst {
+    float H2, invH, sy, sz, c0;
+    float K0, K1, K3, K4, K5;
+    template <class P>
+    __device__ __forceinline__ explicit PairConst(const P &prm)
+        : H2(prm.H2), invH(prm.invH), sy(prm.sy), sz(prm.sz), c0(prm.c0), K0(prm.Kc[0]),
+          K1(prm.Kc[1]), K3(prm.Kc[3]), K4(prm.Kc[4]), K5(prm.Kc[5])
+    {
+    }
+};
+
 // Dcal factor of the pair (without the kernel shape): x^T Kc x / r^2 + c0.
 template <int DIM>
-__device__ __forceinline__ float dcal(float dx, float dy, float dz, float rinv2, const RateParams &prm)
+__device__ __forceinline__ float dcal(float dx, float dy, float dz, float rinv2, const PairConst &k)
 {
     float Q;
     if (DIM == 2) {
-        Q = dx * fmaf(prm.Kc[0], dx, prm.Kc[3] * dy);
+        Q = dx * fmaf(k.K0, dx, k.K3 * dy);
     } else {
-        float qx = fmaf(prm.Kc[0], dx, fmaf(prm.Kc[3], dy, prm.Kc[4] * dz));
-        float qy = fmaf(prm.Kc[1], dy, prm.Kc[5] * dz);
+        float qx = fmaf(k.K0, dx, fmaf(k.K3, dy, k.K4 * dz));
+        float qy = fmaf(k.K1, dy, k.K5 * dz);
         Q = fmaf(dx, qx, dy * qy);
     }
-    return fmaf(Q, rinv2, prm.c0);
+    return fmaf(Q, rinv2, k.c0);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -91,8 +104,8 @@ __device__ __forceinline__ float dcal(float dx, float dy, float dz, float rinv2,
 // ---------------------------------------------------------------------------------------------
 template <int DIM, int KERNEL, bool ISO, bool COUNT>
 __device__ __forceinline__ void pair_range_direct(const uint4 *__restrict__ P, int j0, int j1,
-                                                  const uint4 &pa, float Ca, const RateParams &prm,
-                                                  float &rs, unsigned &cnt)
+                                                  const uint4 &pa, float Ca, const PairConst &k,
+                                                  const RateParams &prm, float &rs, unsigned &cnt)
 {
     for (int j = j0; j < j1; ++j) {
         uint4 pb = __ldg(P + j);
@@ -102,16 +115,16 @@ __device__ __forceinline__ void pair_range_direct(const uint4 *__restrict__ P, i
         float dz = 0.f;
         if (DIM == 3) dz = (float)(int)(pa.z - pb.z);
         if (!ISO) {
-            dy *= prm.sy;
-            if (DIM == 3) dz *= prm.sz;
+            dy *= k.sy;
+            if (DIM == 3) dz *= k.sz;
         }
         float r2 = fmaf(dx, dx, dy * dy);
         if (DIM == 3) r2 = fmaf(dz, dz, r2);
-        if (r2 < prm.H2 && r2 > 0.f) {
+        if (r2 < k.H2 && r2 > 0.f) {
             float rinv = rsqrtf(r2);
             float r = r2 * rinv;
-            float f = shape<KERNEL>(fmaf(-r, prm.invH, 1.f));
-            float s = dcal<DIM>(dx, dy, dz, rinv * rinv, prm);
+            float f = shape<KERNEL>(fmaf(-r, k.invH, 1.f));
+            float s = dcal<DIM>(dx, dy, dz, rinv * rinv, k);
             rs = fmaf(f * s, Ca - __uint_as_float(pb.w), rs);
         }
     }
@@ -123,10 +136,11 @@ __device__ float rate_direct(const uint4 *__restrict__ Pe, const uint32_t *__res
                              const uint4 &pa, int cx, int cy, int cz, const RateParams &prm,
                              unsigned &cnt)
 {
-    const int ncx = prm.ncx, ncy = prm.ncy, ncz = prm.ncz;
+    const int ncx = prm.ncx, ncy = prm.ncy, ncz = prm.ncz, nrows = prm.nrows;
+    const PairConst kc(prm);
     const float Ca = __uint_as_float(pa.w);
     float acc = 0.f, comp = 0.f;
-    for (int ri = 0; ri < prm.nrows; ++ri) {
+    for (int ri = 0; ri < nrows; ++ri) {
         const StencilRow row = prm.rows[ri];
         int yy = cy + row.dy;
         yy += (yy < 0) ? ncy : 0;
@@ -155,8 +169,8 @@ __device__ float rate_direct(const uint4 *__restrict__ Pe, const uint32_t *__res
             e0 = __ldg(cs + base + hi);
         }
         float rs = 0.f;
-        pair_range_direct<DIM, KERNEL, ISO, COUNT>(Pe, s0, e0, pa, Ca, prm, rs, cnt);
-        pair_range_direct<DIM, KERNEL, ISO, COUNT>(Pe, s1, e1, pa, Ca, prm, rs, cnt);
+        pair_range_direct<DIM, KERNEL, ISO, COUNT>(Pe, s0, e0, pa, Ca, kc, prm, rs, cnt);
+        pair_range_direct<DIM, KERNEL, ISO, COUNT>(Pe, s1, e1, pa, Ca, kc, prm, rs, cnt);
         neumaier_add(acc, comp, rs);
     }
     return prm.pf * (acc + comp);
@@ -165,13 +179,24 @@ __device__ float rate_direct(const uint4 *__restrict__ Pe, const uint32_t *__res
 // ---------------------------------------------------------------------------------------------
 // epilogue and block reductions
 // ---------------------------------------------------------------------------------------------
-// Per-thread accumulators of the corrector's reductions: FP64 sum of C, FP32 min and max (exact:
-// the values are FP32), in-support pair count.
+// Per-thread accumulators of the corrector's reductions: the sum of C as an unevaluated FP32 pair
+// hi + lo kept with Knuth's error-free two-sum (converted to FP64 once per warp, so the FP64 pipe,
+// which is scarce on this part, sees a few instructions per warp), FP32 min and max (exact: the
+// values are FP32), in-support pair count.
 struct Acc {
-    double s;
+    float hi, lo;
     float mn, mx;
     unsigned cnt;
 };
+
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float x, float xlo)
+{
+    const float s = hi + x;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (x - bb);
+    hi = s;
+    lo = lo + (err + xlo);
+}
 
 // Writes of one particle at sorted position gi; pe = evaluation state {x, y, z, C}.
 template <int DIM, int EPI>
@@ -206,7 +231,7 @@ __device__ __forceinline__ void epilogue(int gi, float rate, const uint4 &pe,
             if (DIM == 3) out.xq[2 * (size_t)prm.n + a] = pe.z - prm.back[2] + prm.inc[2];
         }
         if (!isfinite(Cn)) atomicOr(out.status, 1);
-        acc.s += (double)Cn;
+        two_sum_add(acc.hi, acc.lo, Cn, 0.f);
         acc.mn = fminf(acc.mn, Cn);
         acc.mx = fmaxf(acc.mx, Cn);
     }
@@ -268,24 +293,21 @@ __device__ __forceinline__ void block_finish(Acc acc, const EpiOut &out)
         if ((threadIdx.x & 31) == 0 && c) atomicAdd(out.pairs, (unsigned long long)c);
     }
     if (EPI != EPI_CORRECT) return;
-    // min and max: FP32 warp shuffles (exact).  Sum: FP64, added serially by one lane per warp in
-    // lane order (FP64 issue is scarce on this part; one lane does 32 adds instead of every lane
-    // doing 5 shuffled adds).
-    float mn = acc.mn, mx = acc.mx;
+    // min and max: FP32 warp shuffles (exact).  Sum: the (hi, lo) pairs are combined by a fixed
+    // shuffle tree with the error-free two-sum, then converted to FP64 by lane 0.
+    float mn = acc.mn, mx = acc.mx, hi = acc.hi, lo = acc.lo;
     for (int o = 16; o > 0; o >>= 1) {
         mn = fminf(mn, __shfl_down_sync(0xffffffffu, mn, o));
         mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
+        two_sum_add(hi, lo, h2, l2);
     }
-    __shared__ double lane_sum[NT];
     __shared__ double red[3][NT / 32];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    lane_sum[threadIdx.x] = acc.s;
-    __syncwarp();
     if (lane == 0) {
-        double s = 0.0;
-        for (int l = 0; l < 32; ++l) s += lane_sum[threadIdx.x + l];
-        red[0][wid] = s;
+        red[0][wid] = (double)hi + (double)lo;
         red[1][wid] = (double)mn;
         red[2][wid] = (double)mx;
     }
@@ -330,7 +352,7 @@ __global__ __launch_bounds__(kRateThreads) void k_rate(const uint4 *__restrict__
     const int cx = (int)__umulhi(pa.x - prm.back[0], (uint32_t)prm.ncx);
     const int cy = (int)__umulhi(pa.y - prm.back[1], (uint32_t)prm.ncy);
     const int cz = DIM == 3 ? (int)__umulhi(pa.z - prm.back[2], (uint32_t)prm.ncz) : 0;
-    Acc acc{0.0, __int_as_float(0x7f800000), __int_as_float(0xff800000), 0u};
+    Acc acc{0.f, 0.f, __int_as_float(0x7f800000), __int_as_float(0xff800000), 0u};
     unsigned cnt = 0u;
     const float rate = rate_direct<DIM, KERNEL, ISO, COUNT>(Pe, cs, pa, cx, cy, cz, prm, cnt);
     if (valid) {
@@ -472,7 +494,7 @@ __global__ __launch_bounds__(kTileThreads, 2) void k_rate_tiled(const uint4 *__r
     __syncthreads();
 
     // 4. targets: thread t takes targets t, t + NT, ... in (row, sorted) order
-    Acc acc{0.0, __int_as_float(0x7f800000), __int_as_float(0xff800000), 0u};
+    Acc acc{0.f, 0.f, __int_as_float(0x7f800000), __int_as_float(0xff800000), 0u};
     int r = 0;
     for (int t = threadIdx.x; t < ntarget; t += kTileThreads) {
         while (tpre[r + 1] <= t) ++r;
@@ -488,6 +510,7 @@ __global__ __launch_bounds__(kTileThreads, 2) void k_rate_tiled(const uint4 *__r
             const int4 a = sp[tloc[r] + off];
             const float Ca = __int_as_float(a.w);
             const int hx = cx - tx0 + k, hy = cy - ty0 + k, hz = DIM == 3 ? cz - tz0 + k : 0;
+            const PairConst kc(prm);
             float sum = 0.f, comp = 0.f;
             for (int ri = 0; ri < prm.nrows; ++ri) {
                 const StencilRow row = prm.rows[ri];
@@ -502,8 +525,8 @@ __global__ __launch_bounds__(kTileThreads, 2) void k_rate_tiled(const uint4 *__r
                     float r2 = fmaf(dx, dx, dy * dy);
                     if (DIM == 3) r2 = fmaf(dz, dz, r2);
                     const float rinv = rsqrtf(fmaxf(r2, 1.0f));
-                    const float omq = fmaxf(fmaf(-r2 * rinv, prm.invH, 1.f), 0.f);
-                    const float s = dcal<DIM>(dx, dy, dz, rinv * rinv, prm);
+                    const float omq = fmaxf(fmaf(-r2 * rinv, kc.invH, 1.f), 0.f);
+                    const float s = dcal<DIM>(dx, dy, dz, rinv * rinv, kc);
                     const float w = r2 > 0.f ? shape<KERNEL>(omq) * s : 0.f;
                     rs = fmaf(w, Ca - __int_as_float(q.w), rs);
                     if (COUNT) cnt += in_support_fp64<DIM>(a.x - q.x, a.y - q.y, a.z - q.z, prm);
@@ -568,7 +591,7 @@ __global__ __launch_bounds__(kRateThreads) void k_rate_batch(const uint4 *__rest
             unsigned c = 0u;
             const float rate = rate_direct<DIM, KERNEL, true, COUNT>(Pe, cs + prm.coff, pa, cx, cy, cz, prm, c);
             cnt += c;
-            Acc acc{0.0, 0.f, 0.f, 0u};
+            Acc acc{0.f, 0.f, 0.f, 0.f, 0u};
             epilogue<DIM, EPI>(gi, rate, pa, perm, prm, o, acc);
         }
         __syncthreads();   // sp and s_item are rewritten by the next item
