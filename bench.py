@@ -471,6 +471,7 @@ def run_ours(args):
     plume = WORKLOADS[args.workload]()
     xq, C = plume.initial_state()
     sim = ade.Simulation(ade.params_for(plume), xq, C, device=device)
+    tune_ms = sim.autotune()
     pairs = sim.count_pairs()
     launches = ade.launches_per_step(sim.ctx)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
@@ -551,7 +552,8 @@ def run_ours(args):
         "config": workload_config(plume),
         "grid": {"cell_subdiv": sim.info.cell_subdiv, "cells": sim.info.ncells,
                  "stencil_rows": sim.info.stencil_rows, "sort_passes": sim.info.sort_passes,
-                 "dt": sim.info.dt},
+                 "variant": "tiled" if sim.info.variant == 1 else "direct",
+                 "autotune_best_ms": tune_ms, "dt": sim.info.dt},
         "steps_per_s": 1e3 / ms_per_step * world,
         "interactions_per_step": 2 * pairs,
         "roofline": roofline, "e2e": e2e, "clocks": clk,

@@ -161,6 +161,12 @@ int ade_get_stats(ade_ctx *ctx, ade_stats *stats_host, void *stream);
 int ade_closed_form_error(ade_ctx *ctx, const double *x0_host, double w, double C0,
                           int nimg, double *out_host, void *stream);
 
+/* Autotuner for a context created with cell_subdiv = 0 and flags = 0: times the cell build plus
+ * one evaluation of Eq. 4 for every cell subdivision (1..4 cells per support radius) and both
+ * interaction variants (direct walk, shared-memory tiles), keeps the fastest; results change only
+ * in summation order.  The particle state is not modified; waits; best_ms_host may be NULL. */
+int ade_autotune(ade_ctx *ctx, double *best_ms_host, void *stream);
+
 /* Change alpha_L, alpha_T and D_m (Eq. 3) of a context, keeping its time step, grid and state. */
 int ade_set_dispersivity(ade_ctx *ctx, double alpha_L, double alpha_T, double D_m);
 

@@ -36,7 +36,7 @@ EXPORTS = ("ade_workspace_bytes", "ade_init_particles", "ade_get_info", "ade_bui
            "ade_batch_stats", "ade_batch_count_pairs", "ade_batch_get_plume_info",
            "ade_batch_autotune", "ade_batch_launches_per_step", "ade_batch_destroy",
            "ade_batch_step_timed", "ade_set_dispersivity", "ade_adjoint_workspace_bytes",
-           "ade_adjoint")
+           "ade_adjoint", "ade_autotune")
 NOALLOC_MAX_PARTICLES = 1 << 20
 NOALLOC_MAX_CELLS = 1 << 20
 
@@ -113,6 +113,7 @@ def load():
         "ade_batch_launches_per_step": (I, [P, ctypes.POINTER(I)]),
         "ade_batch_step_timed": (I, [P, ctypes.POINTER(ctypes.c_double), V]),
         "ade_set_dispersivity": (I, [P, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+        "ade_autotune": (I, [P, ctypes.POINTER(ctypes.c_double), V]),
         "ade_adjoint_workspace_bytes": (I, [P, I, I, ctypes.POINTER(SZ)]),
         "ade_adjoint": (I, [P, P, I, I, P, SZ, P, ctypes.POINTER(ctypes.c_double),
                             ctypes.POINTER(ctypes.c_double), P, V]),
@@ -308,6 +309,13 @@ class Simulation:
 
     def closed_form_error(self, x0, w, C0=1.0, nimg=2):
         return closed_form_error(self.ctx, x0, w, C0, nimg, self.stream)
+
+    def autotune(self):
+        """Pick the cell subdivision and interaction variant by timing (ade_autotune)."""
+        ms = ctypes.c_double(0.0)
+        _check(load().ade_autotune(self.ctx, ctypes.byref(ms), self.stream))
+        self.info = get_info(self.ctx)
+        return ms.value
 
     def set_dispersivity(self, alpha_L, alpha_T, D_m):
         _check(load().ade_set_dispersivity(self.ctx, alpha_L, alpha_T, D_m))

@@ -132,6 +132,8 @@ struct ade_ctx {
     int nc[3];
     int ncells;
     int subdiv;
+    int ncells_cap;       // workspace capacity in cells (every grid the autotuner may pick)
+    int partials_cap;     // workspace capacity in reduction partials
     uint32_t *xq;
     float *C;
     void *ws;

@@ -295,6 +295,7 @@ struct Derived {
     double H;
     Grid g;
     int nb_partials;
+    int ncells_cap;
     ade::RateParams tiles;
     Layout L;
 };
@@ -314,7 +315,22 @@ int derive(const ade_params *p, int n, Derived *d)
     int nbt = ade::rate_launch_blocks(p->dim, d->tiles, iso);
     d->nb_partials = nbr > nbc ? nbr : nbc;
     if (nbt > d->nb_partials) d->nb_partials = nbt;
-    d->L = layout(n, d->g.ncells, d->nb_partials);
+    int ncells_cap = d->g.ncells;
+    if (p->cell_subdiv == 0 && p->flags == 0u) {
+        // automatic grid: size the workspace for every configuration the autotuner may pick
+        for (int k = 1; k <= ade::kMaxSubdiv; ++k) {
+            Grid g;
+            if (!make_grid(*p, d->H, k, &g)) continue;
+            ncells_cap = std::max(ncells_cap, g.ncells);
+            ade::RateParams t;
+            memset(&t, 0, sizeof(t));
+            t.n = n;
+            choose_tiles(p->dim, n, g, iso, ADE_FLAG_TILED, &t);
+            d->nb_partials = std::max(d->nb_partials, ade::rate_launch_blocks(p->dim, t, iso));
+        }
+    }
+    d->ncells_cap = ncells_cap;
+    d->L = layout(n, ncells_cap, d->nb_partials);
     return ADE_OK;
 }
 
@@ -522,6 +538,8 @@ int ade_init_particles(ade_ctx **out, const ade_params *p, int n, uint32_t *xq_d
     for (int i = 0; i < 3; ++i) c->nc[i] = d.g.nc[i];
     c->ncells = d.g.ncells;
     c->subdiv = d.g.subdiv;
+    c->ncells_cap = d.ncells_cap;
+    c->partials_cap = d.nb_partials;
     c->xq = xq_dev;
     c->C = C_dev;
     c->ws = workspace_dev;
@@ -549,6 +567,106 @@ int ade_init_particles(ade_ctx **out, const ade_params *p, int n, uint32_t *xq_d
         return rc;
     }
     *out = c;
+    return ADE_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Switch a context to cell subdivision k and kernel variant (tiled or direct); the workspace
+// layout is fixed at init, so only the grid, the stencil and the tile fields change.
+int apply_config(ade_ctx *c, int k, bool tiled)
+{
+    Grid g;
+    if (!make_grid(c->p, c->H, k, &g)) return fail(ADE_ERR_ARG, "subdivision %d does not fit", k);
+    if (g.ncells > c->ncells_cap) return fail(ADE_ERR_CAPACITY, "grid exceeds the workspace");
+    ade::RateParams t;
+    memset(&t, 0, sizeof(t));
+    t.n = c->n;
+    choose_tiles(c->dim, c->n, g, c->iso, tiled ? ADE_FLAG_TILED : ADE_FLAG_DIRECT, &t);
+    if (tiled && t.variant != 1) return fail(ADE_ERR_ARG, "tiles do not fit this grid");
+    if (ade::rate_launch_blocks(c->dim, t, c->iso) > c->partials_cap)
+        return fail(ADE_ERR_CAPACITY, "tiles exceed the workspace");
+    for (int i = 0; i < 3; ++i) c->nc[i] = g.nc[i];
+    c->ncells = g.ncells;
+    c->subdiv = g.subdiv;
+    ade::RateParams &rp = c->rp;
+    rp.ncx = g.nc[0];
+    rp.ncy = g.nc[1];
+    rp.ncz = g.nc[2];
+    rp.nrows = g.nrows;
+    for (int r = 0; r < g.nrows; ++r) rp.rows[r] = g.rows[r];
+    rp.variant = t.variant;
+    rp.k = t.k;
+    rp.tx = t.tx;
+    rp.ty = t.ty;
+    rp.tz = t.tz;
+    rp.ntx = t.ntx;
+    rp.nty = t.nty;
+    rp.ntz = t.ntz;
+    rp.cap = t.cap;
+    if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+    }
+    if (c->graph) {
+        cudaGraphDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return ADE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ade_autotune(ade_ctx *c, double *best_ms_host, void *stream)
+{
+    if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
+    if (c->p.cell_subdiv != 0 || c->p.flags != 0u)
+        return fail(ADE_ERR_STATE, "autotuning needs cell_subdiv = 0 and flags = 0");
+    if (c->n == 0) {
+        if (best_ms_host) *best_ms_host = 0.0;
+        return ADE_OK;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    ADE_CK(cudaEventCreate(&e0));
+    ADE_CK(cudaEventCreate(&e1));
+    double best = 1e30;
+    int best_k = c->subdiv;
+    bool best_tiled = c->rp.variant == 1;
+    int rc = ADE_OK;
+    for (int k = 1; rc == ADE_OK && k <= ade::kMaxSubdiv; ++k)
+        for (int tiled = 0; tiled < 2; ++tiled) {
+            if (apply_config(c, k, tiled != 0) != ADE_OK) continue;
+            double ms = 1e30;
+            for (int rep = 0; rep < 2 && rc == ADE_OK; ++rep) {
+                cudaError_t e = cudaEventRecord(e0, s);
+                if (e == cudaSuccess) rc = enqueue_cells(c, s);
+                if (rc == ADE_OK && e == cudaSuccess)
+                    e = ade::launch_rate(c->dim, c->p.kernel, c->iso, ade::EPI_RATE, c->w.P0, c->w.P0,
+                                         c->w.cell_start, c->w.perm, c->rp, epi_none(), s);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float f = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&f, e0, e1);
+                if (e != cudaSuccess) rc = fail(ADE_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+                ms = std::min(ms, (double)f);
+            }
+            if (rc == ADE_OK && ms < best) {
+                best = ms;
+                best_k = k;
+                best_tiled = tiled != 0;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    rc = apply_config(c, best_k, best_tiled);
+    if (rc) return rc;
+    if (best_ms_host) *best_ms_host = best;
     return ADE_OK;
 }
 

@@ -295,3 +295,20 @@ def test_full_size_3d_sampled(lib, orc):
     assert np.max(np.abs(r[sel] - r_orc)) <= RATE_TOL * np.max(np.abs(r))
     assert pairs == 3000 * 250
     assert sim.count_pairs() == plume.n * 250
+
+
+@pytest.mark.parametrize("name", ["256sq-n28-r100", "3d-32cube-h2", "jitter-100sq"])
+def test_autotune_keeps_state_and_parity(lib, orc, name):
+    plume = CASES[name]()
+    xq, C = plume.initial_state()
+    sim = _sim(lib, plume)
+    ms = sim.autotune()
+    assert ms > 0.0
+    x1, C1 = sim.state()
+    assert np.array_equal(x1, xq) and np.array_equal(C1.view(np.uint32), C.view(np.uint32))
+    r_orc, pairs = _oracle_rate(orc, plume, xq, C)
+    assert _rel(sim.rate().cpu().numpy(), r_orc) <= RATE_TOL
+    assert sim.count_pairs() == pairs
+    sim.step(2)
+    st = sim.stats()
+    assert st.status == 0 and np.isfinite(st.mass)
