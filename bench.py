@@ -558,7 +558,7 @@ def run_ours(args):
         "config": workload_config(plume),
         "grid": {"cell_subdiv": sim.info.cell_subdiv, "cells": sim.info.ncells,
                  "stencil_rows": sim.info.stencil_rows, "sort_passes": sim.info.sort_passes,
-                 "variant": "tiled" if sim.info.variant == 1 else "direct",
+                 "variant": {0: "direct-branch-free", 1: "tiled", 2: "direct-branched"}[sim.info.variant],
                  "autotune_best_ms": tune_ms, "dt": sim.info.dt},
         "steps_per_s": 1e3 / ms_per_step * world,
         "interactions_per_step": 2 * pairs,

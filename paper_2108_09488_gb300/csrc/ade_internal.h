@@ -37,7 +37,8 @@ struct RateParams {
     float dt;        // step length used by the epilogue
     uint32_t inc[3]; // fixed-point position increment used by the epilogue
     uint32_t back[3];// evaluation position minus cell-build position (0, or the half-step drift)
-    int variant;     // 0 = direct walk over global memory, 1 = shared-memory tiles
+    int variant;     // 0 = direct walk (branch-free), 1 = shared-memory tiles, 2 = direct walk
+                     // branching on the support test
     int k;           // halo width in cells (cells per support radius)
     int tx, ty, tz;  // target cells per tile
     int ntx, nty, ntz;  // tiles per axis

@@ -201,8 +201,8 @@ int validate(const ade_params *p, int n)
     if (!isfinite(p->dt) || !isfinite(p->gamma)) return fail(ADE_ERR_ARG, "dt and gamma must be finite");
     if (p->dt_rule != ADE_DT_LAMBDA_MAX && p->dt_rule != ADE_DT_TRACE) return fail(ADE_ERR_ARG, "unknown dt_rule");
     if (p->cell_subdiv < 0 || p->cell_subdiv > ade::kMaxSubdiv) return fail(ADE_ERR_ARG, "cell_subdiv must be 0..4");
-    if ((p->flags & ~(ADE_FLAG_DIRECT | ADE_FLAG_TILED)) != 0u ||
-        p->flags == (ADE_FLAG_DIRECT | ADE_FLAG_TILED))
+    if (p->flags != 0u && p->flags != ADE_FLAG_DIRECT && p->flags != ADE_FLAG_TILED &&
+        p->flags != ADE_FLAG_BRANCHED)
         return fail(ADE_ERR_ARG, "unknown or conflicting flags");
     const double H = p->kernel == ADE_WENDLAND_C2 ? 2.0 * p->h : p->h;
     for (int i = 0; i < p->dim; ++i)
@@ -462,7 +462,7 @@ int plume_constants(const ade_params *p, int n, const Derived &d, double *D, dou
         kc = -(56.0 / 3.0) * B / (H * H);
     }
     rp.pf = (float)(0.5 * (p->mass / p->rho) * kc);
-    rp.variant = d.tiles.variant;
+    rp.variant = d.tiles.variant == 1 ? 1 : (p->flags == ADE_FLAG_BRANCHED ? 2 : 0);
     rp.k = d.tiles.k;
     rp.tx = d.tiles.tx;
     rp.ty = d.tiles.ty;
@@ -576,8 +576,9 @@ namespace {
 
 // Switch a context to cell subdivision k and kernel variant (tiled or direct); the workspace
 // layout is fixed at init, so only the grid, the stencil and the tile fields change.
-int apply_config(ade_ctx *c, int k, bool tiled)
+int apply_config(ade_ctx *c, int k, int variant)
 {
+    const bool tiled = variant == 1;
     Grid g;
     if (!make_grid(c->p, c->H, k, &g)) return fail(ADE_ERR_ARG, "subdivision %d does not fit", k);
     if (g.ncells > c->ncells_cap) return fail(ADE_ERR_CAPACITY, "grid exceeds the workspace");
@@ -597,7 +598,7 @@ int apply_config(ade_ctx *c, int k, bool tiled)
     rp.ncz = g.nc[2];
     rp.nrows = g.nrows;
     for (int r = 0; r < g.nrows; ++r) rp.rows[r] = g.rows[r];
-    rp.variant = t.variant;
+    rp.variant = tiled ? 1 : variant;
     rp.k = t.k;
     rp.tx = t.tx;
     rp.ty = t.ty;
@@ -636,11 +637,11 @@ int ade_autotune(ade_ctx *c, double *best_ms_host, void *stream)
     ADE_CK(cudaEventCreate(&e1));
     double best = 1e30;
     int best_k = c->subdiv;
-    bool best_tiled = c->rp.variant == 1;
+    int best_variant = c->rp.variant;
     int rc = ADE_OK;
     for (int k = 1; rc == ADE_OK && k <= ade::kMaxSubdiv; ++k)
-        for (int tiled = 0; tiled < 2; ++tiled) {
-            if (apply_config(c, k, tiled != 0) != ADE_OK) continue;
+        for (int variant = 0; variant < 3; ++variant) {
+            if (apply_config(c, k, variant) != ADE_OK) continue;
             double ms = 1e30;
             for (int rep = 0; rep < 2 && rc == ADE_OK; ++rep) {
                 cudaError_t e = cudaEventRecord(e0, s);
@@ -658,13 +659,13 @@ int ade_autotune(ade_ctx *c, double *best_ms_host, void *stream)
             if (rc == ADE_OK && ms < best) {
                 best = ms;
                 best_k = k;
-                best_tiled = tiled != 0;
+                best_variant = variant;
             }
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    rc = apply_config(c, best_k, best_tiled);
+    rc = apply_config(c, best_k, best_variant);
     if (rc) return rc;
     if (best_ms_host) *best_ms_host = best;
     return ADE_OK;

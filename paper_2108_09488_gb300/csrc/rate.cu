@@ -102,13 +102,22 @@ __device__ __forceinline__ float dcal(float dx, float dy, float dz, float rinv2,
 // ---------------------------------------------------------------------------------------------
 // direct walk over global memory
 // ---------------------------------------------------------------------------------------------
-template <int DIM, int KERNEL, bool ISO, bool COUNT>
+// One candidate range of the direct walk.  The evaluation is branch-free: outside the support
+// (1 - q) is clamped to 0, so the term is exactly 0; at zero separation (the particle itself, or a
+// coincident particle) rsqrt(0) = inf makes q and s NaN, and IEEE max-num (fmaxf returns the
+// non-NaN operand) turns them into (1 - q) = 0 and s = -FLT_MAX, so the weight is exactly 0 as
+// well.  In-support terms use the same operations as a branched evaluation, so adding the zero
+// terms leaves the sum unchanged.  The pair counter keeps an explicit FP64 test.
+// BF = false keeps the branch on r^2 < H^2 instead: a warp whose lanes all miss skips the term,
+// which pays off when warps are spatially coherent and the stencil is large (3D).
+template <int DIM, int KERNEL, bool ISO, bool COUNT, bool BF>
 __device__ __forceinline__ void pair_range_direct(const uint4 *__restrict__ P, int j0, int j1,
                                                   const uint4 &pa, float Ca, const PairConst &k,
                                                   const RateParams &prm, float &rs, unsigned &cnt)
 {
+#pragma unroll 2
     for (int j = j0; j < j1; ++j) {
-        uint4 pb = __ldg(P + j);
+        const uint4 pb = __ldg(P + j);
         if (COUNT) cnt += in_support_fp64<DIM>((int)(pa.x - pb.x), (int)(pa.y - pb.y), (int)(pa.z - pb.z), prm);
         float dx = (float)(int)(pa.x - pb.x);
         float dy = (float)(int)(pa.y - pb.y);
@@ -120,18 +129,22 @@ __device__ __forceinline__ void pair_range_direct(const uint4 *__restrict__ P, i
         }
         float r2 = fmaf(dx, dx, dy * dy);
         if (DIM == 3) r2 = fmaf(dz, dz, r2);
-        if (r2 < k.H2 && r2 > 0.f) {
-            float rinv = rsqrtf(r2);
-            float r = r2 * rinv;
-            float f = shape<KERNEL>(fmaf(-r, k.invH, 1.f));
-            float s = dcal<DIM>(dx, dy, dz, rinv * rinv, k);
-            rs = fmaf(f * s, Ca - __uint_as_float(pb.w), rs);
+        if (BF) {
+            const float rinv = rsqrtf(r2);
+            const float omq = fmaxf(fmaf(-(r2 * rinv), k.invH, 1.f), 0.f);
+            const float s = fmaxf(dcal<DIM>(dx, dy, dz, rinv * rinv, k), -3.402823466e38f);
+            rs = fmaf(shape<KERNEL>(omq) * s, Ca - __uint_as_float(pb.w), rs);
+        } else if (r2 < k.H2 && r2 > 0.f) {
+            const float rinv = rsqrtf(r2);
+            const float omq = fmaf(-(r2 * rinv), k.invH, 1.f);
+            const float s = dcal<DIM>(dx, dy, dz, rinv * rinv, k);
+            rs = fmaf(shape<KERNEL>(omq) * s, Ca - __uint_as_float(pb.w), rs);
         }
     }
 }
 
 // Eq. 4 at one particle by the direct walk; (cx, cy, cz) is its cell.
-template <int DIM, int KERNEL, bool ISO, bool COUNT>
+template <int DIM, int KERNEL, bool ISO, bool COUNT, bool BF = true>
 __device__ float rate_direct(const uint4 *__restrict__ Pe, const uint32_t *__restrict__ cs,
                              const uint4 &pa, int cx, int cy, int cz, const RateParams &prm,
                              unsigned &cnt)
@@ -169,8 +182,8 @@ __device__ float rate_direct(const uint4 *__restrict__ Pe, const uint32_t *__res
             e0 = __ldg(cs + base + hi);
         }
         float rs = 0.f;
-        pair_range_direct<DIM, KERNEL, ISO, COUNT>(Pe, s0, e0, pa, Ca, kc, prm, rs, cnt);
-        pair_range_direct<DIM, KERNEL, ISO, COUNT>(Pe, s1, e1, pa, Ca, kc, prm, rs, cnt);
+        pair_range_direct<DIM, KERNEL, ISO, COUNT, BF>(Pe, s0, e0, pa, Ca, kc, prm, rs, cnt);
+        pair_range_direct<DIM, KERNEL, ISO, COUNT, BF>(Pe, s1, e1, pa, Ca, kc, prm, rs, cnt);
         neumaier_add(acc, comp, rs);
     }
     return prm.pf * (acc + comp);
@@ -337,7 +350,7 @@ __device__ __forceinline__ void block_finish(Acc acc, const EpiOut &out)
 // ---------------------------------------------------------------------------------------------
 // direct kernel
 // ---------------------------------------------------------------------------------------------
-template <int DIM, int KERNEL, int EPI, bool ISO, bool COUNT>
+template <int DIM, int KERNEL, int EPI, bool ISO, bool COUNT, bool BF>
 __global__ __launch_bounds__(kRateThreads) void k_rate(const uint4 *__restrict__ Pe,
                                                        const uint4 *__restrict__ Pc,
                                                        const uint32_t *__restrict__ cs,
@@ -354,7 +367,7 @@ __global__ __launch_bounds__(kRateThreads) void k_rate(const uint4 *__restrict__
     const int cz = DIM == 3 ? (int)__umulhi(pa.z - prm.back[2], (uint32_t)prm.ncz) : 0;
     Acc acc{0.f, 0.f, __int_as_float(0x7f800000), __int_as_float(0xff800000), 0u};
     unsigned cnt = 0u;
-    const float rate = rate_direct<DIM, KERNEL, ISO, COUNT>(Pe, cs, pa, cx, cy, cz, prm, cnt);
+    const float rate = rate_direct<DIM, KERNEL, ISO, COUNT, BF>(Pe, cs, pa, cx, cy, cz, prm, cnt);
     if (valid) {
         acc.cnt = cnt;
         epilogue<DIM, EPI>(i, rate, pa, perm, prm, out, acc);
@@ -637,10 +650,18 @@ cudaError_t launch_variant(bool iso, const uint4 *Pe, const uint4 *Pc, const uin
         return cudaGetLastError();
     }
     const int blocks = rate_blocks(prm.n);
-    if (iso)
-        k_rate<DIM, KERNEL, EPI, true, COUNT><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
-    else
-        k_rate<DIM, KERNEL, EPI, false, COUNT><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
+    const bool bf = prm.variant != 2;   // 2: branched direct walk
+    if (iso) {
+        if (bf)
+            k_rate<DIM, KERNEL, EPI, true, COUNT, true><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
+        else
+            k_rate<DIM, KERNEL, EPI, true, COUNT, false><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
+    } else {
+        if (bf)
+            k_rate<DIM, KERNEL, EPI, false, COUNT, true><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
+        else
+            k_rate<DIM, KERNEL, EPI, false, COUNT, false><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
+    }
     return cudaGetLastError();
 }
 

@@ -97,7 +97,7 @@ def test_cells_bit_exact_every_subdivision(lib, orc, k):
     assert np.array_equal(perm, perm_o) and np.array_equal(cs, cs_o)
 
 
-VARIANTS = {"tiled": 2, "direct": 1}     # ADE_FLAG_TILED, ADE_FLAG_DIRECT
+VARIANTS = {"tiled": 2, "direct": 1, "branched": 4}   # ADE_FLAG_TILED, _DIRECT, _BRANCHED
 
 
 @pytest.mark.parametrize("variant", sorted(VARIANTS))
@@ -108,6 +108,8 @@ def test_rate_parity(lib, orc, name, variant):
     sim = _sim(lib, plume, flags=VARIANTS[variant])
     if variant == "direct":
         assert sim.info.variant == 0
+    if variant == "branched":
+        assert sim.info.variant == 2
     r_gpu = sim.rate().cpu().numpy()
     r_orc, pairs = _oracle_rate(orc, plume, xq, C)
     assert _rel(r_gpu, r_orc) <= RATE_TOL
