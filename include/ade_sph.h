@@ -73,7 +73,7 @@ typedef struct ade_params {
     double dt;         /* time step; <= 0 selects the rule in dt_rule */
     int dt_rule;       /* ADE_DT_LAMBDA_MAX or ADE_DT_TRACE */
     double dt_coef;    /* coefficient of the rule; <= 0 selects 0.1 (Eq. 10) */
-    int cell_subdiv;   /* cells per support radius along each axis, 1..4; 0 = automatic */
+    int cell_subdiv;   /* cells per support radius along each axis, 1..6; 0 = automatic */
     unsigned flags;    /* 0 (library's choice), ADE_FLAG_DIRECT, ADE_FLAG_TILED or ADE_FLAG_BRANCHED */
 } ade_params;
 
@@ -164,7 +164,7 @@ int ade_closed_form_error(ade_ctx *ctx, const double *x0_host, double w, double 
                           int nimg, double *out_host, void *stream);
 
 /* Autotuner for a context created with cell_subdiv = 0 and flags = 0: times the cell build plus
- * one evaluation of Eq. 4 for every cell subdivision (1..4 cells per support radius) and every
+ * one evaluation of Eq. 4 for every cell subdivision (1..6 cells per support radius) and every
  * interaction variant (branch-free direct walk, branched direct walk, shared-memory tiles), keeps
  * the fastest; results change only in summation order.  The particle state is not modified; waits; best_ms_host may be NULL. */
 int ade_autotune(ade_ctx *ctx, double *best_ms_host, void *stream);
@@ -232,7 +232,7 @@ int ade_batch_count_pairs(ade_batch *b, long long *pairs_host, void *stream);
 int ade_batch_get_plume_info(const ade_batch *b, int plume, ade_info *info_host);
 
 /* Autotuner: times the cell build plus one evaluation of every plume for each cell-subdivision
- * policy (per-plume cost model, or 1..4 cells per support radius), work-item size (64..512
+ * policy (per-plume cost model, or 1..6 cells per support radius), work-item size (64..512
  * particles) and persistent grid size (4, 8, 16 blocks per SM), keeps the fastest and re-plans.
  * Leaves the particle state unchanged; waits; best_ms_host (may be NULL) gets the best time. */
 int ade_batch_autotune(ade_batch *b, double *best_ms_host, void *stream);

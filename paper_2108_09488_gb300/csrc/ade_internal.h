@@ -8,7 +8,7 @@
 
 namespace ade {
 
-constexpr int kMaxSubdiv = 4;                                   // cells per support radius
+constexpr int kMaxSubdiv = 6;                                   // cells per support radius
 constexpr int kMaxRows = (2 * kMaxSubdiv + 1) * (2 * kMaxSubdiv + 1);
 constexpr int kRateThreads = 128;                              // direct variant
 constexpr int kTileThreads = 256;                              // tiled variant

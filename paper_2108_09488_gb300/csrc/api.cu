@@ -200,7 +200,7 @@ int validate(const ade_params *p, int n)
         if (!isfinite(p->v[i])) return fail(ADE_ERR_ARG, "v must be finite");
     if (!isfinite(p->dt) || !isfinite(p->gamma)) return fail(ADE_ERR_ARG, "dt and gamma must be finite");
     if (p->dt_rule != ADE_DT_LAMBDA_MAX && p->dt_rule != ADE_DT_TRACE) return fail(ADE_ERR_ARG, "unknown dt_rule");
-    if (p->cell_subdiv < 0 || p->cell_subdiv > ade::kMaxSubdiv) return fail(ADE_ERR_ARG, "cell_subdiv must be 0..4");
+    if (p->cell_subdiv < 0 || p->cell_subdiv > ade::kMaxSubdiv) return fail(ADE_ERR_ARG, "cell_subdiv must be 0..6");
     if (p->flags != 0u && p->flags != ADE_FLAG_DIRECT && p->flags != ADE_FLAG_TILED &&
         p->flags != ADE_FLAG_BRANCHED)
         return fail(ADE_ERR_ARG, "unknown or conflicting flags");
@@ -979,7 +979,7 @@ struct ade_batch {
     std::vector<int> ncells;
     int NC = 0, NC_max = 0;
     int tile_size = ade::kRateThreads, grid = 0, sms = 0;
-    int subdiv_mode = 0;                  // 0 = per-plume cost model, 1..4 forced where valid
+    int subdiv_mode = 0;                  // 0 = per-plume cost model, 1..6 forced where valid
     std::vector<ade::BatchTile> tiles;
     uint32_t *xq = nullptr;
     float *C = nullptr;
