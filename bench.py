@@ -39,9 +39,13 @@ WORKLOADS = {
     "ladder-256-n28-r10": lambda: inputs.ladder_2d(256, 10),
     "lattice-64-h1.3": inputs.lattice_2d_64,
     "cube-128-h2": inputs.cube_3d_128,
+    "field-1024-n120-r10": lambda: inputs.ladder_2d(1024, 10),   # + per-particle velocity field
     "batched-64": None,          # 64 uneven 2D plumes in one batch (inputs.batched_2d)
     "adjoint-512": None,         # gradient of the misfit: 512^2, 400 steps, checkpoints every 40
 }
+# velocity-field workloads: vmax of the smooth seeded field (inputs.velocity_field, speed 0.1,
+# relative amplitude 0.5, so max |v| ~ 0.17)
+FIELD_VMAX = {"field-1024-n120-r10": 0.2}
 ADJ_THETA = (1e-2, 1e-3, 1e-6)
 ADJ_THETA_STAR = (2e-2, 2e-3, 1e-6)
 ADJ_STEPS, ADJ_CKPT = 400, 40
@@ -58,6 +62,11 @@ UNIT = "interactions/s"
 # (2D: 16, 3D: 22); the derivation is in the design doc.  The ALU roof is
 # SMs x 128 FP32 lanes x clock / I_MIN pairs per second.
 I_MIN = {2: 16, 3: 22}
+# Velocity-field pair term (per-particle D, harmonic means, convective term): minimum FP32-pipe
+# instructions and MUFU operations (rsqrt + one reciprocal per tensor component) per pair; the
+# roof takes the slower of the two pipes (128 FP32 lanes and 16 MUFU lanes per SM).
+FIELD_PIPE_COST = {2: (33, 4), 3: (51, 7)}
+MUFU_LANES_PER_SM = 16
 
 # DRAM bytes per rate launch (read + write, mean of predictor and corrector) from one ncu capture
 # of the current kernels (profiles/k_rate_ladder1024.md, profiles/k_rate_batch_batched64.md).
@@ -156,15 +165,28 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------------------
-def cpu_oracle_rate(plume, xq, C, sample, min_seconds, max_steps=None):
+def field_setup(workload, plume, xq):
+    """(velocity field float32 [dim][n], vmax, plume renamed) of a velocity-field workload, or
+    (None, 0, plume)."""
+    import dataclasses
+    vmax = FIELD_VMAX.get(workload)
+    if vmax is None:
+        return None, 0.0, plume
+    v = inputs.velocity_field(inputs.from_fixed(xq, plume.boxv), plume.boxv)
+    return v, vmax, dataclasses.replace(plume, name=f"{plume.name}-velocity-field-vmax{vmax}")
+
+
+def cpu_oracle_rate(plume, xq, C, sample, min_seconds, max_steps=None, v=None):
     """Time the FP64 oracle: each step evaluates Eq. 4 twice (predictor and corrector
-    evaluation) for a fixed random sample of particles.  Returns (interactions/s, steps, secs)."""
+    evaluation) for a fixed random sample of particles.  Returns (interactions/s, steps, secs).
+    v: per-particle velocities (float32 [dim][n]) of a velocity-field workload."""
     import oracle
     oracle.build()
     x = inputs.from_fixed(xq, plume.boxv)
     Cd = np.asarray(C, dtype=np.float64)
     sel = np.sort(np.random.default_rng(12345).choice(plume.n, min(sample, plume.n), replace=False))
-    args = (plume.velocity, Cd, plume.mass, plume.rho, plume.boxv, plume.kernel, plume.support,
+    vel = plume.velocity if v is None else np.ascontiguousarray(v.T, dtype=np.float64)
+    args = (vel, Cd, plume.mass, plume.rho, plume.boxv, plume.kernel, plume.support,
             plume.dim + 2.0, plume.alpha_L, plume.alpha_T, plume.D_m)
     pairs = 0
     steps = 0
@@ -235,9 +257,10 @@ def run_reference(args):
         return 0
     plume = adjoint_plume() if args.workload == "adjoint-512" else WORKLOADS[args.workload]()
     xq, C = plume.initial_state()
+    v, _, plume = field_setup(args.workload, plume, xq)
     sample = args.cpu_sample
-    cpu_oracle_rate(plume, xq, C, sample, 0.0, max_steps=args.warmup) if args.warmup else None
-    value, steps, secs, ns = cpu_oracle_rate(plume, xq, C, sample, 0.0, max_steps=args.steps)
+    cpu_oracle_rate(plume, xq, C, sample, 0.0, max_steps=args.warmup, v=v) if args.warmup else None
+    value, steps, secs, ns = cpu_oracle_rate(plume, xq, C, sample, 0.0, max_steps=args.steps, v=v)
     cores = os.cpu_count()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -475,7 +498,10 @@ def run_ours(args):
 
     plume = WORKLOADS[args.workload]()
     xq, C = plume.initial_state()
-    sim = ade.Simulation(ade.params_for(plume), xq, C, device=device)
+    v, vmax, plume = field_setup(args.workload, plume, xq)
+    sim = ade.Simulation(ade.params_for(plume, vmax=vmax), xq, C, device=device)
+    if v is not None:
+        sim.set_velocity_field(v)
     tune_ms = sim.autotune()
     pairs = sim.count_pairs()
     launches = ade.launches_per_step(sim.ctx)
@@ -507,14 +533,24 @@ def run_ours(args):
     props = torch.cuda.get_device_properties(device)
     sms = props.multi_processor_count
     f_max = clk.get("sm_max_mhz") or 2070.0
-    peak = sms * FP32_LANES_PER_SM * f_max * 1e6 / I_MIN[plume.dim] / 1e9
+    if v is None:
+        peak = sms * FP32_LANES_PER_SM * f_max * 1e6 / I_MIN[plume.dim] / 1e9
+        basis = (f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {f_max:.0f} MHz / "
+                 f"{I_MIN[plume.dim]} FP32-pipe instructions per pair")
+        kname = "k_rate (predictor + corrector)"
+    else:
+        n32, nmufu = FIELD_PIPE_COST[plume.dim]
+        cyc = max(n32 / FP32_LANES_PER_SM, nmufu / MUFU_LANES_PER_SM)
+        peak = sms * f_max * 1e6 / cyc / 1e9
+        basis = (f"{sms} SMs x {f_max:.0f} MHz / max({n32} FP32-pipe instr / {FP32_LANES_PER_SM} lanes, "
+                 f"{nmufu} MUFU ops / {MUFU_LANES_PER_SM} lanes) per pair")
+        kname = "k_rate_field (predictor + corrector)"
     achieved = pairs / (rate_avg_ms * 1e-3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
                 "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(args.workload),
                 "traffic_unit": "bytes per launch (ncu dram read + write)",
-                "kernel": "k_rate (predictor + corrector)",
-                "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {f_max:.0f} MHz / "
-                              f"{I_MIN[plume.dim]} FP32-pipe instructions per pair",
+                "kernel": kname,
+                "peak_basis": basis,
                 "rate_kernel_ms": rate_avg_ms,
                 "phase_ms_per_step": {k: sum(p[i] for p in phases) / len(phases)
                                       for i, k in enumerate(("cells", "predictor", "corrector", "reduce"))}}
@@ -558,16 +594,17 @@ def run_ours(args):
         "config": workload_config(plume),
         "grid": {"cell_subdiv": sim.info.cell_subdiv, "cells": sim.info.ncells,
                  "stencil_rows": sim.info.stencil_rows, "sort_passes": sim.info.sort_passes,
-                 "variant": {0: "direct-branch-free", 1: "tiled", 2: "direct-branched"}[sim.info.variant],
-                 "autotune_best_ms": tune_ms, "dt": sim.info.dt},
+                 "variant": ("velocity-field-direct" if v is not None else
+                             {0: "direct-branch-free", 1: "tiled", 2: "direct-branched"}[sim.info.variant]),
+                 "autotune_best_ms": tune_ms, "dt": sim.info.dt, "skin": sim.info.skin},
         "steps_per_s": 1e3 / ms_per_step * world,
         "interactions_per_step": 2 * pairs,
         "roofline": roofline, "e2e": e2e, "clocks": clk,
         "gpu_launches": launches * args.steps,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, steps, secs, ns = cpu_oracle_rate(plume, xq, C, args.cpu_sample, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+        cv, steps, secs, ns = cpu_oracle_rate(plume, xq, C, args.cpu_sample, args.cpu_seconds, v=v)
+        line["cpu_baseline"] = {"value": cv, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"Eq. 4 evaluated twice per step on a fixed sample of {ns} "
                                           f"of {plume.n} particles; {steps} steps in {secs:.1f} s"}
     sim.close()

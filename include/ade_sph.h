@@ -75,6 +75,10 @@ typedef struct ade_params {
     double dt_coef;    /* coefficient of the rule; <= 0 selects 0.1 (Eq. 10) */
     int cell_subdiv;   /* cells per support radius along each axis, 1..6; 0 = automatic */
     unsigned flags;    /* 0 (library's choice), ADE_FLAG_DIRECT, ADE_FLAG_TILED or ADE_FLAG_BRANCHED */
+    double vmax;       /* 0: uniform velocity v.  > 0: velocity-field mode -- each particle carries
+                          its own constant velocity (ade_set_velocity_field), |v_a| <= vmax; v is
+                          then unused, the dt rules take |v| = vmax, and the cell grid is sized for
+                          H + dt vmax (see ade_set_velocity_field). */
 } ade_params;
 
 /* FP64 diagnostics of the current state. */
@@ -103,6 +107,7 @@ typedef struct ade_info {
     int tile[3];      /* target cells per tile (tiled variant) */
     int tile_capacity;/* staged particles per tile (tiled variant) */
     size_t workspace_bytes;
+    double skin;      /* velocity-field mode: cell-grid margin dt vmax (+ rounding) added to H */
 } ade_info;
 
 /* Device workspace needed for n particles with parameters p (bytes, 256-byte aligned). */
@@ -149,7 +154,8 @@ int ade_run(ade_ctx *ctx, int nsteps, ade_stats *stats_host, void *stream);
  * (milliseconds).  Used for per-kernel roofline measurements. */
 int ade_step_timed(ade_ctx *ctx, double *phase_ms_host, void *stream);
 
-/* Kernel launches one step enqueues (cell build passes, reorder, two rate launches, reduction). */
+/* Kernel launches one step enqueues (cell build passes, reorder, the velocity-field gather in
+ * velocity-field mode, two rate launches). */
 int ade_launches_per_step(const ade_ctx *ctx, int *launches);
 
 /* FP64 mass, min and max of the current concentrations; waits for the stream. */
@@ -171,6 +177,22 @@ int ade_autotune(ade_ctx *ctx, double *best_ms_host, void *stream);
 
 /* Change alpha_L, alpha_T and D_m (Eq. 3) of a context, keeping its time step, grid and state. */
 int ade_set_dispersivity(ade_ctx *ctx, double alpha_L, double alpha_T, double D_m);
+
+/* ---- Velocity-field mode (heterogeneous flow) -----------------------------------------------
+ * For a context created with vmax > 0.  Each particle a moves with its own constant velocity v_a
+ * (dx_a/dt = v_a, Eq. 1) and carries its own tensor D_a (Eq. 3); the rate of Eq. 4 then has both
+ * terms: the dispersive sum with the per-component harmonic mean of Eq. 5,
+ * K_ij = 4 D_ij,a D_ij,b / (D_ij,a + D_ij,b) (0 where both are 0), and the convective sum
+ * C_a (m/rho) (v_a - v_b) . grad_a W_ab.  Relative positions change during a step, so the cell
+ * list built at the start of a step is sized for H + dt vmax (every pair within H at the half step
+ * is found), while the support test uses H.  Interaction kernel: direct walk (no tiles); the
+ * adjoint, the closed-form error and batches are for the uniform case and return ADE_ERR_STATE /
+ * ADE_ERR_ARG here.
+ *   v_dev [dim][n] float (axis-major, caller order, device): copied into the workspace, so the
+ *   caller may free it on return.  Checks max_a |v_a| <= vmax and that every component is finite
+ *   (ADE_ERR_ARG otherwise; the context then has no field).  Waits for the stream.  Until a field
+ *   is set, rate, pair-count and step calls return ADE_ERR_STATE. */
+int ade_set_velocity_field(ade_ctx *ctx, const float *v_dev, void *stream);
 
 /* ---- Adjoint (dispersivity inversion) ---------------------------------------------------------
  * The paper has no adjoint; it is derived from Eq. 3-5 and Eq. 8-9 for the uniform-velocity case.

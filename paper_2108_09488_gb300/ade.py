@@ -37,7 +37,7 @@ EXPORTS = ("ade_workspace_bytes", "ade_init_particles", "ade_get_info", "ade_bui
            "ade_batch_stats", "ade_batch_count_pairs", "ade_batch_get_plume_info",
            "ade_batch_autotune", "ade_batch_launches_per_step", "ade_batch_destroy",
            "ade_batch_step_timed", "ade_set_dispersivity", "ade_adjoint_workspace_bytes",
-           "ade_adjoint", "ade_autotune")
+           "ade_adjoint", "ade_autotune", "ade_set_velocity_field")
 NOALLOC_MAX_PARTICLES = 1 << 20
 NOALLOC_MAX_CELLS = 1 << 20
 
@@ -54,7 +54,7 @@ class Params(ctypes.Structure):
                 ("D_m", ctypes.c_double), ("v", ctypes.c_double * 3), ("mass", ctypes.c_double),
                 ("rho", ctypes.c_double), ("gamma", ctypes.c_double), ("dt", ctypes.c_double),
                 ("dt_rule", ctypes.c_int), ("dt_coef", ctypes.c_double),
-                ("cell_subdiv", ctypes.c_int), ("flags", ctypes.c_uint)]
+                ("cell_subdiv", ctypes.c_int), ("flags", ctypes.c_uint), ("vmax", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -71,7 +71,8 @@ class Info(ctypes.Structure):
                 ("nc", ctypes.c_int * 3), ("ncells", ctypes.c_int), ("cell_subdiv", ctypes.c_int),
                 ("stencil_rows", ctypes.c_int), ("sort_passes", ctypes.c_int),
                 ("variant", ctypes.c_int), ("tile", ctypes.c_int * 3),
-                ("tile_capacity", ctypes.c_int), ("workspace_bytes", ctypes.c_size_t)]
+                ("tile_capacity", ctypes.c_int), ("workspace_bytes", ctypes.c_size_t),
+                ("skin", ctypes.c_double)]
 
 
 _lib = None
@@ -114,6 +115,7 @@ def load():
         "ade_batch_launches_per_step": (I, [P, ctypes.POINTER(I)]),
         "ade_batch_step_timed": (I, [P, ctypes.POINTER(ctypes.c_double), V]),
         "ade_set_dispersivity": (I, [P, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+        "ade_set_velocity_field": (I, [P, P, V]),
         "ade_autotune": (I, [P, ctypes.POINTER(ctypes.c_double), V]),
         "ade_adjoint_workspace_bytes": (I, [P, I, I, ctypes.POINTER(SZ)]),
         "ade_adjoint": (I, [P, P, I, I, P, SZ, P, ctypes.POINTER(ctypes.c_double),
@@ -137,7 +139,7 @@ def _check(rc):
 
 
 def params(dim, h, alpha_L, alpha_T, D_m, v, mass, rho=1.0, box=1.0, kernel=WENDLAND_C2,
-           gamma=0.0, dt=0.0, dt_rule=DT_LAMBDA_MAX, dt_coef=0.0, cell_subdiv=0, flags=0):
+           gamma=0.0, dt=0.0, dt_rule=DT_LAMBDA_MAX, dt_coef=0.0, cell_subdiv=0, flags=0, vmax=0.0):
     p = Params()
     p.dim = dim
     p.kernel = kernel
@@ -149,6 +151,7 @@ def params(dim, h, alpha_L, alpha_T, D_m, v, mass, rho=1.0, box=1.0, kernel=WEND
     p.h, p.alpha_L, p.alpha_T, p.D_m = h, alpha_L, alpha_T, D_m
     p.mass, p.rho, p.gamma, p.dt = mass, rho, gamma, dt
     p.dt_rule, p.dt_coef, p.cell_subdiv, p.flags = dt_rule, dt_coef, cell_subdiv, flags
+    p.vmax = vmax
     return p
 
 
@@ -320,6 +323,16 @@ class Simulation:
 
     def set_dispersivity(self, alpha_L, alpha_T, D_m):
         _check(load().ade_set_dispersivity(self.ctx, alpha_L, alpha_T, D_m))
+
+    def set_velocity_field(self, v):
+        """Per-particle velocities (float32 [dim][n], caller order) of a context created with
+        vmax > 0 (ade_set_velocity_field); the library keeps its own copy."""
+        t = self.torch
+        vt = t.as_tensor(np.ascontiguousarray(v, dtype=np.float32) if not t.is_tensor(v) else v,
+                         dtype=t.float32, device=self.C.device).contiguous()
+        if tuple(vt.shape) != (self.dim, self.n):
+            raise ValueError(f"velocity field must be [{self.dim}][{self.n}], got {tuple(vt.shape)}")
+        _check(load().ade_set_velocity_field(self.ctx, vt.data_ptr() if self.n else None, self.stream))
 
     def adjoint(self, C_target, nsteps, ckpt_every=40, want_dC0=True, want_final=False):
         """Misfit J = 1/2 |C^N - C*|^2 and its gradients (adjoint of Eq. 8-9, see ade_adjoint).

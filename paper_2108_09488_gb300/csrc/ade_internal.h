@@ -49,6 +49,24 @@ struct RateParams {
     int coff;        // batched plumes: first cell of this plume in the global cell table
 };
 
+// Velocity-field mode: per-particle velocities (Eq. 1) and tensors (Eq. 3).
+struct FieldParams {
+    double aL, aT, Dm;       // Eq. 3 coefficients (the per-particle D is formed in FP64)
+    float gamma;             // Gamma of Eq. 5
+    float pconv;             // (m / rho) kc L_x / 2^32: convective prefactor (x_ab in x-axis units)
+    double inc_scale[3];     // epilogue drift per unit velocity: tau / L_i * 2^32
+    double back_scale[3];    // drift since the cell build per unit velocity: tau_b / L_i * 2^32
+};
+
+// Sorted per-particle field data of velocity-field mode (workspace).
+struct FieldWork {
+    float *v;                // [dim][n] caller-order velocities (copy of the caller's field)
+    float4 *V;               // [n] sorted {vx, vy, vz, 0}
+    float4 *DA;              // [n] sorted {Dxx, Dxy, Dyy, 0} (2D) or {Dxx, Dxy, Dxz, 0} (3D)
+    float4 *DB;              // [n] sorted {Dyy, Dyz, Dzz, 0} (3D only)
+    unsigned *vmax_bits;     // max |v_a| as FP32 bits (ade_set_velocity_field)
+};
+
 // One work item of the batched rate kernel: `count` sorted particles of plume `plume` starting
 // at plume-local sorted index `start`.
 struct BatchTile {
@@ -119,6 +137,14 @@ cudaError_t launch_closed_form_error(int dim, const uint32_t *xq, const float *C
 
 cudaError_t launch_state_stats(const float *C, int n, double *partials, double *stats, cudaStream_t s);
 
+// Velocity-field mode (rate_field.cu).
+cudaError_t launch_field_gather(int dim, const uint32_t *perm, const float *v, int n, const FieldParams &fp,
+                                const FieldWork &fw, cudaStream_t s);
+cudaError_t launch_max_speed(const float *v, int n, int dim, unsigned *out_bits, cudaStream_t s);
+cudaError_t launch_rate_field(int dim, int kernel, int epi, const uint4 *Pe, const uint32_t *cell_start,
+                              const uint32_t *perm, const FieldWork &fw, const RateParams &prm,
+                              const FieldParams &fp, const EpiOut &out, cudaStream_t s);
+
 int rate_blocks(int n);
 int rate_launch_blocks(int dim, const RateParams &prm, bool iso);
 size_t tiled_smem_bytes(int dim, const RateParams &prm);
@@ -156,4 +182,12 @@ struct ade_ctx {
     bool status_cleared;
     cudaEvent_t ev[5];    // per-phase timing events (created on first timed step)
     bool ev_ready;
+    // velocity-field mode (p.vmax > 0)
+    bool field;
+    bool field_set;       // a valid field has been copied in
+    double Hgrid;         // radius the cell grid is built for: H, or H + skin in field mode
+    double skin;
+    double vscale[3];     // dt / L_i * 2^32: fixed-point drift per unit velocity over one step
+    ade::FieldParams fp;  // constants (scales set per use)
+    ade::FieldWork fw;
 };

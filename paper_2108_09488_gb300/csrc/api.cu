@@ -90,6 +90,33 @@ double lambda_max(int dim, const double *Din)
     return m;
 }
 
+// Time step: p->dt when positive, else coef h^2 / den with den = lambda_max(D) or tr D (Eq. 10).
+// In velocity-field mode D varies per particle; den is then the largest value the rule takes over
+// |v| <= vmax: lambda_max = max(aL, aT) vmax + Dm, tr D = (aL + (dim - 1) aT) vmax + dim Dm.
+int time_step(const ade_params *p, const double *D, double *dt_out)
+{
+    double dt = p->dt;
+    if (!(dt > 0.0)) {
+        const double coef = p->dt_coef > 0.0 ? p->dt_coef : 0.1;
+        double den;
+        if (p->vmax > 0.0) {
+            if (p->dt_rule == ADE_DT_TRACE)
+                den = (p->alpha_L + (p->dim - 1) * p->alpha_T) * p->vmax + p->dim * p->D_m;
+            else
+                den = fmax(p->alpha_L, p->alpha_T) * p->vmax + p->D_m;
+        } else if (p->dt_rule == ADE_DT_TRACE) {
+            den = 0.0;
+            for (int i = 0; i < p->dim; ++i) den += D[i * p->dim + i];
+        } else {
+            den = lambda_max(p->dim, D);
+        }
+        if (!(den > 0.0)) return fail(ADE_ERR_ARG, "dispersion tensor is zero: give dt explicitly");
+        dt = coef * p->h * p->h / den;
+    }
+    *dt_out = dt;
+    return ADE_OK;
+}
+
 // Neighbour-cell stencil for cells of side s[] and support H: every row (dy, dz) whose cells can
 // hold a point within H of a point in the centre cell, with the x half-width w of that row.
 // Two cells offset by o are at least sum_i (max(|o_i| - 1, 0) s_i)^2 apart (squared).
@@ -204,6 +231,9 @@ int validate(const ade_params *p, int n)
     if (p->flags != 0u && p->flags != ADE_FLAG_DIRECT && p->flags != ADE_FLAG_TILED &&
         p->flags != ADE_FLAG_BRANCHED)
         return fail(ADE_ERR_ARG, "unknown or conflicting flags");
+    if (!(p->vmax >= 0.0) || !isfinite(p->vmax)) return fail(ADE_ERR_ARG, "vmax must be finite and >= 0");
+    if (p->vmax > 0.0 && p->flags != 0u && p->flags != ADE_FLAG_DIRECT)
+        return fail(ADE_ERR_ARG, "velocity-field mode uses the direct walk: flags must be 0 or ADE_FLAG_DIRECT");
     const double H = p->kernel == ADE_WENDLAND_C2 ? 2.0 * p->h : p->h;
     for (int i = 0; i < p->dim; ++i)
         if (!(H < 0.5 * p->box[i])) return fail(ADE_ERR_ARG, "support radius must be < box/2 (minimum image)");
@@ -260,10 +290,11 @@ void choose_tiles(int dim, int n, const Grid &g, bool iso, unsigned flags, ade::
 
 struct Layout {
     size_t keys, rank, count, block_sums, perm_tmp, perm, cell_start, P0, P1, partials, stats,
-        cf_partials, status, done, pairs, total;
+        cf_partials, status, done, pairs, fv, fV, fDA, fDB, fbits, total;
 };
 
-Layout layout(int n, int ncells, int nb_partials)
+// field_dim: 0 for a uniform velocity, else dim (velocity-field buffers are added at the end).
+Layout layout(int n, int ncells, int nb_partials, int field_dim = 0)
 {
     Layout L;
     size_t off = 0;
@@ -287,12 +318,24 @@ Layout layout(int n, int ncells, int nb_partials)
     L.status = take(64);
     L.done = take(64);
     L.pairs = take(64);
+    L.fv = L.fV = L.fDA = L.fDB = L.fbits = 0;
+    if (field_dim) {
+        L.fv = take((size_t)field_dim * n * 4);
+        L.fV = take((size_t)n * 16);
+        L.fDA = take((size_t)n * 16);
+        L.fDB = take(field_dim == 3 ? (size_t)n * 16 : 16);
+        L.fbits = take(64);
+    }
     L.total = off;
     return L;
 }
 
 struct Derived {
     double H;
+    double dt;
+    double D[9];     // Eq. 3 for the uniform velocity p->v
+    double skin;     // velocity-field mode: relative drift allowance of the cell grid
+    double Hgrid;    // radius the grid and stencil are built for: H + skin
     Grid g;
     int nb_partials;
     int ncells_cap;
@@ -305,9 +348,22 @@ int derive(const ade_params *p, int n, Derived *d)
     int rc = validate(p, n);
     if (rc) return rc;
     d->H = p->kernel == ADE_WENDLAND_C2 ? 2.0 * p->h : p->h;
-    rc = choose_grid(*p, d->H, n, &d->g);
+    dispersion_tensor(p->dim, p->v, p->alpha_L, p->alpha_T, p->D_m, d->D);
+    rc = time_step(p, d->D, &d->dt);
     if (rc) return rc;
-    const bool iso = p->box[1] == p->box[0] && (p->dim == 2 || p->box[2] == p->box[0]);
+    d->skin = 0.0;
+    if (p->vmax > 0.0) {
+        // relative drift up to the half step, |v_a - v_b| dt / 2 <= vmax dt, plus the rounding of
+        // two fixed-point increments per axis
+        double umax = 0.0;
+        for (int i = 0; i < p->dim; ++i) umax = fmax(umax, p->box[i] / kTwo32);
+        d->skin = p->vmax * d->dt + 4.0 * umax;
+    }
+    d->Hgrid = d->H + d->skin;
+    rc = choose_grid(*p, d->Hgrid, n, &d->g);
+    if (rc) return rc;
+    // tiles are for the uniform-velocity kernel in a cubic box
+    const bool iso = p->box[1] == p->box[0] && (p->dim == 2 || p->box[2] == p->box[0]) && !(p->vmax > 0.0);
     memset(&d->tiles, 0, sizeof(d->tiles));
     d->tiles.n = n;
     choose_tiles(p->dim, n, d->g, iso, p->flags, &d->tiles);
@@ -320,7 +376,7 @@ int derive(const ade_params *p, int n, Derived *d)
         // automatic grid: size the workspace for every configuration the autotuner may pick
         for (int k = 1; k <= ade::kMaxSubdiv; ++k) {
             Grid g;
-            if (!make_grid(*p, d->H, k, &g)) continue;
+            if (!make_grid(*p, d->Hgrid, k, &g)) continue;
             ncells_cap = std::max(ncells_cap, g.ncells);
             ade::RateParams t;
             memset(&t, 0, sizeof(t));
@@ -330,7 +386,7 @@ int derive(const ade_params *p, int n, Derived *d)
         }
     }
     d->ncells_cap = ncells_cap;
-    d->L = layout(n, ncells_cap, d->nb_partials);
+    d->L = layout(n, ncells_cap, d->nb_partials, p->vmax > 0.0 ? p->dim : 0);
     return ADE_OK;
 }
 
@@ -341,10 +397,20 @@ uint32_t fixed_increment(double v, double dt, double L)
     return (uint32_t)w;
 }
 
-// Enqueue one cell build.
+// Velocity-field mode needs a field before any evaluation.
+int need_field(const ade_ctx *c)
+{
+    if (c->field && !c->field_set) return fail(ADE_ERR_STATE, "velocity-field mode: call ade_set_velocity_field first");
+    return ADE_OK;
+}
+
+// Enqueue one cell build; in velocity-field mode followed by the gather of the sorted v and D.
 int enqueue_cells(ade_ctx *c, cudaStream_t s)
 {
+    int rc = need_field(c);
+    if (rc) return rc;
     ADE_CK(ade::launch_build_cells(c->dim, c->xq, c->C, c->n, c->nc, c->ncells, c->w, s));
+    if (c->field) ADE_CK(ade::launch_field_gather(c->dim, c->w.perm, c->fw.v, c->n, c->fp, c->fw, s));
     return ADE_OK;
 }
 
@@ -355,40 +421,60 @@ ade::EpiOut epi_none()
     return o;
 }
 
-// Enqueue one predictor-corrector step (Eq. 8-9).
-int enqueue_step(ade_ctx *c, cudaStream_t s)
+enum Phase { AT_BUILD = 0, PREDICTOR = 1, CORRECTOR = 2 };
+
+// One rate evaluation on the last cell build.  AT_BUILD: the state of the build (rate or pair
+// count).  PREDICTOR: C^{l+1/2} = C^l + dt/2 r^l, x^{l+1/2} = x^l + dt/2 v.  CORRECTOR:
+// C^{l+1} = C^l + dt r^{l+1/2}, x^{l+1} = x^l + dt v, evaluated at the half-step state P1.
+int enqueue_eval(ade_ctx *c, Phase ph, ade::EpiOut out, cudaStream_t s)
 {
-    int rc = enqueue_cells(c, s);
-    if (rc) return rc;
-    if (c->n == 0) return ADE_OK;
-    const uint32_t *perm = c->w.perm;
+    const int epi = ph == PREDICTOR ? ade::EPI_PREDICT : (ph == CORRECTOR ? ade::EPI_CORRECT : ade::EPI_RATE);
+    const uint4 *Pe = ph == CORRECTOR ? c->w.P1 : c->w.P0;
     ade::RateParams rp = c->rp;
+    rp.dt = ph == PREDICTOR ? (float)(0.5 * c->dt) : (ph == CORRECTOR ? (float)c->dt : 0.f);
+    for (int i = 0; i < 3; ++i) {
+        rp.inc[i] = ph == PREDICTOR ? c->inc_half[i] : (ph == CORRECTOR ? c->inc[i] : 0u);
+        rp.back[i] = ph == CORRECTOR ? c->inc_half[i] : 0u;
+    }
+    if (c->field) {
+        ade::FieldParams fp = c->fp;
+        for (int i = 0; i < 3; ++i) {
+            const double full = c->vscale[i], half = 0.5 * c->vscale[i];
+            fp.inc_scale[i] = ph == PREDICTOR ? half : (ph == CORRECTOR ? full : 0.0);
+            fp.back_scale[i] = ph == CORRECTOR ? half : 0.0;
+        }
+        ADE_CK(ade::launch_rate_field(c->dim, c->p.kernel, epi, Pe, c->w.cell_start, c->w.perm, c->fw, rp, fp,
+                                      out, s));
+        return ADE_OK;
+    }
+    ADE_CK(ade::launch_rate(c->dim, c->p.kernel, c->iso, epi, Pe, c->w.P0, c->w.cell_start, c->w.perm, rp,
+                            out, s));
+    return ADE_OK;
+}
+
+ade::EpiOut epi_corrector(ade_ctx *c)
+{
     ade::EpiOut out = epi_none();
-    // predictor: C^{l+1/2} = C^l + dt/2 r^l, x^{l+1/2} = x^l + dt/2 v
-    rp.dt = (float)(0.5 * c->dt);
-    for (int i = 0; i < 3; ++i) {
-        rp.inc[i] = c->inc_half[i];
-        rp.back[i] = 0u;
-    }
-    out.Pout = c->w.P1;
-    ADE_CK(ade::launch_rate(c->dim, c->p.kernel, c->iso, ade::EPI_PREDICT, c->w.P0, c->w.P0, c->w.cell_start,
-                            perm, rp, out, s));
-    // corrector: C^{l+1} = C^l + dt r^{l+1/2}, x^{l+1} = x^l + dt v
-    rp.dt = (float)c->dt;
-    for (int i = 0; i < 3; ++i) {
-        rp.inc[i] = c->inc[i];
-        rp.back[i] = c->inc_half[i];
-    }
-    out = epi_none();
     out.xq = c->xq;
     out.C = c->C;
     out.partials = c->w.partials;
     out.stats = c->w.stats;
     out.done = c->w.done;
     out.status = c->w.status;
-    ADE_CK(ade::launch_rate(c->dim, c->p.kernel, c->iso, ade::EPI_CORRECT, c->w.P1, c->w.P0, c->w.cell_start,
-                            perm, rp, out, s));
-    return ADE_OK;
+    return out;
+}
+
+// Enqueue one predictor-corrector step (Eq. 8-9).
+int enqueue_step(ade_ctx *c, cudaStream_t s)
+{
+    int rc = enqueue_cells(c, s);
+    if (rc) return rc;
+    if (c->n == 0) return ADE_OK;
+    ade::EpiOut out = epi_none();
+    out.Pout = c->w.P1;
+    rc = enqueue_eval(c, PREDICTOR, out, s);
+    if (rc) return rc;
+    return enqueue_eval(c, CORRECTOR, epi_corrector(c), s);
 }
 
 // The workspace arrives uninitialised: clear the status word once, before the first step.
@@ -402,27 +488,43 @@ int clear_status_once(ade_ctx *c, cudaStream_t s)
     return ADE_OK;
 }
 
+// kc of W'(r)/r = kc f(q) for support H: Wendland C2 (support 2h, f = (1-q)^3) kc = -20 B / H^2;
+// Wendland C4 (Eq. 7, support h, f = (1-q)^5 (1+5q)) kc = -(56/3) B / H^2; B the normalisation.
+double kernel_kc(int kernel, int dm, double H)
+{
+    if (kernel == ADE_WENDLAND_C2) {
+        const double B = dm == 2 ? 7.0 / (kPi * H * H) : 21.0 / (2.0 * kPi * H * H * H);
+        return -20.0 * B / (H * H);
+    }
+    const double B = dm == 2 ? 9.0 / (kPi * H * H) : 495.0 / (32.0 * kPi * H * H * H);
+    return -(56.0 / 3.0) * B / (H * H);
+}
+
+// Velocity-field constants: Eq. 3 coefficients for the per-particle tensors, Gamma, the convective
+// prefactor (m/rho) kc L_x/2^32 (x_ab in fixed-point units of the x axis) and the fixed-point
+// drift per unit velocity over one step, dt / L_i 2^32.
+void field_constants(ade_ctx *c)
+{
+    const ade_params &p = c->p;
+    ade::FieldParams &fp = c->fp;
+    memset(&fp, 0, sizeof(fp));
+    fp.aL = p.alpha_L;
+    fp.aT = p.alpha_T;
+    fp.Dm = p.D_m;
+    fp.gamma = (float)(p.gamma > 0.0 ? p.gamma : p.dim + 2.0);
+    fp.pconv = (float)((p.mass / p.rho) * kernel_kc(p.kernel, p.dim, c->H) * (p.box[0] / kTwo32));
+    for (int i = 0; i < 3; ++i) c->vscale[i] = i < p.dim ? c->dt / p.box[i] * kTwo32 : 0.0;
+}
+
 // Per-plume constants: Eq. 3 (D), the time step (Eq. 10 or the largest-eigenvalue rule), the
 // fixed-point drift per step and half step, and the interaction constants of Eq. 4-5 / Eq. 7 in
 // fixed-point units of the x axis.
 int plume_constants(const ade_params *p, int n, const Derived &d, double *D, double *dt_out,
                     uint32_t *inc, uint32_t *inc_half, ade::RateParams *rp_out, bool *iso)
 {
-    // Eq. 3 and the time step
-    dispersion_tensor(p->dim, p->v, p->alpha_L, p->alpha_T, p->D_m, D);
-    double dt = p->dt;
-    if (!(dt > 0.0)) {
-        double coef = p->dt_coef > 0.0 ? p->dt_coef : 0.1;
-        double den;
-        if (p->dt_rule == ADE_DT_TRACE) {
-            den = 0.0;
-            for (int i = 0; i < p->dim; ++i) den += D[i * p->dim + i];
-        } else {
-            den = lambda_max(p->dim, D);
-        }
-        if (!(den > 0.0)) return fail(ADE_ERR_ARG, "dispersion tensor is zero: give dt explicitly");
-        dt = coef * p->h * p->h / den;
-    }
+    // Eq. 3 and the time step (from derive)
+    for (int i = 0; i < 9; ++i) D[i] = d.D[i];
+    const double dt = d.dt;
     *dt_out = dt;
     for (int i = 0; i < 3; ++i) {
         double L = i < p->dim ? p->box[i] : 1.0;
@@ -452,16 +554,7 @@ int plume_constants(const ade_params *p, int n, const Derived &d, double *D, dou
     const double gamma = p->gamma > 0.0 ? p->gamma : p->dim + 2.0;
     const int dm = p->dim;
     ade::pair_coeffs(dm, gamma, D, rp.Kc, &rp.c0);
-    const double H = d.H;
-    double B, kc;
-    if (p->kernel == ADE_WENDLAND_C2) {
-        B = dm == 2 ? 7.0 / (kPi * H * H) : 21.0 / (2.0 * kPi * H * H * H);
-        kc = -20.0 * B / (H * H);
-    } else {
-        B = dm == 2 ? 9.0 / (kPi * H * H) : 495.0 / (32.0 * kPi * H * H * H);
-        kc = -(56.0 / 3.0) * B / (H * H);
-    }
-    rp.pf = (float)(0.5 * (p->mass / p->rho) * kc);
+    rp.pf = (float)(0.5 * (p->mass / p->rho) * kernel_kc(p->kernel, dm, d.H));
     rp.variant = d.tiles.variant == 1 ? 1 : (p->flags == ADE_FLAG_BRANCHED ? 2 : 0);
     rp.k = d.tiles.k;
     rp.tx = d.tiles.tx;
@@ -566,6 +659,19 @@ int ade_init_particles(ade_ctx **out, const ade_params *p, int n, uint32_t *xq_d
         delete c;
         return rc;
     }
+    c->Hgrid = d.Hgrid;
+    c->skin = d.skin;
+    c->field = p->vmax > 0.0;
+    if (c->field) {
+        c->iso = false;
+        c->fw.v = at<float>(workspace_dev, d.L.fv);
+        c->fw.V = at<float4>(workspace_dev, d.L.fV);
+        c->fw.DA = at<float4>(workspace_dev, d.L.fDA);
+        c->fw.DB = at<float4>(workspace_dev, d.L.fDB);
+        c->fw.vmax_bits = at<unsigned>(workspace_dev, d.L.fbits);
+        field_constants(c);
+        c->field_set = n == 0;
+    }
     *out = c;
     return ADE_OK;
 }
@@ -580,7 +686,7 @@ int apply_config(ade_ctx *c, int k, int variant)
 {
     const bool tiled = variant == 1;
     Grid g;
-    if (!make_grid(c->p, c->H, k, &g)) return fail(ADE_ERR_ARG, "subdivision %d does not fit", k);
+    if (!make_grid(c->p, c->Hgrid, k, &g)) return fail(ADE_ERR_ARG, "subdivision %d does not fit", k);
     if (g.ncells > c->ncells_cap) return fail(ADE_ERR_CAPACITY, "grid exceeds the workspace");
     ade::RateParams t;
     memset(&t, 0, sizeof(t));
@@ -641,14 +747,14 @@ int ade_autotune(ade_ctx *c, double *best_ms_host, void *stream)
     int rc = ADE_OK;
     for (int k = 1; rc == ADE_OK && k <= ade::kMaxSubdiv; ++k)
         for (int variant = 0; variant < 3; ++variant) {
+            if (c->field && variant != 0) continue;  // one interaction kernel in velocity-field mode
             if (apply_config(c, k, variant) != ADE_OK) continue;
             double ms = 1e30;
             for (int rep = 0; rep < 2 && rc == ADE_OK; ++rep) {
                 cudaError_t e = cudaEventRecord(e0, s);
                 if (e == cudaSuccess) rc = enqueue_cells(c, s);
-                if (rc == ADE_OK && e == cudaSuccess)
-                    e = ade::launch_rate(c->dim, c->p.kernel, c->iso, ade::EPI_RATE, c->w.P0, c->w.P0,
-                                         c->w.cell_start, c->w.perm, c->rp, epi_none(), s);
+                if (rc == ADE_OK && e == cudaSuccess) rc = enqueue_eval(c, AT_BUILD, epi_none(), s);
+                if (rc != ADE_OK) break;
                 if (e == cudaSuccess) e = cudaEventRecord(e1, s);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 float f = 0.f;
@@ -671,6 +777,31 @@ int ade_autotune(ade_ctx *c, double *best_ms_host, void *stream)
     return ADE_OK;
 }
 
+int ade_set_velocity_field(ade_ctx *c, const float *v_dev, void *stream)
+{
+    if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
+    if (!c->field) return fail(ADE_ERR_STATE, "context was created with vmax = 0 (uniform velocity)");
+    if (c->n > 0 && !v_dev) return fail(ADE_ERR_ARG, "v_dev is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    c->field_set = false;
+    if (c->n == 0) {
+        c->field_set = true;
+        return ADE_OK;
+    }
+    ADE_CK(cudaMemcpyAsync(c->fw.v, v_dev, (size_t)c->dim * c->n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    ADE_CK(ade::launch_max_speed(c->fw.v, c->n, c->dim, c->fw.vmax_bits, s));
+    unsigned bits = 0;
+    ADE_CK(cudaMemcpyAsync(&bits, c->fw.vmax_bits, sizeof(bits), cudaMemcpyDeviceToHost, s));
+    ADE_CK(cudaStreamSynchronize(s));
+    float smax;
+    memcpy(&smax, &bits, sizeof(smax));
+    if (!((double)smax <= c->p.vmax))
+        return fail(ADE_ERR_ARG, "velocity field: max |v| = %g exceeds vmax = %g (or is not finite)", (double)smax,
+                    c->p.vmax);
+    c->field_set = true;
+    return ADE_OK;
+}
+
 int ade_set_dispersivity(ade_ctx *c, double alpha_L, double alpha_T, double D_m)
 {
     if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
@@ -683,6 +814,11 @@ int ade_set_dispersivity(ade_ctx *c, double alpha_L, double alpha_T, double D_m)
     dispersion_tensor(c->dim, c->p.v, alpha_L, alpha_T, D_m, c->D);
     const double gamma = c->p.gamma > 0.0 ? c->p.gamma : c->dim + 2.0;
     ade::pair_coeffs(c->dim, gamma, c->D, c->rp.Kc, &c->rp.c0);
+    if (c->field) {
+        c->fp.aL = alpha_L;
+        c->fp.aT = alpha_T;
+        c->fp.Dm = D_m;
+    }
     if (c->graph_exec) {
         cudaGraphExecDestroy(c->graph_exec);
         c->graph_exec = nullptr;
@@ -712,6 +848,7 @@ int ade_get_info(const ade_ctx *c, ade_info *info)
     info->tile[2] = c->rp.tz;
     info->tile_capacity = c->rp.cap;
     info->workspace_bytes = c->ws_bytes;
+    info->skin = c->skin;
     return ADE_OK;
 }
 
@@ -742,9 +879,7 @@ int ade_dispersion_rate(ade_ctx *c, float *dCdt_dev, void *stream)
     if (rc || c->n == 0) return rc;
     ade::EpiOut out = epi_none();
     out.rate = dCdt_dev;
-    ADE_CK(ade::launch_rate(c->dim, c->p.kernel, c->iso, ade::EPI_RATE, c->w.P0, c->w.P0, c->w.cell_start,
-                            c->w.perm, c->rp, out, s));
-    return ADE_OK;
+    return enqueue_eval(c, AT_BUILD, out, s);
 }
 
 int ade_count_pairs(ade_ctx *c, long long *pairs_host, void *stream)
@@ -757,8 +892,8 @@ int ade_count_pairs(ade_ctx *c, long long *pairs_host, void *stream)
     ADE_CK(cudaMemsetAsync(c->w.pairs, 0, 8, s));
     ade::EpiOut out = epi_none();
     out.pairs = c->w.pairs;
-    ADE_CK(ade::launch_rate(c->dim, c->p.kernel, c->iso, ade::EPI_RATE, c->w.P0, c->w.P0, c->w.cell_start,
-                            c->w.perm, c->rp, out, s));
+    rc = enqueue_eval(c, AT_BUILD, out, s);
+    if (rc) return rc;
     unsigned long long v = 0;
     ADE_CK(cudaMemcpyAsync(&v, c->w.pairs, 8, cudaMemcpyDeviceToHost, s));
     ADE_CK(cudaStreamSynchronize(s));
@@ -771,6 +906,7 @@ int ade_step(ade_ctx *c, int nsteps, void *stream)
 {
     if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
     if (nsteps < 0) return fail(ADE_ERR_ARG, "nsteps must be >= 0");
+    if (need_field(c)) return ADE_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
     int rc0 = clear_status_once(c, s);
     if (rc0) return rc0;
@@ -809,6 +945,7 @@ int ade_run(ade_ctx *c, int nsteps, ade_stats *st, void *stream)
 {
     if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
     if (nsteps < 0) return fail(ADE_ERR_ARG, "nsteps must be >= 0");
+    if (need_field(c)) return ADE_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
     int rc0 = clear_status_once(c, s);
     if (rc0) return rc0;
@@ -841,6 +978,7 @@ int ade_run(ade_ctx *c, int nsteps, ade_stats *st, void *stream)
 int ade_step_timed(ade_ctx *c, double *phase_ms, void *stream)
 {
     if (!c || !phase_ms) return fail(ADE_ERR_ARG, "NULL argument");
+    if (need_field(c)) return ADE_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
     int rc = clear_status_once(c, s);
     if (rc) return rc;
@@ -853,32 +991,13 @@ int ade_step_timed(ade_ctx *c, double *phase_ms, void *stream)
     if (rc) return rc;
     ADE_CK(cudaEventRecord(c->ev[1], s));
     if (c->n > 0) {
-        const uint32_t *perm = c->w.perm;
-        ade::RateParams rp = c->rp;
         ade::EpiOut out = epi_none();
-        rp.dt = (float)(0.5 * c->dt);
-        for (int i = 0; i < 3; ++i) {
-            rp.inc[i] = c->inc_half[i];
-            rp.back[i] = 0u;
-        }
         out.Pout = c->w.P1;
-        ADE_CK(ade::launch_rate(c->dim, c->p.kernel, c->iso, ade::EPI_PREDICT, c->w.P0, c->w.P0,
-                                c->w.cell_start, perm, rp, out, s));
+        rc = enqueue_eval(c, PREDICTOR, out, s);
+        if (rc) return rc;
         ADE_CK(cudaEventRecord(c->ev[2], s));
-        rp.dt = (float)c->dt;
-        for (int i = 0; i < 3; ++i) {
-            rp.inc[i] = c->inc[i];
-            rp.back[i] = c->inc_half[i];
-        }
-        out = epi_none();
-        out.xq = c->xq;
-        out.C = c->C;
-        out.partials = c->w.partials;
-        out.stats = c->w.stats;
-        out.done = c->w.done;
-        out.status = c->w.status;
-        ADE_CK(ade::launch_rate(c->dim, c->p.kernel, c->iso, ade::EPI_CORRECT, c->w.P1, c->w.P0,
-                                c->w.cell_start, perm, rp, out, s));
+        rc = enqueue_eval(c, CORRECTOR, epi_corrector(c), s);
+        if (rc) return rc;
         ADE_CK(cudaEventRecord(c->ev[3], s));
     } else {
         ADE_CK(cudaEventRecord(c->ev[2], s));
@@ -899,8 +1018,9 @@ int ade_step_timed(ade_ctx *c, double *phase_ms, void *stream)
 int ade_launches_per_step(const ade_ctx *c, int *launches)
 {
     if (!c || !launches) return fail(ADE_ERR_ARG, "NULL argument");
-    // count, 3 scan launches, place, order, predictor, corrector (the memset is not a kernel)
-    *launches = c->n > 0 ? 8 : 4;
+    // count, 3 scan launches, place, order, [velocity-field gather,] predictor, corrector (the
+    // memset is not a kernel)
+    *launches = c->n > 0 ? 8 + (c->field ? 1 : 0) : 4;
     return ADE_OK;
 }
 
@@ -909,6 +1029,7 @@ int ade_closed_form_error(ade_ctx *c, const double *x0, double w, double C0, int
 {
     if (!c || !x0 || !outh) return fail(ADE_ERR_ARG, "NULL argument");
     if (!(w > 0.0) || nimg < 0 || nimg > 8) return fail(ADE_ERR_ARG, "need w > 0 and 0 <= nimg <= 8");
+    if (c->field) return fail(ADE_ERR_STATE, "the closed form of Eq. 12-13 is for a uniform velocity");
     cudaStream_t s = (cudaStream_t)stream;
     const int dm = c->dim;
     double center[3] = {0, 0, 0}, box[3] = {1, 1, 1};
@@ -1052,6 +1173,7 @@ int batch_validate(int P, const ade_params *p, const int *n)
             return fail(ADE_ERR_ARG, "all plumes of a batch need the same dim and kernel");
         if (!(p[i].box[1] == p[i].box[0] && (p[i].dim == 2 || p[i].box[2] == p[i].box[0])))
             return fail(ADE_ERR_ARG, "batched plumes need a cubic box (equal sides)");
+        if (p[i].vmax > 0.0) return fail(ADE_ERR_ARG, "batched plumes have a uniform velocity (vmax must be 0)");
         N += n[i];
     }
     if (N > (1ll << 28)) return fail(ADE_ERR_ARG, "total particles exceed 2^28");

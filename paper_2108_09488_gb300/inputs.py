@@ -179,3 +179,38 @@ def batched_2d(nplumes=64, seed=20210821, steps=500, side_lo=32, side_hi=512):
         out.append(Plume(dim=2, side=side, h_over_dx=h_dx, alpha_T=1e-3, alpha_L=1e-3 * ratio,
                          angle=angle, steps=steps, name=f"batch{p}-{side}^2"))
     return out
+
+
+def velocity_field(x, box, speed=0.1, amplitude=0.5, modes=3, seed=2108):
+    """Seeded smooth, periodic, non-uniform velocity field at positions x [n][dim] (float32
+    [dim][n], axis-major like the positions): a uniform drift of the given speed along the
+    diagonal plus `modes` random Fourier modes per component with relative amplitude `amplitude`
+    (it has a nonzero divergence, so the convective term of Eq. 4 is exercised)."""
+    x = np.asarray(x, dtype=np.float64)
+    box = np.asarray(box, dtype=np.float64)
+    n, dim = x.shape
+    rng = np.random.Generator(np.random.PCG64(seed))
+    u = x / box[None, :dim]
+    v = np.zeros((dim, n))
+    base = speed / math.sqrt(dim)
+    for d in range(dim):
+        v[d] = base
+        for _ in range(modes):
+            k = rng.integers(-2, 3, size=dim)
+            if not np.any(k):
+                k[d] = 1
+            a = rng.uniform(-1.0, 1.0) * amplitude * base
+            ph = rng.uniform(0.0, 2.0 * math.pi)
+            v[d] += a * np.sin(2.0 * math.pi * (u @ k) + ph)
+    return np.ascontiguousarray(v.astype(np.float32))
+
+
+def velocity_noise(n, dim, vmax, seed=7):
+    """Seeded white-noise velocity field (float32 [dim][n]): independent directions, speeds
+    uniform in [0, vmax).  Neighbours move apart at up to 2 vmax, the case the cell-grid skin of
+    velocity-field mode has to cover."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    d = rng.standard_normal((dim, n))
+    d /= np.maximum(np.linalg.norm(d, axis=0), 1e-30)
+    s = rng.uniform(0.0, vmax, size=n) * (1.0 - 1e-6)
+    return np.ascontiguousarray((d * s).astype(np.float32))

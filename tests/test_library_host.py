@@ -134,3 +134,74 @@ def test_batch_workspace_and_validation(adelib):
     with pytest.raises(adelib.AdeError) as e:
         adelib.batch_workspace_bytes(bad, ns[:2] + [16 ** 3] + ns[3:])
     assert e.value.code == -1
+
+
+def _field_plume():
+    return inputs.Plume(dim=2, side=96, h_over_dx=1.9, jitter=0.3, seed=11)
+
+
+@pytest.mark.parametrize("rule", ["lambda_max", "trace"])
+def test_velocity_field_mode_time_step_skin_and_grid(adelib, orc, rule):
+    """vmax > 0: the dt rule takes the largest tensor any |v| <= vmax gives (the oracle's rule on
+    D(v) for |v| = vmax), and the grid is built for H + dt vmax (+ 4 fixed-point units)."""
+    plume = _field_plume()
+    vmax = 0.25
+    code = adelib.DT_LAMBDA_MAX if rule == "lambda_max" else adelib.DT_TRACE
+    p = adelib.params_for(plume, vmax=vmax, dt_rule=code)
+    ctx, nbytes = _ctx(adelib, p, plume.n)
+    try:
+        info = adelib.get_info(ctx)
+        D = orc.dispersion_tensor([vmax, 0.0], plume.alpha_L, plume.alpha_T, plume.D_m)
+        dt = orc.dt_rule(D, plume.h, rule)
+        assert info.dt == pytest.approx(dt, rel=1e-14)
+        assert info.skin == pytest.approx(vmax * dt + 4.0 / 2 ** 32, rel=1e-14)
+        k = info.cell_subdiv
+        assert info.nc[0] == math.floor(k / (info.support + info.skin))
+        assert info.variant == 0
+        assert adelib.launches_per_step(ctx) == 9
+        assert nbytes >= (40 + 32) * plume.n   # v, sorted V and D (2D) + the two sorted states
+    finally:
+        adelib.destroy(ctx)
+
+
+@pytest.mark.parametrize("bad", [dict(vmax=-1.0), dict(vmax=float("inf")), dict(vmax=0.2, flags=2),
+                                 dict(vmax=0.2, flags=4), dict(vmax=0.2, dt=3.0)])
+def test_velocity_field_mode_invalid(adelib, bad):
+    """Negative or infinite vmax, the tiled or branched kernels, and a skin so wide that the grid
+    cannot hold the stencil are rejected before any device work."""
+    plume = _field_plume()
+    with pytest.raises(adelib.AdeError) as e:
+        adelib.workspace_bytes(adelib.params_for(plume, **bad), plume.n)
+    assert e.value.code == -1
+
+
+def test_velocity_field_mode_call_order(adelib):
+    """Calls that need a field fail with ADE_ERR_STATE until one is set; the uniform-only calls
+    (closed form, adjoint, batches) refuse field mode; a uniform context refuses a field."""
+    import ctypes
+    plume = _field_plume()
+    lib = adelib.load()
+    ctx, _ = _ctx(adelib, adelib.params_for(plume, vmax=0.2), plume.n)
+    try:
+        for call in (lambda: adelib.build_cells(ctx), lambda: adelib.dispersion_rate(ctx, FAKE),
+                     lambda: adelib.count_pairs(ctx), lambda: adelib.step(ctx, 1),
+                     lambda: adelib.closed_form_error(ctx, [0.3, 0.3], 0.05)):
+            with pytest.raises(adelib.AdeError) as e:
+                call()
+            assert e.value.code == -6
+        g = (ctypes.c_double * 3)()
+        J = ctypes.c_double(0.0)
+        rc = lib.ade_adjoint(ctx, FAKE, 4, 2, FAKE, 1 << 40, None, g, ctypes.byref(J), None, None)
+        assert rc == -6
+    finally:
+        adelib.destroy(ctx)
+    ctx, _ = _ctx(adelib, adelib.params_for(plume), plume.n)
+    try:
+        assert lib.ade_set_velocity_field(ctx, FAKE, None) == -6
+    finally:
+        adelib.destroy(ctx)
+    plumes = inputs.batched_2d(nplumes=2, side_lo=16, side_hi=32)
+    with pytest.raises(adelib.AdeError) as e:
+        adelib.batch_workspace_bytes([adelib.params_for(q, vmax=0.2) for q in plumes],
+                                     [q.n for q in plumes])
+    assert e.value.code == -1
