@@ -58,12 +58,14 @@ struct FieldParams {
     double back_scale[3];    // drift since the cell build per unit velocity: tau_b / L_i * 2^32
 };
 
-// Sorted per-particle field data of velocity-field mode (workspace).
+// Per-particle field records of velocity-field mode (workspace).  v is constant in time, so the
+// records are formed once per field (or dispersivity change) in the caller's order and only
+// permuted into the cell-sorted order after each cell build:
+//   2D: V = {vx, vy, 0, 0},          DA = {Dxx, Dxy, Dyy, lo(Dxy)}
+//   3D: V = {vx, vy, vz, lo(Dxz)},   DA = {Dxx, Dxy, Dxz, lo(Dxy)}, DB = {Dyy, Dyz, Dzz, lo(Dyz)}
 struct FieldWork {
-    float *v;                // [dim][n] caller-order velocities (copy of the caller's field)
-    float4 *V;               // [n] sorted {vx, vy, vz, 0}
-    float4 *DA;              // [n] sorted {Dxx, Dxy, Dyy, 0} (2D) or {Dxx, Dxy, Dxz, 0} (3D)
-    float4 *DB;              // [n] sorted {Dyy, Dyz, Dzz, 0} (3D only)
+    float4 *Vc, *DAc, *DBc;  // [n] caller order (DBc: 3D only)
+    float4 *V, *DA, *DB;     // [n] cell-sorted order
     unsigned *vmax_bits;     // max |v_a| as FP32 bits (ade_set_velocity_field)
 };
 
@@ -138,9 +140,12 @@ cudaError_t launch_closed_form_error(int dim, const uint32_t *xq, const float *C
 cudaError_t launch_state_stats(const float *C, int n, double *partials, double *stats, cudaStream_t s);
 
 // Velocity-field mode (rate_field.cu).
-cudaError_t launch_field_gather(int dim, const uint32_t *perm, const float *v, int n, const FieldParams &fp,
-                                const FieldWork &fw, cudaStream_t s);
-cudaError_t launch_max_speed(const float *v, int n, int dim, unsigned *out_bits, cudaStream_t s);
+// Caller-order records from v [dim][n] (vx, vy, vz into Vc; v_dev may be NULL to re-form the
+// tensors from the velocities already in Vc), and max |v| into fw.vmax_bits when v_dev is given.
+cudaError_t launch_field_records(int dim, const float *v_dev, int n, const FieldParams &fp, const FieldWork &fw,
+                                 cudaStream_t s);
+// Sorted records: V[i] = Vc[perm[i]] (and DA, DB).
+cudaError_t launch_field_permute(int dim, const uint32_t *perm, int n, const FieldWork &fw, cudaStream_t s);
 cudaError_t launch_rate_field(int dim, int kernel, int epi, const uint4 *Pe, const uint32_t *cell_start,
                               const uint32_t *perm, const FieldWork &fw, const RateParams &prm,
                               const FieldParams &fp, const EpiOut &out, cudaStream_t s);
@@ -185,6 +190,7 @@ struct ade_ctx {
     // velocity-field mode (p.vmax > 0)
     bool field;
     bool field_set;       // a valid field has been copied in
+    bool field_dirty;     // tensors must be re-formed (dispersivities changed)
     double Hgrid;         // radius the cell grid is built for: H, or H + skin in field mode
     double skin;
     double vscale[3];     // dt / L_i * 2^32: fixed-point drift per unit velocity over one step

@@ -290,7 +290,7 @@ void choose_tiles(int dim, int n, const Grid &g, bool iso, unsigned flags, ade::
 
 struct Layout {
     size_t keys, rank, count, block_sums, perm_tmp, perm, cell_start, P0, P1, partials, stats,
-        cf_partials, status, done, pairs, fv, fV, fDA, fDB, fbits, total;
+        cf_partials, status, done, pairs, fVc, fDAc, fDBc, fV, fDA, fDB, fbits, total;
 };
 
 // field_dim: 0 for a uniform velocity, else dim (velocity-field buffers are added at the end).
@@ -318,12 +318,15 @@ Layout layout(int n, int ncells, int nb_partials, int field_dim = 0)
     L.status = take(64);
     L.done = take(64);
     L.pairs = take(64);
-    L.fv = L.fV = L.fDA = L.fDB = L.fbits = 0;
+    L.fVc = L.fDAc = L.fDBc = L.fV = L.fDA = L.fDB = L.fbits = 0;
     if (field_dim) {
-        L.fv = take((size_t)field_dim * n * 4);
-        L.fV = take((size_t)n * 16);
-        L.fDA = take((size_t)n * 16);
-        L.fDB = take(field_dim == 3 ? (size_t)n * 16 : 16);
+        const size_t rec = (size_t)n * 16, rec3 = field_dim == 3 ? (size_t)n * 16 : 16;
+        L.fVc = take(rec);
+        L.fDAc = take(rec);
+        L.fDBc = take(rec3);
+        L.fV = take(rec);
+        L.fDA = take(rec);
+        L.fDB = take(rec3);
         L.fbits = take(64);
     }
     L.total = off;
@@ -404,13 +407,27 @@ int need_field(const ade_ctx *c)
     return ADE_OK;
 }
 
-// Enqueue one cell build; in velocity-field mode followed by the gather of the sorted v and D.
+// Re-form the caller-order tensor records after a dispersivity change (not inside a capture:
+// ade_run calls this before capturing).
+int refresh_field(ade_ctx *c, cudaStream_t s)
+{
+    if (c->field && c->field_set && c->field_dirty) {
+        ADE_CK(ade::launch_field_records(c->dim, nullptr, c->n, c->fp, c->fw, s));
+        c->field_dirty = false;
+    }
+    return ADE_OK;
+}
+
+// Enqueue one cell build; in velocity-field mode followed by the permutation of the v and D
+// records into the sorted order.
 int enqueue_cells(ade_ctx *c, cudaStream_t s)
 {
     int rc = need_field(c);
     if (rc) return rc;
+    rc = refresh_field(c, s);
+    if (rc) return rc;
     ADE_CK(ade::launch_build_cells(c->dim, c->xq, c->C, c->n, c->nc, c->ncells, c->w, s));
-    if (c->field) ADE_CK(ade::launch_field_gather(c->dim, c->w.perm, c->fw.v, c->n, c->fp, c->fw, s));
+    if (c->field) ADE_CK(ade::launch_field_permute(c->dim, c->w.perm, c->n, c->fw, s));
     return ADE_OK;
 }
 
@@ -664,7 +681,9 @@ int ade_init_particles(ade_ctx **out, const ade_params *p, int n, uint32_t *xq_d
     c->field = p->vmax > 0.0;
     if (c->field) {
         c->iso = false;
-        c->fw.v = at<float>(workspace_dev, d.L.fv);
+        c->fw.Vc = at<float4>(workspace_dev, d.L.fVc);
+        c->fw.DAc = at<float4>(workspace_dev, d.L.fDAc);
+        c->fw.DBc = at<float4>(workspace_dev, d.L.fDBc);
         c->fw.V = at<float4>(workspace_dev, d.L.fV);
         c->fw.DA = at<float4>(workspace_dev, d.L.fDA);
         c->fw.DB = at<float4>(workspace_dev, d.L.fDB);
@@ -788,8 +807,7 @@ int ade_set_velocity_field(ade_ctx *c, const float *v_dev, void *stream)
         c->field_set = true;
         return ADE_OK;
     }
-    ADE_CK(cudaMemcpyAsync(c->fw.v, v_dev, (size_t)c->dim * c->n * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    ADE_CK(ade::launch_max_speed(c->fw.v, c->n, c->dim, c->fw.vmax_bits, s));
+    ADE_CK(ade::launch_field_records(c->dim, v_dev, c->n, c->fp, c->fw, s));
     unsigned bits = 0;
     ADE_CK(cudaMemcpyAsync(&bits, c->fw.vmax_bits, sizeof(bits), cudaMemcpyDeviceToHost, s));
     ADE_CK(cudaStreamSynchronize(s));
@@ -799,6 +817,7 @@ int ade_set_velocity_field(ade_ctx *c, const float *v_dev, void *stream)
         return fail(ADE_ERR_ARG, "velocity field: max |v| = %g exceeds vmax = %g (or is not finite)", (double)smax,
                     c->p.vmax);
     c->field_set = true;
+    c->field_dirty = false;
     return ADE_OK;
 }
 
@@ -818,6 +837,7 @@ int ade_set_dispersivity(ade_ctx *c, double alpha_L, double alpha_T, double D_m)
         c->fp.aL = alpha_L;
         c->fp.aT = alpha_T;
         c->fp.Dm = D_m;
+        c->field_dirty = true;   // tensors re-formed on the caller's stream before the next use
     }
     if (c->graph_exec) {
         cudaGraphExecDestroy(c->graph_exec);
@@ -948,6 +968,8 @@ int ade_run(ade_ctx *c, int nsteps, ade_stats *st, void *stream)
     if (need_field(c)) return ADE_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
     int rc0 = clear_status_once(c, s);
+    if (rc0) return rc0;
+    rc0 = refresh_field(c, s);
     if (rc0) return rc0;
     if (!c->graph_exec && nsteps > 0) {
         if (!c->cap_stream) ADE_CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));

@@ -13,8 +13,9 @@
 // test uses H.  One thread per cell-sorted particle walks the stencil rows of its build-time
 // cell as in the direct kernel; the row sums of both terms are added with Neumaier compensation
 // in a fixed order, so results are deterministic.
-// Sorted copies of v and D (computed once per cell build by k_field_gather) keep the pair loop's
-// loads contiguous: candidates of a row are consecutive sorted indices.
+// Records of v and D are formed once per field in the caller's order (v is constant in time) and
+// permuted into the cell-sorted order after every cell build (k_field_permute), so the pair
+// loop's loads stay contiguous: candidates of a row are consecutive sorted indices.
 //
 // Conditioning of Eq. 5.  Diagonal components of D (Eq. 3) are never negative, but off-diagonal
 // ones take the sign of v_i v_j, so for neighbours whose velocities point into different quadrants
@@ -34,18 +35,30 @@ namespace {
 
 constexpr int kT = kRateThreads;
 
-// Harmonic-mean component of Eq. 5 for a diagonal entry (both >= 0: no cancellation).
-__device__ __forceinline__ float hmean(float a, float b)
+// Approximate reciprocal (MUFU, about 1 ulp; subnormal input and output flushed to zero).
+__device__ __forceinline__ float rcp_approx(float x)
 {
-    const float den = a + b;
-    return den != 0.f ? __fdividef(4.f * a * b, den) : 0.f;
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
-// Off-diagonal entry given as hi + lo pairs (see the conditioning note above).
-__device__ __forceinline__ float hmean2(float ah, float al, float bh, float bl)
+// Harmonic-mean component of Eq. 5 for a diagonal entry, with a4 = 4 a precomputed per particle.
+// a, b >= 0, so a + b = 0 only when 4ab = 0 too: clamping the denominator to the smallest normal
+// number returns K = 0 there without a branch.
+__device__ __forceinline__ float hmean_diag(float a, float a4, float b)
+{
+    return (a4 * b) * rcp_approx(fmaxf(a + b, 1.17549435e-38f));
+}
+
+// Twice an off-diagonal component, 2 K_ij, from hi + lo pairs (see the conditioning note above),
+// with a8 = 8 a_hi precomputed per particle.  A zero denominator gives K_ij = 0 as in Eq. 5's
+// convention; denominators below the smallest normal number count as zero.
+__device__ __forceinline__ float hmean_off2(float ah, float a8, float al, float bh, float bl)
 {
     const float den = (ah + bh) + (al + bl);
-    return den != 0.f ? __fdividef(4.f * ah * bh, den) : 0.f;
+    const float k2 = (a8 * bh) * rcp_approx(den);
+    return fabsf(den) >= 1.17549435e-38f ? k2 : 0.f;
 }
 
 // Fixed-point drift round(v tau / L_i 2^32) mod 2^32 of one particle, per axis (FP64: one
@@ -58,19 +71,35 @@ __device__ __forceinline__ void drift(const float4 &v, const double scale[3], ui
     out[2] = DIM == 3 ? (uint32_t)(unsigned long long)__double2ll_rn((double)v.z * scale[2]) : 0u;
 }
 
-// Sorted velocity and dispersion tensor (Eq. 3, FP64) of every particle, in the cell-sorted order:
-//   2D: V = {vx, vy, 0, 0},     DA = {Dxx, Dxy, Dyy, lo(Dxy)}
-//   3D: V = {vx, vy, vz, lo(Dxz)}, DA = {Dxx, Dxy, Dxz, lo(Dxy)}, DB = {Dyy, Dyz, Dzz, lo(Dyz)}
+// Velocities of the caller's field into the caller-order records (fourth lane cleared) and
+// max_a |v_a| as FP32 bits (non-negative floats order like their bit patterns); a non-finite speed
+// counts as +inf so that the host check rejects it.
 template <int DIM>
-__global__ __launch_bounds__(kT) void k_field_gather(const uint32_t *__restrict__ perm, const float *__restrict__ v,
-                                                     int n, FieldParams fp, float4 *__restrict__ V,
-                                                     float4 *__restrict__ DA, float4 *__restrict__ DB)
+__global__ __launch_bounds__(kT) void k_field_velocity(const float *__restrict__ v, int n, float4 *__restrict__ Vc,
+                                                       unsigned *__restrict__ out_bits)
+{
+    const int i = blockIdx.x * kT + threadIdx.x;
+    float s = 0.f;
+    if (i < n) {
+        const float a = v[i], b = v[(size_t)n + i], c = DIM == 3 ? v[2 * (size_t)n + i] : 0.f;
+        Vc[i] = make_float4(a, b, c, 0.f);
+        s = sqrtf(a * a + b * b + c * c);
+        if (!(s <= 3.0e38f)) s = __int_as_float(0x7f800000);
+    }
+    for (int o = 16; o > 0; o >>= 1) s = fmaxf(s, __shfl_down_sync(0xffffffffu, s, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out_bits, __float_as_uint(s));
+}
+
+// Dispersion tensor (Eq. 3) of every particle in FP64 from its velocity, stored as the records
+// described in ade_internal.h (caller order).
+template <int DIM>
+__global__ __launch_bounds__(kT) void k_field_tensors(int n, FieldParams fp, float4 *__restrict__ Vc,
+                                                      float4 *__restrict__ DAc, float4 *__restrict__ DBc)
 {
     const int i = blockIdx.x * kT + threadIdx.x;
     if (i >= n) return;
-    const uint32_t a = __ldg(perm + i);
-    const float vf[3] = {__ldg(v + a), __ldg(v + (size_t)n + a), DIM == 3 ? __ldg(v + 2 * (size_t)n + a) : 0.f};
-    const double vv[3] = {vf[0], vf[1], vf[2]};
+    const float4 vr = Vc[i];
+    const double vv[3] = {vr.x, vr.y, DIM == 3 ? (double)vr.z : 0.0};
     const double s = sqrt(vv[0] * vv[0] + vv[1] * vv[1] + vv[2] * vv[2]);
     const double iso = fp.aT * s + fp.Dm;
     const double g = s > 0.0 ? (fp.aL - fp.aT) / s : 0.0;
@@ -78,30 +107,28 @@ __global__ __launch_bounds__(kT) void k_field_gather(const uint32_t *__restrict_
     auto lo = [](double d) { return (float)(d - (double)(float)d); };
     const double dxx = iso + g * (vv[0] * vv[0]), dxy = g * (vv[0] * vv[1]), dyy = iso + g * (vv[1] * vv[1]);
     if (DIM == 2) {
-        V[i] = make_float4(vf[0], vf[1], 0.f, 0.f);
-        DA[i] = make_float4(hi(dxx), hi(dxy), hi(dyy), lo(dxy));
+        DAc[i] = make_float4(hi(dxx), hi(dxy), hi(dyy), lo(dxy));
     } else {
         const double dxz = g * (vv[0] * vv[2]), dyz = g * (vv[1] * vv[2]), dzz = iso + g * (vv[2] * vv[2]);
-        V[i] = make_float4(vf[0], vf[1], vf[2], lo(dxz));
-        DA[i] = make_float4(hi(dxx), hi(dxy), hi(dxz), lo(dxy));
-        DB[i] = make_float4(hi(dyy), hi(dyz), hi(dzz), lo(dyz));
+        Vc[i].w = lo(dxz);
+        DAc[i] = make_float4(hi(dxx), hi(dxy), hi(dxz), lo(dxy));
+        DBc[i] = make_float4(hi(dyy), hi(dyz), hi(dzz), lo(dyz));
     }
 }
 
-// max_a |v_a| as FP32 bits (non-negative floats order like their bit patterns); a non-finite
-// speed counts as +inf so that the host check rejects it.
-__global__ __launch_bounds__(kT) void k_max_speed(const float *__restrict__ v, int n, int dim,
-                                                  unsigned *__restrict__ out_bits)
+// Sorted records after a cell build.
+template <int DIM>
+__global__ __launch_bounds__(kT) void k_field_permute(const uint32_t *__restrict__ perm, int n,
+                                                      const float4 *__restrict__ Vc, const float4 *__restrict__ DAc,
+                                                      const float4 *__restrict__ DBc, float4 *__restrict__ V,
+                                                      float4 *__restrict__ DA, float4 *__restrict__ DB)
 {
     const int i = blockIdx.x * kT + threadIdx.x;
-    float s = 0.f;
-    if (i < n) {
-        const float a = v[i], b = v[(size_t)n + i], c = dim == 3 ? v[2 * (size_t)n + i] : 0.f;
-        s = sqrtf(a * a + b * b + c * c);
-        if (!(s <= 3.0e38f)) s = __int_as_float(0x7f800000);
-    }
-    for (int o = 16; o > 0; o >>= 1) s = fmaxf(s, __shfl_down_sync(0xffffffffu, s, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out_bits, __float_as_uint(s));
+    if (i >= n) return;
+    const uint32_t a = __ldg(perm + i);
+    V[i] = __ldg(Vc + a);
+    DA[i] = __ldg(DAc + a);
+    if (DIM == 3) DB[i] = __ldg(DBc + a);
 }
 
 template <int DIM, int KERNEL, int EPI, bool COUNT>
@@ -130,6 +157,10 @@ __global__ __launch_bounds__(kT) void k_rate_field(const uint4 *__restrict__ Pe,
     }
     const float Ca = __uint_as_float(pa.w);
     const float H2 = prm.H2, invH = prm.invH, sy = prm.sy, sz = prm.sz, gam = fp.gamma;
+    // 4 D (diagonal) and 8 D (off-diagonal) of this particle for the harmonic means
+    // (da.z is Dyy in 2D, Dxz in 3D)
+    const float4 da4 = make_float4(4.f * da.x, 8.f * da.y, (DIM == 2 ? 4.f : 8.f) * da.z, 0.f);
+    const float4 db4 = make_float4(4.f * db.x, 8.f * db.y, 4.f * db.z, 0.f);
     float sd = 0.f, cd = 0.f, sc = 0.f, cc = 0.f;
     unsigned cnt = 0u;
     for (int ri = 0; ri < prm.nrows; ++ri) {
@@ -163,6 +194,7 @@ __global__ __launch_bounds__(kT) void k_rate_field(const uint4 *__restrict__ Pe,
         }
         float rd = 0.f, rc = 0.f;
         for (int piece = 0; piece < 2; ++piece)
+#pragma unroll 2
             for (int j = r0[piece]; j < r1[piece]; ++j) {
                 const uint4 pb = __ldg(Pe + j);
                 const int ix = (int)(pa.x - pb.x), iy = (int)(pa.y - pb.y), iz = (int)(pa.z - pb.z);
@@ -187,18 +219,21 @@ __global__ __launch_bounds__(kT) void k_rate_field(const uint4 *__restrict__ Pe,
                     const float4 d1 = __ldg(DA + j);
                     float Q, tr;
                     if (DIM == 2) {
-                        const float kxx = hmean(da.x, d1.x), kxy = hmean2(da.y, da.w, d1.y, d1.w);
-                        const float kyy = hmean(da.z, d1.z);
-                        Q = fmaf(dx, fmaf(kxx, dx, 2.f * kxy * dy), kyy * dy * dy);
+                        const float kxx = hmean_diag(da.x, da4.x, d1.x);
+                        const float kxy2 = hmean_off2(da.y, da4.y, da.w, d1.y, d1.w);
+                        const float kyy = hmean_diag(da.z, da4.z, d1.z);
+                        Q = fmaf(dx, fmaf(kxx, dx, kxy2 * dy), kyy * dy * dy);
                         tr = kxx + kyy;
                     } else {
                         const float4 d2 = __ldg(DB + j);
-                        const float kxx = hmean(da.x, d1.x), kxy = hmean2(da.y, da.w, d1.y, d1.w);
-                        const float kxz = hmean2(da.z, va.w, d1.z, vb.w);
-                        const float kyy = hmean(db.x, d2.x), kyz = hmean2(db.y, db.w, d2.y, d2.w);
-                        const float kzz = hmean(db.z, d2.z);
-                        const float qx = fmaf(kxx, dx, fmaf(2.f * kxy, dy, 2.f * kxz * dz));
-                        const float qy = fmaf(kyy, dy, 2.f * kyz * dz);
+                        const float kxx = hmean_diag(da.x, da4.x, d1.x);
+                        const float kxy2 = hmean_off2(da.y, da4.y, da.w, d1.y, d1.w);
+                        const float kxz2 = hmean_off2(da.z, da4.z, va.w, d1.z, vb.w);
+                        const float kyy = hmean_diag(db.x, db4.x, d2.x);
+                        const float kyz2 = hmean_off2(db.y, db4.y, db.w, d2.y, d2.w);
+                        const float kzz = hmean_diag(db.z, db4.z, d2.z);
+                        const float qx = fmaf(kxx, dx, fmaf(kxy2, dy, kxz2 * dz));
+                        const float qy = fmaf(kyy, dy, kyz2 * dz);
                         Q = fmaf(dx, qx, fmaf(dy, qy, kzz * dz * dz));
                         tr = kxx + kyy + kzz;
                     }
@@ -288,23 +323,33 @@ void launch_field_count(bool count, int epi, int blocks, const uint4 *Pe, const 
 
 }  // namespace
 
-cudaError_t launch_field_gather(int dim, const uint32_t *perm, const float *v, int n, const FieldParams &fp,
-                                const FieldWork &fw, cudaStream_t s)
+cudaError_t launch_field_records(int dim, const float *v_dev, int n, const FieldParams &fp, const FieldWork &fw,
+                                 cudaStream_t s)
+{
+    if (v_dev) {
+        cudaError_t e = cudaMemsetAsync(fw.vmax_bits, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+    }
+    if (n == 0) return cudaSuccess;
+    const int blocks = (n + kT - 1) / kT;
+    if (dim == 2) {
+        if (v_dev) k_field_velocity<2><<<blocks, kT, 0, s>>>(v_dev, n, fw.Vc, fw.vmax_bits);
+        k_field_tensors<2><<<blocks, kT, 0, s>>>(n, fp, fw.Vc, fw.DAc, fw.DBc);
+    } else {
+        if (v_dev) k_field_velocity<3><<<blocks, kT, 0, s>>>(v_dev, n, fw.Vc, fw.vmax_bits);
+        k_field_tensors<3><<<blocks, kT, 0, s>>>(n, fp, fw.Vc, fw.DAc, fw.DBc);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_permute(int dim, const uint32_t *perm, int n, const FieldWork &fw, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
     const int blocks = (n + kT - 1) / kT;
     if (dim == 2)
-        k_field_gather<2><<<blocks, kT, 0, s>>>(perm, v, n, fp, fw.V, fw.DA, fw.DB);
+        k_field_permute<2><<<blocks, kT, 0, s>>>(perm, n, fw.Vc, fw.DAc, fw.DBc, fw.V, fw.DA, fw.DB);
     else
-        k_field_gather<3><<<blocks, kT, 0, s>>>(perm, v, n, fp, fw.V, fw.DA, fw.DB);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_max_speed(const float *v, int n, int dim, unsigned *out_bits, cudaStream_t s)
-{
-    cudaError_t e = cudaMemsetAsync(out_bits, 0, sizeof(unsigned), s);
-    if (e != cudaSuccess || n == 0) return e;
-    k_max_speed<<<(n + kT - 1) / kT, kT, 0, s>>>(v, n, dim, out_bits);
+        k_field_permute<3><<<blocks, kT, 0, s>>>(perm, n, fw.Vc, fw.DAc, fw.DBc, fw.V, fw.DA, fw.DB);
     return cudaGetLastError();
 }
 

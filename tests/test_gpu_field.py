@@ -184,6 +184,27 @@ def test_field_autotune_keeps_state_and_parity(lib, orc):
     assert sim.count_pairs() == pairs
 
 
+def test_field_set_dispersivity_reforms_tensors(lib, orc):
+    """ade_set_dispersivity in field mode: the per-particle tensors are re-formed before the next
+    evaluation, for single calls and for a run whose graph is captured afterwards."""
+    import dataclasses
+    plume, xq, C, v, sim = _setup(lib, "3d-24-c2-smooth")
+    sim.run(1)
+    new = dataclasses.replace(plume, alpha_L=3e-2, alpha_T=2e-3, D_m=1e-5)
+    sim.set_dispersivity(new.alpha_L, new.alpha_T, new.D_m)
+    xq1, C1 = sim.state()
+    r, _ = orc.rate(inputs.from_fixed(xq1, plume.boxv), *_oracle_args(new, v, C1))
+    assert _rel(sim.rate().cpu().numpy(), r) <= RATE_TOL
+    ref = _setup(lib, "3d-24-c2-smooth")[4]
+    ref.run(1)
+    ref.set_dispersivity(new.alpha_L, new.alpha_T, new.D_m)
+    ref.step(2)
+    sim.run(2)
+    xa, Ca = sim.state()
+    xb, Cb = ref.state()
+    assert np.array_equal(xa, xb) and np.array_equal(Ca.view(np.uint32), Cb.view(np.uint32))
+
+
 def test_field_rejects_fast_or_nonfinite_velocities(lib):
     plume, xq, C, v, sim = _setup(lib, "2d-96-c2-smooth")
     fast = v.copy()

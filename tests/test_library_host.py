@@ -159,7 +159,7 @@ def test_velocity_field_mode_time_step_skin_and_grid(adelib, orc, rule):
         assert info.nc[0] == math.floor(k / (info.support + info.skin))
         assert info.variant == 0
         assert adelib.launches_per_step(ctx) == 9
-        assert nbytes >= (40 + 32) * plume.n   # v, sorted V and D (2D) + the two sorted states
+        assert nbytes >= (64 + 32) * plume.n   # caller-order and sorted V, D records + 2 sorted states
     finally:
         adelib.destroy(ctx)
 
