@@ -40,6 +40,10 @@ WORKLOADS = {
     "lattice-64-h1.3": inputs.lattice_2d_64,
     "cube-128-h2": inputs.cube_3d_128,
     "field-1024-n120-r10": lambda: inputs.ladder_2d(1024, 10),   # + per-particle velocity field
+    # Table 1 resolutions of the Sec. 3 test model (C4, support h, irregular particles)
+    "paper-1m-n31k-c4": lambda: inputs.paper_plume(1000, 0.1),
+    "paper-2m-n50k-c4": lambda: inputs.paper_plume(1414, 0.1),
+    "paper-4m-n80k-c4": lambda: inputs.paper_plume(2000, 0.1),
     "batched-64": None,          # 64 uneven 2D plumes in one batch (inputs.batched_2d)
     "adjoint-512": None,         # gradient of the misfit: 512^2, 400 steps, checkpoints every 40
 }
@@ -176,6 +180,13 @@ def field_setup(workload, plume, xq):
     return v, vmax, dataclasses.replace(plume, name=f"{plume.name}-velocity-field-vmax{vmax}")
 
 
+def oracle_sample(plume, requested):
+    """Particles the CPU oracle evaluates per rate evaluation: the requested sample, capped at
+    about 2e8 pairs (about a second of FP64 work on the host cores) for wide kernels."""
+    neighbours = max(sharding.plume_cost(plume) / plume.n, 1.0)
+    return int(max(256, min(requested, 2e8 / neighbours, plume.n)))
+
+
 def cpu_oracle_rate(plume, xq, C, sample, min_seconds, max_steps=None, v=None):
     """Time the FP64 oracle: each step evaluates Eq. 4 twice (predictor and corrector
     evaluation) for a fixed random sample of particles.  Returns (interactions/s, steps, secs).
@@ -258,7 +269,7 @@ def run_reference(args):
     plume = adjoint_plume() if args.workload == "adjoint-512" else WORKLOADS[args.workload]()
     xq, C = plume.initial_state()
     v, _, plume = field_setup(args.workload, plume, xq)
-    sample = args.cpu_sample
+    sample = oracle_sample(plume, args.cpu_sample)
     cpu_oracle_rate(plume, xq, C, sample, 0.0, max_steps=args.warmup, v=v) if args.warmup else None
     value, steps, secs, ns = cpu_oracle_rate(plume, xq, C, sample, 0.0, max_steps=args.steps, v=v)
     cores = os.cpu_count()
@@ -480,6 +491,22 @@ def run_adjoint(args):
     return 0
 
 
+def measured_alu_roof(ade, dim, field, achieved, sms):
+    """The pair roof re-derived from the FFMA and MUFU.RSQ issue rates measured on this device
+    (ade_alu_peaks, outside the timed region)."""
+    ffma, rsq = ade.alu_peaks()
+    if field:
+        n32, nmufu = FIELD_PIPE_COST[dim]
+        roof = min(ffma / n32, rsq / nmufu) / 1e9
+    else:
+        n32, nmufu = I_MIN[dim], 1
+        roof = min(ffma / n32, rsq / nmufu) / 1e9
+    return {"ffma_per_s": ffma, "rsqrt_per_s": rsq,
+            "ffma_per_sm_per_ns": ffma / sms / 1e9, "rsqrt_per_sm_per_ns": rsq / sms / 1e9,
+            "pair_roof": roof, "unit": "Gpair/s", "frac": achieved / roof,
+            "basis": f"min(FFMA/s / {n32}, RSQRT/s / {nmufu}) per pair"}
+
+
 def run_ours(args):
     import torch
 
@@ -556,6 +583,7 @@ def run_ours(args):
                                       for i, k in enumerate(("cells", "predictor", "corrector", "reduce"))}}
     if clk.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = achieved / (peak * clk["sm_mhz"] / f_max)
+    roofline["measured_alu"] = measured_alu_roof(ade, plume.dim, v is not None, achieved, sms)
 
     # end to end through the C ABI with host buffers: H2D of the step's inputs, the step, D2H of C
     xq_pin = torch.from_numpy(np.ascontiguousarray(xq).view(np.int32)).pin_memory()
@@ -587,6 +615,14 @@ def run_ours(args):
            "d2h_bytes_per_step": int(C_out.numel() * 4),
            "ms_per_step": e2e_ms / args.steps, "path": "ade_run (graph replay) via ctypes"}
 
+    line_extra = {}
+    if args.workload.startswith("paper-"):
+        N = 4000000 if plume.n > 3000000 else (2000000 if plume.n > 1500000 else 1000000)
+        line_extra["paper_context"] = {
+            "paper_cpu_time_s": inputs.PAPER_CPU_TIME_S[N],
+            "paper_hardware": "Intel Xeon E5-2690 v3, 2.6 GHz, 12 cores (modified DualSPHysics)",
+            "paper_steps": "not stated",
+            "run_of_300_days_at_dt_1_day_s": 300 * ms_per_step / 1e3 / world}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -601,9 +637,11 @@ def run_ours(args):
         "interactions_per_step": 2 * pairs,
         "roofline": roofline, "e2e": e2e, "clocks": clk,
         "gpu_launches": launches * args.steps,
+        **line_extra,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cv, steps, secs, ns = cpu_oracle_rate(plume, xq, C, args.cpu_sample, args.cpu_seconds, v=v)
+        cv, steps, secs, ns = cpu_oracle_rate(plume, xq, C, oracle_sample(plume, args.cpu_sample),
+                                              args.cpu_seconds, v=v)
         line["cpu_baseline"] = {"value": cv, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"Eq. 4 evaluated twice per step on a fixed sample of {ns} "
                                           f"of {plume.n} particles; {steps} steps in {secs:.1f} s"}

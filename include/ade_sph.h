@@ -290,6 +290,13 @@ int ade_build_cells_noalloc(int dim, int n, const uint32_t *xq_dev, const float 
                             const int *nc_host, uint32_t *perm_dev, uint32_t *cell_start_dev,
                             void *sorted_dev, void *stream);
 
+/* Measured issue rates of the FP32 fused multiply-add pipe and of the reciprocal-square-root unit
+ * on the current device (operations per second, best of three timed launches after a warm-up
+ * launch on `stream`; about 10 ms of work in all).  The interaction kernels' ALU roof is stated in
+ * FP32-pipe instructions and MUFU operations per pair; this turns those counts into time on the
+ * device at hand.  Allocates (and frees) one small device buffer; waits for the stream. */
+int ade_alu_peaks(double *ffma_per_s_host, double *rsqrt_per_s_host, void *stream);
+
 /* Release the context (not the caller's buffers). */
 void ade_destroy(ade_ctx *ctx);
 

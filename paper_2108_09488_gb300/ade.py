@@ -37,7 +37,7 @@ EXPORTS = ("ade_workspace_bytes", "ade_init_particles", "ade_get_info", "ade_bui
            "ade_batch_stats", "ade_batch_count_pairs", "ade_batch_get_plume_info",
            "ade_batch_autotune", "ade_batch_launches_per_step", "ade_batch_destroy",
            "ade_batch_step_timed", "ade_set_dispersivity", "ade_adjoint_workspace_bytes",
-           "ade_adjoint", "ade_autotune", "ade_set_velocity_field")
+           "ade_adjoint", "ade_autotune", "ade_set_velocity_field", "ade_alu_peaks")
 NOALLOC_MAX_PARTICLES = 1 << 20
 NOALLOC_MAX_CELLS = 1 << 20
 
@@ -116,6 +116,7 @@ def load():
         "ade_batch_step_timed": (I, [P, ctypes.POINTER(ctypes.c_double), V]),
         "ade_set_dispersivity": (I, [P, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
         "ade_set_velocity_field": (I, [P, P, V]),
+        "ade_alu_peaks": (I, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), V]),
         "ade_autotune": (I, [P, ctypes.POINTER(ctypes.c_double), V]),
         "ade_adjoint_workspace_bytes": (I, [P, I, I, ctypes.POINTER(SZ)]),
         "ade_adjoint": (I, [P, P, I, I, P, SZ, P, ctypes.POINTER(ctypes.c_double),
@@ -159,7 +160,7 @@ def params_for(plume, **over):
     """Params of an ``inputs.Plume`` workload (keyword overrides allowed)."""
     kw = dict(dim=plume.dim, h=plume.h, alpha_L=plume.alpha_L, alpha_T=plume.alpha_T,
               D_m=plume.D_m, v=plume.velocity, mass=plume.mass, rho=plume.rho, box=plume.box,
-              kernel=plume.kernel)
+              kernel=plume.kernel, dt=plume.dt)
     kw.update(over)
     return params(**kw)
 
@@ -245,6 +246,14 @@ def build_cells_noalloc(dim, n, xq_ptr, C_ptr, nc, perm_ptr, cell_start_ptr, sor
     ncv = (ctypes.c_int * 3)(*([int(c) for c in nc[:dim]] + [1] * (3 - dim)))
     _check(load().ade_build_cells_noalloc(dim, n, xq_ptr, C_ptr, ncv, perm_ptr, cell_start_ptr,
                                           sorted_ptr, stream))
+
+
+def alu_peaks(stream=None):
+    """(FFMA/s, RSQRT/s) measured on the current device (ade_alu_peaks)."""
+    f = ctypes.c_double(0.0)
+    r = ctypes.c_double(0.0)
+    _check(load().ade_alu_peaks(ctypes.byref(f), ctypes.byref(r), stream))
+    return f.value, r.value
 
 
 def destroy(ctx):

@@ -54,8 +54,7 @@ struct FieldParams {
     double aL, aT, Dm;       // Eq. 3 coefficients (the per-particle D is formed in FP64)
     float gamma;             // Gamma of Eq. 5
     float pconv;             // (m / rho) kc L_x / 2^32: convective prefactor (x_ab in x-axis units)
-    double inc_scale[3];     // epilogue drift per unit velocity: tau / L_i * 2^32
-    double back_scale[3];    // drift since the cell build per unit velocity: tau_b / L_i * 2^32
+    double vscale[3];        // dt / L_i * 2^32: fixed-point drift per unit velocity over one step
 };
 
 // Per-particle field records of velocity-field mode (workspace).  v is constant in time, so the
@@ -63,9 +62,14 @@ struct FieldParams {
 // permuted into the cell-sorted order after each cell build:
 //   2D: V = {vx, vy, 0, 0},          DA = {Dxx, Dxy, Dyy, lo(Dxy)}
 //   3D: V = {vx, vy, vz, lo(Dxz)},   DA = {Dxx, Dxy, Dxz, lo(Dxy)}, DB = {Dyy, Dyz, Dzz, lo(Dyz)}
+//   Inc = {hx, hy, hz, c}: fixed-point half-step drift h_i = round(v_i dt/2 / L_i 2^32) and the
+//   full-step drift round(v_i dt / L_i 2^32) = 2 h_i + c_i, c_i in {-1, 0, 1} packed as 2-bit
+//   fields (c_i + 1) << 2i.
 struct FieldWork {
     float4 *Vc, *DAc, *DBc;  // [n] caller order (DBc: 3D only)
+    uint4 *IncC;             // [n] caller order
     float4 *V, *DA, *DB;     // [n] cell-sorted order
+    uint4 *Inc;              // [n] cell-sorted order
     unsigned *vmax_bits;     // max |v_a| as FP32 bits (ade_set_velocity_field)
 };
 
@@ -193,7 +197,6 @@ struct ade_ctx {
     bool field_dirty;     // tensors must be re-formed (dispersivities changed)
     double Hgrid;         // radius the cell grid is built for: H, or H + skin in field mode
     double skin;
-    double vscale[3];     // dt / L_i * 2^32: fixed-point drift per unit velocity over one step
     ade::FieldParams fp;  // constants (scales set per use)
     ade::FieldWork fw;
 };

@@ -290,7 +290,7 @@ void choose_tiles(int dim, int n, const Grid &g, bool iso, unsigned flags, ade::
 
 struct Layout {
     size_t keys, rank, count, block_sums, perm_tmp, perm, cell_start, P0, P1, partials, stats,
-        cf_partials, status, done, pairs, fVc, fDAc, fDBc, fV, fDA, fDB, fbits, total;
+        cf_partials, status, done, pairs, fVc, fDAc, fDBc, fIncC, fV, fDA, fDB, fInc, fbits, total;
 };
 
 // field_dim: 0 for a uniform velocity, else dim (velocity-field buffers are added at the end).
@@ -318,15 +318,17 @@ Layout layout(int n, int ncells, int nb_partials, int field_dim = 0)
     L.status = take(64);
     L.done = take(64);
     L.pairs = take(64);
-    L.fVc = L.fDAc = L.fDBc = L.fV = L.fDA = L.fDB = L.fbits = 0;
+    L.fVc = L.fDAc = L.fDBc = L.fIncC = L.fV = L.fDA = L.fDB = L.fInc = L.fbits = 0;
     if (field_dim) {
         const size_t rec = (size_t)n * 16, rec3 = field_dim == 3 ? (size_t)n * 16 : 16;
         L.fVc = take(rec);
         L.fDAc = take(rec);
         L.fDBc = take(rec3);
+        L.fIncC = take(rec);
         L.fV = take(rec);
         L.fDA = take(rec);
         L.fDB = take(rec3);
+        L.fInc = take(rec);
         L.fbits = take(64);
     }
     L.total = off;
@@ -454,13 +456,7 @@ int enqueue_eval(ade_ctx *c, Phase ph, ade::EpiOut out, cudaStream_t s)
         rp.back[i] = ph == CORRECTOR ? c->inc_half[i] : 0u;
     }
     if (c->field) {
-        ade::FieldParams fp = c->fp;
-        for (int i = 0; i < 3; ++i) {
-            const double full = c->vscale[i], half = 0.5 * c->vscale[i];
-            fp.inc_scale[i] = ph == PREDICTOR ? half : (ph == CORRECTOR ? full : 0.0);
-            fp.back_scale[i] = ph == CORRECTOR ? half : 0.0;
-        }
-        ADE_CK(ade::launch_rate_field(c->dim, c->p.kernel, epi, Pe, c->w.cell_start, c->w.perm, c->fw, rp, fp,
+        ADE_CK(ade::launch_rate_field(c->dim, c->p.kernel, epi, Pe, c->w.cell_start, c->w.perm, c->fw, rp, c->fp,
                                       out, s));
         return ADE_OK;
     }
@@ -530,7 +526,7 @@ void field_constants(ade_ctx *c)
     fp.Dm = p.D_m;
     fp.gamma = (float)(p.gamma > 0.0 ? p.gamma : p.dim + 2.0);
     fp.pconv = (float)((p.mass / p.rho) * kernel_kc(p.kernel, p.dim, c->H) * (p.box[0] / kTwo32));
-    for (int i = 0; i < 3; ++i) c->vscale[i] = i < p.dim ? c->dt / p.box[i] * kTwo32 : 0.0;
+    for (int i = 0; i < 3; ++i) fp.vscale[i] = i < p.dim ? c->dt / p.box[i] * kTwo32 : 0.0;
 }
 
 // Per-plume constants: Eq. 3 (D), the time step (Eq. 10 or the largest-eigenvalue rule), the
@@ -684,6 +680,8 @@ int ade_init_particles(ade_ctx **out, const ade_params *p, int n, uint32_t *xq_d
         c->fw.Vc = at<float4>(workspace_dev, d.L.fVc);
         c->fw.DAc = at<float4>(workspace_dev, d.L.fDAc);
         c->fw.DBc = at<float4>(workspace_dev, d.L.fDBc);
+        c->fw.IncC = at<uint4>(workspace_dev, d.L.fIncC);
+        c->fw.Inc = at<uint4>(workspace_dev, d.L.fInc);
         c->fw.V = at<float4>(workspace_dev, d.L.fV);
         c->fw.DA = at<float4>(workspace_dev, d.L.fDA);
         c->fw.DB = at<float4>(workspace_dev, d.L.fDB);

@@ -61,14 +61,19 @@ __device__ __forceinline__ float hmean_off2(float ah, float a8, float al, float 
     return fabsf(den) >= 1.17549435e-38f ? k2 : 0.f;
 }
 
-// Fixed-point drift round(v tau / L_i 2^32) mod 2^32 of one particle, per axis (FP64: one
-// multiply per axis and particle).
-template <int DIM>
-__device__ __forceinline__ void drift(const float4 &v, const double scale[3], uint32_t out[3])
+// Fixed-point drift of one particle read from its Inc record: half step, or full step 2h + c.
+__device__ __forceinline__ void half_drift(const uint4 &ic, uint32_t out[3])
 {
-    out[0] = (uint32_t)(unsigned long long)__double2ll_rn((double)v.x * scale[0]);
-    out[1] = (uint32_t)(unsigned long long)__double2ll_rn((double)v.y * scale[1]);
-    out[2] = DIM == 3 ? (uint32_t)(unsigned long long)__double2ll_rn((double)v.z * scale[2]) : 0u;
+    out[0] = ic.x;
+    out[1] = ic.y;
+    out[2] = ic.z;
+}
+
+__device__ __forceinline__ void full_drift(const uint4 &ic, uint32_t out[3])
+{
+    out[0] = 2u * ic.x + ((ic.w & 3u) - 1u);
+    out[1] = 2u * ic.y + (((ic.w >> 2) & 3u) - 1u);
+    out[2] = 2u * ic.z + (((ic.w >> 4) & 3u) - 1u);
 }
 
 // Velocities of the caller's field into the caller-order records (fourth lane cleared) and
@@ -90,16 +95,25 @@ __global__ __launch_bounds__(kT) void k_field_velocity(const float *__restrict__
     if ((threadIdx.x & 31) == 0) atomicMax(out_bits, __float_as_uint(s));
 }
 
-// Dispersion tensor (Eq. 3) of every particle in FP64 from its velocity, stored as the records
-// described in ade_internal.h (caller order).
+// Dispersion tensor (Eq. 3) of every particle in FP64 from its velocity, and its fixed-point
+// drift per half and full step, stored as the records described in ade_internal.h (caller order).
 template <int DIM>
 __global__ __launch_bounds__(kT) void k_field_tensors(int n, FieldParams fp, float4 *__restrict__ Vc,
-                                                      float4 *__restrict__ DAc, float4 *__restrict__ DBc)
+                                                      float4 *__restrict__ DAc, float4 *__restrict__ DBc,
+                                                      uint4 *__restrict__ IncC)
 {
     const int i = blockIdx.x * kT + threadIdx.x;
     if (i >= n) return;
     const float4 vr = Vc[i];
     const double vv[3] = {vr.x, vr.y, DIM == 3 ? (double)vr.z : 0.0};
+    uint32_t h[3], cbits = 0u;
+    for (int k = 0; k < 3; ++k) {
+        const long long hk = __double2ll_rn(vv[k] * (0.5 * fp.vscale[k]));
+        const long long fk = __double2ll_rn(vv[k] * fp.vscale[k]);
+        h[k] = (uint32_t)(unsigned long long)hk;
+        cbits |= (uint32_t)(fk - 2 * hk + 1) << (2 * k);
+    }
+    IncC[i] = make_uint4(h[0], h[1], h[2], cbits);
     const double s = sqrt(vv[0] * vv[0] + vv[1] * vv[1] + vv[2] * vv[2]);
     const double iso = fp.aT * s + fp.Dm;
     const double g = s > 0.0 ? (fp.aL - fp.aT) / s : 0.0;
@@ -120,8 +134,9 @@ __global__ __launch_bounds__(kT) void k_field_tensors(int n, FieldParams fp, flo
 template <int DIM>
 __global__ __launch_bounds__(kT) void k_field_permute(const uint32_t *__restrict__ perm, int n,
                                                       const float4 *__restrict__ Vc, const float4 *__restrict__ DAc,
-                                                      const float4 *__restrict__ DBc, float4 *__restrict__ V,
-                                                      float4 *__restrict__ DA, float4 *__restrict__ DB)
+                                                      const float4 *__restrict__ DBc, const uint4 *__restrict__ IncC,
+                                                      float4 *__restrict__ V, float4 *__restrict__ DA,
+                                                      float4 *__restrict__ DB, uint4 *__restrict__ Inc)
 {
     const int i = blockIdx.x * kT + threadIdx.x;
     if (i >= n) return;
@@ -129,14 +144,15 @@ __global__ __launch_bounds__(kT) void k_field_permute(const uint32_t *__restrict
     V[i] = __ldg(Vc + a);
     DA[i] = __ldg(DAc + a);
     if (DIM == 3) DB[i] = __ldg(DBc + a);
+    Inc[i] = __ldg(IncC + a);
 }
 
 template <int DIM, int KERNEL, int EPI, bool COUNT>
 __global__ __launch_bounds__(kT) void k_rate_field(const uint4 *__restrict__ Pe, const uint32_t *__restrict__ cs,
                                                    const uint32_t *__restrict__ perm,
                                                    const float4 *__restrict__ V, const float4 *__restrict__ DA,
-                                                   const float4 *__restrict__ DB, const RateParams prm,
-                                                   const FieldParams fp, const EpiOut out)
+                                                   const float4 *__restrict__ DB, const uint4 *__restrict__ Inc,
+                                                   const RateParams prm, const FieldParams fp, const EpiOut out)
 {
     const int i = blockIdx.x * kT + threadIdx.x;
     const bool valid = i < prm.n;
@@ -145,16 +161,15 @@ __global__ __launch_bounds__(kT) void k_rate_field(const uint4 *__restrict__ Pe,
     const float4 va = __ldg(V + ii);
     const float4 da = __ldg(DA + ii);
     const float4 db = DIM == 3 ? __ldg(DB + ii) : make_float4(0.f, 0.f, 0.f, 0.f);
-    // cell of the cell build: evaluation position minus this particle's drift since the build
-    int cx, cy, cz;
+    // fixed-point drift of this particle; the cell of the cell build is the evaluation position
+    // minus the drift since the build (the half step, in the corrector)
+    const uint4 ic = EPI == EPI_RATE ? make_uint4(0u, 0u, 0u, 0u) : __ldg(Inc + ii);
+    uint32_t back[3] = {0u, 0u, 0u};
+    if (EPI == EPI_CORRECT) half_drift(ic, back);
     const int ncx = prm.ncx, ncy = prm.ncy, ncz = prm.ncz;
-    {
-        uint32_t back[3];
-        drift<DIM>(va, fp.back_scale, back);
-        cx = (int)__umulhi(pa.x - back[0], (uint32_t)ncx);
-        cy = (int)__umulhi(pa.y - back[1], (uint32_t)ncy);
-        cz = DIM == 3 ? (int)__umulhi(pa.z - back[2], (uint32_t)ncz) : 0;
-    }
+    const int cx = (int)__umulhi(pa.x - back[0], (uint32_t)ncx);
+    const int cy = (int)__umulhi(pa.y - back[1], (uint32_t)ncy);
+    const int cz = DIM == 3 ? (int)__umulhi(pa.z - back[2], (uint32_t)ncz) : 0;
     const float Ca = __uint_as_float(pa.w);
     const float H2 = prm.H2, invH = prm.invH, sy = prm.sy, sz = prm.sz, gam = fp.gamma;
     // 4 D (diagonal) and 8 D (off-diagonal) of this particle for the harmonic means
@@ -251,8 +266,6 @@ __global__ __launch_bounds__(kT) void k_rate_field(const uint4 *__restrict__ Pe,
 
     Acc acc{0.f, 0.f, __int_as_float(0x7f800000), __int_as_float(0xff800000), valid ? cnt : 0u};
     if (valid) {
-        uint32_t inc[3];
-        drift<DIM>(va, fp.inc_scale, inc);
         if (EPI == EPI_RATE) {
             if (out.rate) {
                 const uint32_t a = __ldg(perm + i);
@@ -260,6 +273,8 @@ __global__ __launch_bounds__(kT) void k_rate_field(const uint4 *__restrict__ Pe,
             }
         } else if (EPI == EPI_PREDICT) {
             // C^{l+1/2} = C^l + dt/2 r^l, x_a^{l+1/2} = x_a^l + dt/2 v_a
+            uint32_t inc[3];
+            half_drift(ic, inc);
             uint4 q;
             q.x = pa.x + inc[0];
             q.y = pa.y + inc[1];
@@ -270,8 +285,8 @@ __global__ __launch_bounds__(kT) void k_rate_field(const uint4 *__restrict__ Pe,
             // C^{l+1} = C^l + dt r^{l+1/2}, x_a^{l+1} = x_a^l + dt v_a (caller order); x^l is the
             // evaluation position minus this particle's half-step drift (exact in fixed point)
             const uint32_t a = __ldg(perm + i);
-            uint32_t back[3];
-            drift<DIM>(va, fp.back_scale, back);
+            uint32_t inc[3];
+            full_drift(ic, inc);
             float Cn = 0.f;
             if (a < (uint32_t)prm.n) {
                 Cn = fmaf(prm.dt, rate, out.C[a]);
@@ -297,15 +312,15 @@ void launch_field_epi(int epi, int blocks, const uint4 *Pe, const uint32_t *cs, 
     switch (epi) {
     case EPI_RATE:
         k_rate_field<DIM, KERNEL, EPI_RATE, COUNT>
-            <<<blocks, kT, 0, s>>>(Pe, cs, perm, fw.V, fw.DA, fw.DB, prm, fp, out);
+            <<<blocks, kT, 0, s>>>(Pe, cs, perm, fw.V, fw.DA, fw.DB, fw.Inc, prm, fp, out);
         break;
     case EPI_PREDICT:
         k_rate_field<DIM, KERNEL, EPI_PREDICT, COUNT>
-            <<<blocks, kT, 0, s>>>(Pe, cs, perm, fw.V, fw.DA, fw.DB, prm, fp, out);
+            <<<blocks, kT, 0, s>>>(Pe, cs, perm, fw.V, fw.DA, fw.DB, fw.Inc, prm, fp, out);
         break;
     default:
         k_rate_field<DIM, KERNEL, EPI_CORRECT, COUNT>
-            <<<blocks, kT, 0, s>>>(Pe, cs, perm, fw.V, fw.DA, fw.DB, prm, fp, out);
+            <<<blocks, kT, 0, s>>>(Pe, cs, perm, fw.V, fw.DA, fw.DB, fw.Inc, prm, fp, out);
         break;
     }
 }
@@ -334,10 +349,10 @@ cudaError_t launch_field_records(int dim, const float *v_dev, int n, const Field
     const int blocks = (n + kT - 1) / kT;
     if (dim == 2) {
         if (v_dev) k_field_velocity<2><<<blocks, kT, 0, s>>>(v_dev, n, fw.Vc, fw.vmax_bits);
-        k_field_tensors<2><<<blocks, kT, 0, s>>>(n, fp, fw.Vc, fw.DAc, fw.DBc);
+        k_field_tensors<2><<<blocks, kT, 0, s>>>(n, fp, fw.Vc, fw.DAc, fw.DBc, fw.IncC);
     } else {
         if (v_dev) k_field_velocity<3><<<blocks, kT, 0, s>>>(v_dev, n, fw.Vc, fw.vmax_bits);
-        k_field_tensors<3><<<blocks, kT, 0, s>>>(n, fp, fw.Vc, fw.DAc, fw.DBc);
+        k_field_tensors<3><<<blocks, kT, 0, s>>>(n, fp, fw.Vc, fw.DAc, fw.DBc, fw.IncC);
     }
     return cudaGetLastError();
 }
@@ -347,9 +362,9 @@ cudaError_t launch_field_permute(int dim, const uint32_t *perm, int n, const Fie
     if (n == 0) return cudaSuccess;
     const int blocks = (n + kT - 1) / kT;
     if (dim == 2)
-        k_field_permute<2><<<blocks, kT, 0, s>>>(perm, n, fw.Vc, fw.DAc, fw.DBc, fw.V, fw.DA, fw.DB);
+        k_field_permute<2><<<blocks, kT, 0, s>>>(perm, n, fw.Vc, fw.DAc, fw.DBc, fw.IncC, fw.V, fw.DA, fw.DB, fw.Inc);
     else
-        k_field_permute<3><<<blocks, kT, 0, s>>>(perm, n, fw.Vc, fw.DAc, fw.DBc, fw.V, fw.DA, fw.DB);
+        k_field_permute<3><<<blocks, kT, 0, s>>>(perm, n, fw.Vc, fw.DAc, fw.DBc, fw.IncC, fw.V, fw.DA, fw.DB, fw.Inc);
     return cudaGetLastError();
 }
 

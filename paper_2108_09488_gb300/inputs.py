@@ -101,6 +101,7 @@ class Plume:
     jitter: float = 0.0
     seed: int = 0
     name: str = ""
+    dt: float = 0.0                       # 0: the library's time-step rule
 
     @property
     def n(self):
@@ -214,3 +215,29 @@ def velocity_noise(n, dim, vmax, seed=7):
     d /= np.maximum(np.linalg.norm(d, axis=0), 1e-30)
     s = rng.uniform(0.0, vmax, size=n) * (1.0 - 1e-6)
     return np.ascontiguousarray((d * s).astype(np.float32))
+
+
+# The test model of Sec. 3 in physical units: periodic square of side 2000 m, alpha_L = 10 m,
+# D_m = 0, |v| = 1.16e-5 m/s at 45 degrees, Gaussian plume C0 = 0.32 kg/m^3, w = 44 m at the
+# centre, 300 days; Table 1 runs of 1, 2 and 4 million irregular particles.
+PAPER_SIDE_M = 2000.0
+PAPER_DAY_S = 86400.0
+PAPER_CPU_TIME_S = {1000000: 98766.54, 2000000: 495064.78, 4000000: 1773900.15}
+
+
+def paper_plume(side, ratio, jitter=0.45, seed=3, steps=300):
+    """The Sec. 3 test model in units of the box side L = 2000 m and of seconds, on side^2
+    irregular particles (a jittered lattice, displacements U(-jitter, jitter) dx): the number of
+    neighbours and the smoothing length follow the scaling relations of Sec. 2.3,
+    n = 2.81 N^0.675 and h = 1.29 n^-0.247 L, with the Wendland C4 kernel (Eq. 7, support h);
+    alpha_T = ratio * alpha_L.  The paper does not state its time step; dt = 1 day here, so 300
+    steps cover its 300 days."""
+    N = side * side
+    n = 2.81 * N ** 0.675
+    h_over_L = 1.29 * n ** -0.247
+    L = PAPER_SIDE_M
+    return Plume(dim=2, side=side, h_over_dx=h_over_L * side, kernel=WENDLAND_C4,
+                 alpha_L=10.0 / L, alpha_T=ratio * 10.0 / L, D_m=0.0, speed=1.16e-5 / L,
+                 angle=math.pi / 4.0, x0=(0.5, 0.5, 0.5), w=44.0 / L, C0=0.32, steps=steps,
+                 jitter=jitter, seed=seed, dt=PAPER_DAY_S,
+                 name=f"paper-2d-{N}-n{round(n)}-c4-aT_over_aL{ratio:g}")

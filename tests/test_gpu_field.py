@@ -249,3 +249,4 @@ def test_field_full_size_sampled(lib, orc):
     assert np.max(np.abs(r[sel] - r_orc)) <= RATE_TOL * np.max(np.abs(r))
     assert pairs == 3000 * 120
     assert sim.count_pairs() == plume.n * 120
+
