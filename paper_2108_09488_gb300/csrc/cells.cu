@@ -12,7 +12,9 @@
 //   scan      exclusive scan of the counts -> cell_start[0..ncells] (three launches)
 //   k_place   provisional position cell_start[key] + rank
 //   k_order   one thread per cell sorts its segment by caller index (insertion sort; cells hold a
-//             handful of particles) and writes the sorted copy {x, y, z, C}
+//             handful of particles) and writes the sorted copy {x, y, z, C}; cells of more than
+//             kSmallCell particles (wide kernels: hundreds to thousands per cell) are ordered by
+//             the whole warp instead, each element placed at its rank among the cell's indices
 // The result is the stable order (key, caller index) regardless of the order the atomics took,
 // so the permutation and cell table are identical on every run and bit-exact against a stable
 // counting sort.
@@ -158,19 +160,15 @@ __global__ __launch_bounds__(kThreads) void k_place(const uint32_t *__restrict__
     if (pos < (uint32_t)n) perm_tmp[pos] = (uint32_t)i;
 }
 
-// One thread per cell: order the cell's segment by caller index and write the sorted copy.
-__global__ __launch_bounds__(kThreads) void k_order(const uint32_t *__restrict__ start, int ncells,
-                                                    const uint32_t *__restrict__ perm_tmp,
-                                                    const uint32_t *__restrict__ xq,
-                                                    const float *__restrict__ C, int n, int dim,
-                                                    uint32_t *__restrict__ perm,
-                                                    uint4 *__restrict__ P)
+constexpr uint32_t kSmallCell = 32;   // cells up to this size are ordered by one thread
+
+// Orders one cell segment [s, e) of perm_tmp by caller index into perm and writes the sorted copy
+// P[k] = rec(perm[k]), for the calling thread's cell when it is small (insertion sort); cells
+// larger than kSmallCell are handled by order_big_cells.
+template <class Rec>
+__device__ __forceinline__ void order_small_cell(uint32_t s, uint32_t e, const uint32_t *__restrict__ perm_tmp,
+                                                 uint32_t *__restrict__ perm, uint4 *__restrict__ P, Rec rec)
 {
-    const int c = blockIdx.x * kThreads + threadIdx.x;
-    if (c >= ncells) return;
-    const uint32_t s = __ldg(start + c), e = __ldg(start + c + 1);
-    if (e <= s || e > (uint32_t)n) return;
-    // insertion sort, written to perm (the segment is small: a few particles per cell)
     for (uint32_t k = s; k < e; ++k) {
         uint32_t v = __ldg(perm_tmp + k);
         uint32_t j = k;
@@ -180,15 +178,76 @@ __global__ __launch_bounds__(kThreads) void k_order(const uint32_t *__restrict__
         }
         perm[j] = v;
     }
-    for (uint32_t k = s; k < e; ++k) {
-        const uint32_t a = perm[k];
+    for (uint32_t k = s; k < e; ++k) P[k] = rec(perm[k]);
+}
+
+// The big cells among the warp's 32 cells, one after another, each ordered by all 32 lanes: every
+// element goes to s + (number of the cell's indices smaller than it), counted by streaming the
+// segment through the warp 32 values at a time (coalesced load, broadcast by shuffles).  The
+// indices are distinct, so the ranks are a permutation of the segment.  Every lane of the warp
+// must call this (big = the lane's cell is valid and larger than kSmallCell).
+template <class Rec>
+__device__ __forceinline__ void order_big_cells(bool big, uint32_t s, uint32_t e,
+                                                const uint32_t *__restrict__ perm_tmp,
+                                                uint32_t *__restrict__ perm, uint4 *__restrict__ P, Rec rec)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned todo = __ballot_sync(0xffffffffu, big);
+    while (todo) {
+        const int l = __ffs(todo) - 1;
+        todo &= todo - 1u;
+        const uint32_t bs = __shfl_sync(0xffffffffu, s, l), be = __shfl_sync(0xffffffffu, e, l);
+        for (uint32_t k0 = bs; k0 < be; k0 += 32) {
+            const uint32_t k = k0 + (uint32_t)lane;
+            const bool has = k < be;
+            const uint32_t v = has ? __ldg(perm_tmp + k) : 0xffffffffu;
+            uint32_t rank = 0u;
+            for (uint32_t t0 = bs; t0 < be; t0 += 32) {
+                const uint32_t u = t0 + (uint32_t)lane < be ? __ldg(perm_tmp + t0 + lane) : 0xffffffffu;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) rank += __shfl_sync(0xffffffffu, u, q) < v ? 1u : 0u;
+            }
+            if (has && bs + rank < be) {
+                perm[bs + rank] = v;
+                P[bs + rank] = rec(v);
+            }
+        }
+    }
+}
+
+struct PlainRec {
+    const uint32_t *xq;
+    const float *C;
+    int n, dim;
+    __device__ __forceinline__ uint4 operator()(uint32_t a) const
+    {
         uint4 p;
         p.x = __ldg(xq + a);
         p.y = __ldg(xq + n + a);
         p.z = dim == 3 ? __ldg(xq + 2 * (size_t)n + a) : 0u;
         p.w = __float_as_uint(__ldg(C + a));
-        P[k] = p;
+        return p;
     }
+};
+
+// One thread per cell: order the cell's segment by caller index and write the sorted copy.
+__global__ __launch_bounds__(kThreads) void k_order(const uint32_t *__restrict__ start, int ncells,
+                                                    const uint32_t *__restrict__ perm_tmp,
+                                                    const uint32_t *__restrict__ xq,
+                                                    const float *__restrict__ C, int n, int dim,
+                                                    uint32_t *__restrict__ perm,
+                                                    uint4 *__restrict__ P)
+{
+    const int c = blockIdx.x * kThreads + threadIdx.x;
+    uint32_t s = 0u, e = 0u;
+    if (c < ncells) {
+        s = __ldg(start + c);
+        e = __ldg(start + c + 1);
+    }
+    const bool valid = e > s && e <= (uint32_t)n;
+    const PlainRec rec{xq, C, n, dim};
+    if (valid && e - s <= kSmallCell) order_small_cell(s, e, perm_tmp, perm, P, rec);
+    order_big_cells(valid && e - s > kSmallCell, s, e, perm_tmp, perm, P, rec);
 }
 
 // Batched plumes: caller particle i belongs to plume p = plume_of[i], whose positions are the
@@ -209,6 +268,26 @@ __global__ __launch_bounds__(kThreads) void k_count_batch(const uint32_t *__rest
     rank[i] = atomicAdd(count + key, 1u);
 }
 
+struct BatchRec {
+    const uint32_t *xq;
+    const float *C;
+    int dim;
+    const RateParams *descs;
+    const uint16_t *plume_of;
+    __device__ __forceinline__ uint4 operator()(uint32_t a) const
+    {
+        const RateParams &d = descs[__ldg(plume_of + a)];
+        const uint32_t *xp = xq + (size_t)dim * d.goff;
+        const uint32_t l = a - (uint32_t)d.goff, np = (uint32_t)d.n;
+        uint4 p;
+        p.x = __ldg(xp + l);
+        p.y = __ldg(xp + np + l);
+        p.z = dim == 3 ? __ldg(xp + 2 * (size_t)np + l) : 0u;
+        p.w = __float_as_uint(__ldg(C + a));
+        return p;
+    }
+};
+
 __global__ __launch_bounds__(kThreads) void k_order_batch(const uint32_t *__restrict__ start, int ncells,
                                                           const uint32_t *__restrict__ perm_tmp,
                                                           const uint32_t *__restrict__ xq,
@@ -219,30 +298,15 @@ __global__ __launch_bounds__(kThreads) void k_order_batch(const uint32_t *__rest
                                                           uint4 *__restrict__ P)
 {
     const int c = blockIdx.x * kThreads + threadIdx.x;
-    if (c >= ncells) return;
-    const uint32_t s = __ldg(start + c), e = __ldg(start + c + 1);
-    if (e <= s || e > (uint32_t)n) return;
-    for (uint32_t k = s; k < e; ++k) {
-        uint32_t v = __ldg(perm_tmp + k);
-        uint32_t j = k;
-        while (j > s && perm[j - 1] > v) {
-            perm[j] = perm[j - 1];
-            --j;
-        }
-        perm[j] = v;
+    uint32_t s = 0u, e = 0u;
+    if (c < ncells) {
+        s = __ldg(start + c);
+        e = __ldg(start + c + 1);
     }
-    for (uint32_t k = s; k < e; ++k) {
-        const uint32_t a = perm[k];
-        const RateParams &d = descs[__ldg(plume_of + a)];
-        const uint32_t *xp = xq + (size_t)dim * d.goff;
-        const uint32_t l = a - (uint32_t)d.goff, np = (uint32_t)d.n;
-        uint4 p;
-        p.x = __ldg(xp + l);
-        p.y = __ldg(xp + np + l);
-        p.z = dim == 3 ? __ldg(xp + 2 * (size_t)np + l) : 0u;
-        p.w = __float_as_uint(__ldg(C + a));
-        P[k] = p;
-    }
+    const bool valid = e > s && e <= (uint32_t)n;
+    const BatchRec rec{xq, C, dim, descs, plume_of};
+    if (valid && e - s <= kSmallCell) order_small_cell(s, e, perm_tmp, perm, P, rec);
+    order_big_cells(valid && e - s > kSmallCell, s, e, perm_tmp, perm, P, rec);
 }
 
 }  // namespace

@@ -70,3 +70,20 @@ def test_paper_scale_1m_sampled(lib, orc):
     r_orc, pairs = orc.rate_at(sel, inputs.from_fixed(xq, plume.boxv), *_args(plume, C))
     assert pairs > 30000 * sel.size
     assert np.max(np.abs(r[sel] - r_orc)) <= RATE_TOL * np.max(np.abs(r))
+
+
+@pytest.mark.parametrize("k", [1, 3, 6])
+def test_big_cells_bit_exact(lib, orc, k):
+    """Wide kernels put hundreds of particles in a cell (about 440 per cell at one cell per support
+    radius here), which the cell build orders warp-cooperatively: permutation and start table are
+    still bit-exact against the oracle's stable counting sort."""
+    plume = inputs.paper_plume(96, 0.1)
+    xq, C = plume.initial_state()
+    sim = lib.Simulation(lib.params_for(plume, cell_subdiv=k), xq, C)
+    sim.build_cells()
+    perm, cs = sim.cells()
+    assert np.max(np.diff(cs)) > 32 or k > 1
+    perm_o, cs_o = orc.sort_cells(orc.cell_keys(xq, np.array(sim.info.nc)), sim.info.ncells)
+    assert np.array_equal(perm, perm_o) and np.array_equal(cs, cs_o)
+    r, _ = orc.rate(inputs.from_fixed(xq, plume.boxv), *_args(plume, C))
+    assert _rel(sim.rate().cpu().numpy(), r) <= RATE_TOL
