@@ -73,9 +73,11 @@ FIELD_PIPE_COST = {2: (33, 4), 3: (51, 7)}
 MUFU_LANES_PER_SM = 16
 
 # DRAM bytes per rate launch (read + write, mean of predictor and corrector) from one ncu capture
-# of the current kernels (profiles/k_rate_ladder1024.md, profiles/k_rate_batch_batched64.md).
+# of the current kernels (profiles/k_rate_ladder1024.md, profiles/k_rate_batch_batched64.md,
+# profiles/k_rate_field_field1024.md).
 # Set an entry to None whenever the kernel changes until it is captured again.
-TRAFFIC_PER_LAUNCH = {"ladder-1024-n120-r10": 22.81e6, "batched-64": 45.16e6}
+TRAFFIC_PER_LAUNCH = {"ladder-1024-n120-r10": 22.81e6, "batched-64": 45.16e6,
+                      "field-1024-n120-r10": 82.9e6}
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
 
