@@ -45,11 +45,18 @@ WORKLOADS = {
     "paper-2m-n50k-c4": lambda: inputs.paper_plume(1414, 0.1),
     "paper-4m-n80k-c4": lambda: inputs.paper_plume(2000, 0.1),
     "batched-64": None,          # 64 uneven 2D plumes in one batch (inputs.batched_2d)
+    "sweep-512-8": None,         # 8 dispersivity sets on the 512^2 rung sharing one cell list
     "adjoint-512": None,         # gradient of the misfit: 512^2, 400 steps, checkpoints every 40
 }
 # velocity-field workloads: vmax of the smooth seeded field (inputs.velocity_field, speed 0.1,
 # relative amplitude 0.5, so max |v| ~ 0.17)
 FIELD_VMAX = {"field-1024-n120-r10": 0.2}
+# dispersivity sweep: alpha_T = 1e-3, alpha_L / alpha_T = 1 .. 100, D_m = 1e-6, on the 512^2 rung
+SWEEP_RATIOS = (1, 2, 5, 10, 20, 30, 50, 100)
+# minimum FP32-pipe instructions of the sweep kernel: 12 per pair for the shared geometry
+# (separation, r^2, r, 1 - q, f, u = (vhat . e)^2) and 4 per pair and set (a u + b, f s, C_a - C_b,
+# accumulation)
+SWEEP_GEOM, SWEEP_PER_SET = 12, 4
 ADJ_THETA = (1e-2, 1e-3, 1e-6)
 ADJ_THETA_STAR = (2e-2, 2e-3, 1e-6)
 ADJ_STEPS, ADJ_CKPT = 400, 40
@@ -268,7 +275,12 @@ def run_reference(args):
         }
         print(json.dumps(line))
         return 0
-    plume = adjoint_plume() if args.workload == "adjoint-512" else WORKLOADS[args.workload]()
+    if args.workload == "adjoint-512":
+        plume = adjoint_plume()
+    elif args.workload == "sweep-512-8":
+        plume = sweep_setup()[0]          # the oracle evaluates one set at a time
+    else:
+        plume = WORKLOADS[args.workload]()
     xq, C = plume.initial_state()
     v, _, plume = field_setup(args.workload, plume, xq)
     sample = oracle_sample(plume, args.cpu_sample)
@@ -509,6 +521,145 @@ def measured_alu_roof(ade, dim, field, achieved, sms):
             "basis": f"min(FFMA/s / {n32}, RSQRT/s / {nmufu}) per pair"}
 
 
+def sweep_setup():
+    plume = inputs.ladder_2d(512, 10)
+    theta = np.array([[1e-3 * r, 1e-3, 1e-6] for r in SWEEP_RATIOS])
+    return plume, theta
+
+
+def run_sweep(args):
+    """8 dispersivity sets on one 512^2 plume in one sweep, against one context per set."""
+    import torch
+
+    from paper_2108_09488_gb300 import ade
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = Dist(world, True)
+    plume, theta = sweep_setup()
+    P = len(theta)
+    xq, C = plume.initial_state()
+    sw = ade.Sweep(ade.params_for(plume), xq, np.broadcast_to(C, (P, plume.n)), theta, device=device)
+    pairs = sw.count_pairs()
+    units_per_step = 2.0 * pairs * P          # every set evaluates every pair twice per step
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+    for _ in range(args.warmup):
+        flush.zero_()
+        sw.step_timed()
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    phases = []
+    for _ in range(args.steps):
+        flush.zero_()
+        phases.append(sw.step_timed())
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    agg_dev = device if world > 1 else None
+    value, total_ms, _ = sharding.aggregate(units_per_step * args.steps, sum(sum(p) for p in phases),
+                                            device=agg_dev)
+    ms_per_step = total_ms / args.steps
+
+    # the same sets as P single-plume contexts (same dt and grid), one graph launch each
+    stream = torch.cuda.current_stream(device)
+    sims = [ade.Simulation(ade.params_for(plume, alpha_L=t[0], alpha_T=t[1], D_m=t[2], dt=sw.info.dt,
+                                          cell_subdiv=sw.info.cell_subdiv, flags=ade.FLAG_DIRECT),
+                           xq, C, device=device) for t in theta]
+    for _ in range(args.warmup):
+        flush.zero_()
+        for sm in sims:
+            sm.run(1, stats=False)
+    torch.cuda.synchronize()
+    ps_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for sm in sims:
+            sm.run(1, stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ps_ms += e0.elapsed_time(e1)
+    ps_value, ps_ms, _ = sharding.aggregate(units_per_step * args.steps, ps_ms, device=agg_dev)
+    for sm in sims:
+        sm.close()
+
+    rate_ms = (sum(p[1] for p in phases) + sum(p[2] for p in phases)) / (2 * len(phases))
+    props = torch.cuda.get_device_properties(device)
+    sms = props.multi_processor_count
+    f_max = clk.get("sm_max_mhz") or 2070.0
+    per_set = SWEEP_PER_SET + SWEEP_GEOM / P
+    peak = sms * FP32_LANES_PER_SM * f_max * 1e6 / per_set / 1e9
+    achieved = pairs * P / (rate_ms * 1e-3) / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair-sets/s",
+                "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get("sweep-512-8"),
+                "traffic_unit": "bytes per evaluation (ncu dram read + write, all groups)",
+                "kernel": "k_rate_sweep (predictor + corrector, one group of 8 sets)",
+                "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {f_max:.0f} MHz / "
+                              f"({SWEEP_PER_SET} + {SWEEP_GEOM}/{P}) FP32-pipe instructions per pair and set",
+                "rate_evaluation_ms": rate_ms,
+                "phase_ms_per_step": {k: sum(p[i] for p in phases) / len(phases)
+                                      for i, k in enumerate(("cells", "predictors", "correctors"))}}
+    roofline["measured_alu"] = {"ffma_per_s": ade.alu_peaks()[0]}
+    roofline["measured_alu"]["pair_set_roof"] = roofline["measured_alu"]["ffma_per_s"] / per_set / 1e9
+    roofline["measured_alu"]["frac"] = achieved / roofline["measured_alu"]["pair_set_roof"]
+
+    # end to end: H2D of x and the P fields, one graph-replayed step, D2H of the P fields
+    xq_pin = sw.xq.cpu().pin_memory()
+    C_pin = sw.C.cpu().pin_memory()
+    C_out = torch.empty_like(C_pin).pin_memory()
+    for _ in range(args.warmup):
+        sw.xq.copy_(xq_pin, non_blocking=True)
+        sw.C.copy_(C_pin, non_blocking=True)
+        sw.run(1)
+        C_out.copy_(sw.C, non_blocking=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sw.xq.copy_(xq_pin, non_blocking=True)
+        sw.C.copy_(C_pin, non_blocking=True)
+        sw.run(1)
+        C_out.copy_(sw.C, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_value, e2e_ms, _ = sharding.aggregate(units_per_step * args.steps, e0.elapsed_time(e1), device=agg_dev)
+    e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(xq_pin.numel() * 4 + C_pin.numel() * 4),
+           "d2h_bytes_per_step": int(C_out.numel() * 4), "ms_per_step": e2e_ms / args.steps,
+           "path": "ade_sweep_run (graph replay) via ctypes"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {**workload_config(plume), "workload": f"sweep-{plume.name}-{P}-sets",
+                   "sets": P, "alpha_L_over_alpha_T": list(SWEEP_RATIOS), "interaction": "one pair for one set"},
+        "grid": {"cell_subdiv": sw.info.cell_subdiv, "cells": sw.info.ncells, "dt": sw.info.dt,
+                 "launches_per_evaluation": sw.info.tile[0]},
+        "per_set_contexts": {"value": ps_value, "ms_per_step": ps_ms / args.steps,
+                             "sweep_speedup": value / ps_value},
+        "steps_per_s": 1e3 / ms_per_step * world, "interactions_per_step": units_per_step,
+        "roofline": roofline, "e2e": e2e, "clocks": clk,
+        "gpu_launches": sw.launches_per_step() * args.steps,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cv, steps, secs, ns = cpu_oracle_rate(plume, xq, C, oracle_sample(plume, args.cpu_sample // P),
+                                              args.cpu_seconds)
+        line["cpu_baseline"] = {"value": cv, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"Eq. 4 evaluated twice per step for one set on {ns} of "
+                                          f"{plume.n} particles; {steps} steps in {secs:.1f} s "
+                                          "(the oracle evaluates each set separately)"}
+    sw.close()
+    if rank == 0:
+        print(json.dumps(line))
+    dist.close()
+    return 0
+
+
 def run_ours(args):
     import torch
 
@@ -517,6 +668,8 @@ def run_ours(args):
     world, rank, local = dist_env()
     if args.workload == "batched-64":
         return run_batched(args)
+    if args.workload == "sweep-512-8":
+        return run_sweep(args)
     if args.workload == "adjoint-512":
         return run_adjoint(args)
     if not torch.cuda.is_available():

@@ -268,6 +268,38 @@ int ade_batch_launches_per_step(const ade_batch *b, int *launches);
 
 void ade_batch_destroy(ade_batch *b);
 
+/* ---- Parameter sweep (many dispersivity sets on one plume) -------------------------------------
+ * P parameter sets theta_k = (alpha_L, alpha_T, D_m)_k (Eq. 3) evolved side by side on one particle
+ * set with one uniform velocity and one time step, each with its own concentration field: the
+ * forward runs of a dispersivity sweep or inversion.  The cell list, the positions and each pair's
+ * geometry are shared; with a uniform v the pair factor of Eq. 5 is affine in u = (vhat . e)^2,
+ * Dcal = a_k u + b_k with a_k = 2 Gamma (aL - aT)|v| and b_k = 2 (Gamma - d)(aT|v| + Dm) - 2 (aL - aT)|v|,
+ * so a set costs a few operations per pair on top of the shared geometry.  Up to 8 sets per rate
+ * launch.  dt = p->dt if positive, else the smallest value of the dt rule over the sets.
+ *   theta_host [ntheta][3]; xq_dev [dim][n] (shared positions, updated in place); C_dev [ntheta][n]
+ *   (set k's field at C_dev + k n, caller order, updated in place).  1 <= ntheta <= 64.
+ * Positions, C and the workspace must stay valid until ade_sweep_destroy.  Velocity-field mode is
+ * not available here (ADE_ERR_ARG). */
+typedef struct ade_sweep ade_sweep;
+int ade_sweep_workspace_bytes(const ade_params *p, int n, int ntheta, size_t *bytes);
+int ade_sweep_init(ade_sweep **out, const ade_params *p, int n, int ntheta, const double *theta_host,
+                   uint32_t *xq_dev, float *C_dev, void *workspace_dev, size_t workspace_bytes);
+/* Support, common dt, grid; tile[0] = rate launches per evaluation (groups of sets). */
+int ade_sweep_get_info(const ade_sweep *sw, ade_info *info_host);
+/* Eq. 4 for every set at the current state: dCdt_dev [ntheta][n], caller order. */
+int ade_sweep_rate(ade_sweep *sw, float *dCdt_dev, void *stream);
+/* Ordered in-support pairs of the shared geometry (each set evaluates them all); waits. */
+int ade_sweep_count_pairs(ade_sweep *sw, long long *pairs_host, void *stream);
+/* nsteps predictor-corrector steps (Eq. 8-9) of every set; ade_sweep_run replays a captured graph. */
+int ade_sweep_step(ade_sweep *sw, int nsteps, void *stream);
+int ade_sweep_run(ade_sweep *sw, int nsteps, void *stream);
+/* One step bracketed by events; waits; phase_ms_host[4] = {cell build, predictors, correctors, 0}. */
+int ade_sweep_step_timed(ade_sweep *sw, double *phase_ms_host, void *stream);
+int ade_sweep_launches_per_step(const ade_sweep *sw, int *launches);
+/* FP64 mass, min and max per set (stats_host[ntheta]); waits. */
+int ade_sweep_stats(ade_sweep *sw, ade_stats *stats_host, void *stream);
+void ade_sweep_destroy(ade_sweep *sw);
+
 /* Cell build that allocates nothing (no counterpart in the paper: it is a service for callers).
  * Some callers cannot call cudaMalloc or give the library a workspace -- plug-ins handed only
  * their input and output buffers, code whose device memory belongs to another allocator, loops

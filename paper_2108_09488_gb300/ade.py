@@ -37,7 +37,10 @@ EXPORTS = ("ade_workspace_bytes", "ade_init_particles", "ade_get_info", "ade_bui
            "ade_batch_stats", "ade_batch_count_pairs", "ade_batch_get_plume_info",
            "ade_batch_autotune", "ade_batch_launches_per_step", "ade_batch_destroy",
            "ade_batch_step_timed", "ade_set_dispersivity", "ade_adjoint_workspace_bytes",
-           "ade_adjoint", "ade_autotune", "ade_set_velocity_field", "ade_alu_peaks")
+           "ade_adjoint", "ade_autotune", "ade_set_velocity_field", "ade_alu_peaks",
+           "ade_sweep_workspace_bytes", "ade_sweep_init", "ade_sweep_get_info", "ade_sweep_rate",
+           "ade_sweep_count_pairs", "ade_sweep_step", "ade_sweep_run", "ade_sweep_step_timed",
+           "ade_sweep_launches_per_step", "ade_sweep_stats", "ade_sweep_destroy")
 NOALLOC_MAX_PARTICLES = 1 << 20
 NOALLOC_MAX_CELLS = 1 << 20
 
@@ -117,6 +120,18 @@ def load():
         "ade_set_dispersivity": (I, [P, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
         "ade_set_velocity_field": (I, [P, P, V]),
         "ade_alu_peaks": (I, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), V]),
+        "ade_sweep_workspace_bytes": (I, [ctypes.POINTER(Params), I, I, ctypes.POINTER(SZ)]),
+        "ade_sweep_init": (I, [ctypes.POINTER(P), ctypes.POINTER(Params), I, I,
+                               ctypes.POINTER(ctypes.c_double), P, P, P, SZ]),
+        "ade_sweep_get_info": (I, [P, ctypes.POINTER(Info)]),
+        "ade_sweep_rate": (I, [P, P, V]),
+        "ade_sweep_count_pairs": (I, [P, ctypes.POINTER(LL), V]),
+        "ade_sweep_step": (I, [P, I, V]),
+        "ade_sweep_run": (I, [P, I, V]),
+        "ade_sweep_step_timed": (I, [P, ctypes.POINTER(ctypes.c_double), V]),
+        "ade_sweep_launches_per_step": (I, [P, ctypes.POINTER(I)]),
+        "ade_sweep_stats": (I, [P, P, V]),
+        "ade_sweep_destroy": (None, [P]),
         "ade_autotune": (I, [P, ctypes.POINTER(ctypes.c_double), V]),
         "ade_adjoint_workspace_bytes": (I, [P, I, I, ctypes.POINTER(SZ)]),
         "ade_adjoint": (I, [P, P, I, I, P, SZ, P, ctypes.POINTER(ctypes.c_double),
@@ -475,6 +490,93 @@ class Batch:
     def close(self):
         if self.ctx:
             load().ade_batch_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- parameter sweep ----------------------------------------------------------------------------
+def sweep_workspace_bytes(p, n, ntheta):
+    out = ctypes.c_size_t(0)
+    _check(load().ade_sweep_workspace_bytes(ctypes.byref(p), n, ntheta, ctypes.byref(out)))
+    return out.value
+
+
+class Sweep:
+    """P dispersivity sets theta[k] = (alpha_L, alpha_T, D_m) on one particle set through the
+    ade_sweep_* entry points.  ``C`` is a float32 [P][n] torch CUDA tensor (set k's field in row k),
+    ``xq`` the shared int32 [dim][n] positions; both are updated in place."""
+
+    def __init__(self, p, xq, C_sets, theta, device="cuda"):
+        import torch
+        self.torch = torch
+        self.p = p
+        xq = np.ascontiguousarray(xq, dtype=np.uint32)
+        self.dim, self.n = xq.shape
+        th = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1, 3)
+        self.P = th.shape[0]
+        C = np.array(np.broadcast_to(np.asarray(C_sets, dtype=np.float32), (self.P, self.n)))
+        self.xq = torch.from_numpy(xq.view(np.int32)).to(device).contiguous()
+        self.C = torch.from_numpy(C).to(device).contiguous()
+        nbytes = sweep_workspace_bytes(p, self.n, self.P)
+        self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        self.ws_ptr = (self.ws.data_ptr() + 255) // 256 * 256
+        self._theta = (ctypes.c_double * th.size)(*th.ravel().tolist())
+        self.ctx = ctypes.c_void_p()
+        _check(load().ade_sweep_init(ctypes.byref(self.ctx), ctypes.byref(p), self.n, self.P,
+                                     self._theta, self.xq.data_ptr(), self.C.data_ptr(), self.ws_ptr,
+                                     nbytes))
+        self.info = Info()
+        _check(load().ade_sweep_get_info(self.ctx, ctypes.byref(self.info)))
+
+    @property
+    def stream(self):
+        return ctypes.c_void_p(self.torch.cuda.current_stream().cuda_stream)
+
+    def rate(self):
+        out = self.torch.empty((self.P, max(self.n, 1)), dtype=self.torch.float32, device=self.C.device)
+        _check(load().ade_sweep_rate(self.ctx, out.data_ptr(), self.stream))
+        return out[:, : self.n]
+
+    def count_pairs(self):
+        v = ctypes.c_longlong(0)
+        _check(load().ade_sweep_count_pairs(self.ctx, ctypes.byref(v), self.stream))
+        return v.value
+
+    def step(self, nsteps=1):
+        _check(load().ade_sweep_step(self.ctx, nsteps, self.stream))
+
+    def run(self, nsteps):
+        _check(load().ade_sweep_run(self.ctx, nsteps, self.stream))
+
+    def step_timed(self):
+        out = (ctypes.c_double * 4)()
+        _check(load().ade_sweep_step_timed(self.ctx, out, self.stream))
+        return list(out)
+
+    def launches_per_step(self):
+        v = ctypes.c_int(0)
+        _check(load().ade_sweep_launches_per_step(self.ctx, ctypes.byref(v)))
+        return v.value
+
+    def stats(self):
+        st = (Stats * self.P)()
+        rc = load().ade_sweep_stats(self.ctx, st, self.stream)
+        if rc not in (ADE_OK, -3):
+            _check(rc)
+        return list(st)
+
+    def state(self):
+        self.torch.cuda.synchronize()
+        return self.xq.cpu().numpy().view(np.uint32), self.C.cpu().numpy()
+
+    def close(self):
+        if self.ctx:
+            load().ade_sweep_destroy(self.ctx)
             self.ctx = None
 
     def __del__(self):

@@ -73,6 +73,28 @@ struct FieldWork {
     unsigned *vmax_bits;     // max |v_a| as FP32 bits (ade_set_velocity_field)
 };
 
+// Parameter sweep (sweep.cu): one group of up to kSweepGroup parameter sets per launch.
+constexpr int kSweepGroup = 8;
+constexpr int kSweepMax = 64;     // parameter sets per sweep
+struct SweepParams {
+    float vh[3];                  // unit vector of the uniform velocity (x axis when v = 0)
+    float a[kSweepGroup];         // Dcal = a u + b per set of the group, u = (vhat . e)^2
+    float b[kSweepGroup];
+    int g0;                       // first set of the group
+    int nt;                       // sets in the group: 1, 2, 4 or 8
+    int P4;                       // stride of the interleaved sorted concentrations
+};
+
+struct SweepOut {
+    float *rate;                  // EPI_RATE: [P][n] caller order (may be NULL)
+    float *Cout;                  // EPI_PREDICT: sorted half-step concentrations [n][P4]
+    uint4 *Pout;                  // EPI_PREDICT: sorted half-step positions (group 0 writes)
+    float *C;                     // EPI_CORRECT: caller concentrations [P][n], updated in place
+    uint32_t *xq;                 // EPI_CORRECT: caller positions (group 0 writes)
+    int *status;                  // EPI_CORRECT: set to 1 on a non-finite C
+    unsigned long long *pairs;    // pair counter (counting launch)
+};
+
 // One work item of the batched rate kernel: `count` sorted particles of plume `plume` starting
 // at plume-local sorted index `start`.
 struct BatchTile {
@@ -153,6 +175,13 @@ cudaError_t launch_field_permute(int dim, const uint32_t *perm, int n, const Fie
 cudaError_t launch_rate_field(int dim, int kernel, int epi, const uint4 *Pe, const uint32_t *cell_start,
                               const uint32_t *perm, const FieldWork &fw, const RateParams &prm,
                               const FieldParams &fp, const EpiOut &out, cudaStream_t s);
+
+// Parameter sweep (sweep.cu).
+cudaError_t launch_sweep_gather(const uint32_t *perm, const float *C, int n, int P, int P4, float *Cs,
+                                cudaStream_t s);
+cudaError_t launch_rate_sweep(int dim, int kernel, int epi, bool count, const uint4 *Pe, const float *Ce,
+                              const uint32_t *cell_start, const uint32_t *perm, const RateParams &prm,
+                              const SweepParams &sp, const SweepOut &out, cudaStream_t s);
 
 int rate_blocks(int n);
 int rate_launch_blocks(int dim, const RateParams &prm, bool iso);

@@ -1689,3 +1689,438 @@ void ade_batch_destroy(ade_batch *b)
 }
 
 }  // extern "C"
+
+// =============================================================================================
+// Parameter sweep: one plume, P dispersivity sets sharing particles, velocity and time step.
+// =============================================================================================
+
+struct ade_sweep {
+    ade_params p;                      // geometry and velocity (dispersivities of set 0)
+    int n = 0, dim = 0, P = 0, P4 = 0;
+    int nc[3] = {1, 1, 1};
+    int ncells = 0;
+    uint32_t *xq = nullptr;
+    float *C = nullptr;                // caller concentrations [P][n]
+    ade::Work w;
+    float *Cs0 = nullptr, *Cs1 = nullptr;   // sorted, interleaved [n][P4] at l and l + 1/2
+    double *pstats = nullptr;               // {sum, min, max} per set
+    ade::RateParams rp;
+    std::vector<ade::SweepParams> groups;
+    std::vector<double> theta;              // [P][3]
+    double dt = 0.0, t = 0.0;
+    long long step = 0, pairs = 0;
+    uint32_t inc[3], inc_half[3];
+    bool status_cleared = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t ev[4];
+    bool ev_ready = false;
+};
+
+namespace {
+
+struct SweepLayout {
+    Derived d;
+    size_t Cs0, Cs1, pstats, total;
+};
+
+// Common parameters and workspace of a sweep.  theta may be NULL (workspace size only: the layout
+// does not depend on the dispersivities or the time step).
+int sweep_layout(const ade_params *p, int n, int P, const double *theta, ade_params *pp_out, SweepLayout *L)
+{
+    if (!p) return fail(ADE_ERR_ARG, "params is NULL");
+    if (P < 1 || P > ade::kSweepMax) return fail(ADE_ERR_ARG, "ntheta must be in 1..%d", ade::kSweepMax);
+    if (p->vmax > 0.0) return fail(ADE_ERR_ARG, "a sweep has a uniform velocity (vmax must be 0)");
+    if (p->flags != 0u && p->flags != ADE_FLAG_DIRECT) return fail(ADE_ERR_ARG, "a sweep uses the direct walk");
+    ade_params pp = *p;
+    pp.flags = ADE_FLAG_DIRECT;
+    if (theta) {
+        for (int k = 0; k < P; ++k)
+            for (int j = 0; j < 3; ++j)
+                if (!(theta[3 * k + j] >= 0.0) || !isfinite(theta[3 * k + j]))
+                    return fail(ADE_ERR_ARG, "theta[%d] must be finite and >= 0", k);
+        if (!(p->dt > 0.0)) {
+            // one time step for all sets: the smallest the rule gives over the sets (a set with a
+            // zero tensor does not disperse and sets no limit)
+            double dtmin = 0.0;
+            bool any = false;
+            for (int k = 0; k < P; ++k) {
+                ade_params q = pp;
+                q.alpha_L = theta[3 * k];
+                q.alpha_T = theta[3 * k + 1];
+                q.D_m = theta[3 * k + 2];
+                double D[9], dtk = 0.0, dmax = 0.0;
+                dispersion_tensor(q.dim == 3 ? 3 : 2, q.v, q.alpha_L, q.alpha_T, q.D_m, D);
+                for (int i = 0; i < 9; ++i) dmax = fmax(dmax, fabs(D[i]));
+                if (!(dmax > 0.0)) continue;
+                int rc = time_step(&q, D, &dtk);
+                if (rc) return rc;
+                dtmin = any ? std::min(dtmin, dtk) : dtk;
+                any = true;
+            }
+            if (!any) return fail(ADE_ERR_ARG, "every set has a zero dispersion tensor: give dt explicitly");
+            pp.dt = dtmin;
+        }
+        pp.alpha_L = theta[0];
+        pp.alpha_T = theta[1];
+        pp.D_m = theta[2];
+    } else if (!(pp.dt > 0.0)) {
+        pp.dt = 1.0;
+    }
+    int rc = derive(&pp, n, &L->d);
+    if (rc) return rc;
+    const int P4 = (P + 3) & ~3;
+    size_t off = L->d.L.total;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align256(bytes > 0 ? bytes : 1);
+        return o;
+    };
+    L->Cs0 = take((size_t)n * P4 * 4);
+    L->Cs1 = take((size_t)n * P4 * 4);
+    L->pstats = take((size_t)3 * P * 8);
+    L->total = off;
+    if (pp_out) *pp_out = pp;
+    return ADE_OK;
+}
+
+int sweep_cells(ade_sweep *sw, cudaStream_t s)
+{
+    ADE_CK(ade::launch_build_cells(sw->dim, sw->xq, sw->C, sw->n, sw->nc, sw->ncells, sw->w, s));
+    ADE_CK(ade::launch_sweep_gather(sw->w.perm, sw->C, sw->n, sw->P, sw->P4, sw->Cs0, s));
+    return ADE_OK;
+}
+
+// The evaluations of every group: predictors (all groups), or correctors (all groups).
+int sweep_evals(ade_sweep *sw, int ph, cudaStream_t s)
+{
+    ade::RateParams rp = sw->rp;
+    ade::SweepOut out;
+    memset(&out, 0, sizeof(out));
+    const uint4 *Pe = sw->w.P0;
+    const float *Ce = sw->Cs0;
+    int epi = ade::EPI_PREDICT;
+    if (ph == 1) {
+        rp.dt = (float)(0.5 * sw->dt);
+        for (int i = 0; i < 3; ++i) {
+            rp.inc[i] = sw->inc_half[i];
+            rp.back[i] = 0u;
+        }
+        out.Cout = sw->Cs1;
+        out.Pout = sw->w.P1;
+    } else {
+        epi = ade::EPI_CORRECT;
+        Pe = sw->w.P1;
+        Ce = sw->Cs1;
+        rp.dt = (float)sw->dt;
+        for (int i = 0; i < 3; ++i) {
+            rp.inc[i] = sw->inc[i];
+            rp.back[i] = sw->inc_half[i];
+        }
+        out.C = sw->C;
+        out.xq = sw->xq;
+        out.status = sw->w.status;
+    }
+    for (const ade::SweepParams &g : sw->groups)
+        ADE_CK(ade::launch_rate_sweep(sw->dim, sw->p.kernel, epi, false, Pe, Ce, sw->w.cell_start, sw->w.perm, rp,
+                                      g, out, s));
+    return ADE_OK;
+}
+
+int sweep_step(ade_sweep *sw, cudaStream_t s)
+{
+    int rc = sweep_cells(sw, s);
+    if (rc || sw->n == 0) return rc;
+    rc = sweep_evals(sw, 1, s);
+    if (rc) return rc;
+    return sweep_evals(sw, 2, s);
+}
+
+int sweep_clear_status_once(ade_sweep *sw, cudaStream_t s)
+{
+    if (!sw->status_cleared) {
+        ADE_CK(cudaMemsetAsync(sw->w.status, 0, sizeof(int), s));
+        sw->status_cleared = true;
+    }
+    return ADE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ade_sweep_workspace_bytes(const ade_params *p, int n, int ntheta, size_t *bytes)
+{
+    if (!bytes) return fail(ADE_ERR_ARG, "bytes is NULL");
+    SweepLayout L;
+    int rc = sweep_layout(p, n, ntheta, nullptr, nullptr, &L);
+    if (rc) return rc;
+    *bytes = L.total;
+    return ADE_OK;
+}
+
+int ade_sweep_init(ade_sweep **out, const ade_params *p, int n, int ntheta, const double *theta_host,
+                   uint32_t *xq_dev, float *C_dev, void *workspace_dev, size_t workspace_bytes)
+{
+    if (!out) return fail(ADE_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!theta_host) return fail(ADE_ERR_ARG, "theta_host is NULL");
+    ade_params pp;
+    SweepLayout L;
+    int rc = sweep_layout(p, n, ntheta, theta_host, &pp, &L);
+    if (rc) return rc;
+    if (n > 0 && (!xq_dev || !C_dev)) return fail(ADE_ERR_ARG, "xq_dev and C_dev must be non-NULL");
+    if (!workspace_dev || ((uintptr_t)workspace_dev & 255u) != 0u)
+        return fail(ADE_ERR_ARG, "workspace must be non-NULL and 256-byte aligned");
+    if (workspace_bytes < L.total)
+        return fail(ADE_ERR_CAPACITY, "workspace too small: %zu < %zu bytes", workspace_bytes, L.total);
+    ade_sweep *sw = new (std::nothrow) ade_sweep;
+    if (!sw) return fail(ADE_ERR_CAPACITY, "out of host memory");
+    sw->p = pp;
+    sw->n = n;
+    sw->dim = pp.dim;
+    sw->P = ntheta;
+    sw->P4 = (ntheta + 3) & ~3;
+    for (int i = 0; i < 3; ++i) sw->nc[i] = L.d.g.nc[i];
+    sw->ncells = L.d.g.ncells;
+    sw->xq = xq_dev;
+    sw->C = C_dev;
+    const Layout &W = L.d.L;
+    sw->w.keys = at<uint32_t>(workspace_dev, W.keys);
+    sw->w.rank = at<uint32_t>(workspace_dev, W.rank);
+    sw->w.count = at<uint32_t>(workspace_dev, W.count);
+    sw->w.block_sums = at<uint32_t>(workspace_dev, W.block_sums);
+    sw->w.perm_tmp = at<uint32_t>(workspace_dev, W.perm_tmp);
+    sw->w.perm = at<uint32_t>(workspace_dev, W.perm);
+    sw->w.cell_start = at<uint32_t>(workspace_dev, W.cell_start);
+    sw->w.P0 = at<uint4>(workspace_dev, W.P0);
+    sw->w.P1 = at<uint4>(workspace_dev, W.P1);
+    sw->w.partials = at<double>(workspace_dev, W.partials);
+    sw->w.stats = at<double>(workspace_dev, W.stats);
+    sw->w.cf_partials = at<double>(workspace_dev, W.cf_partials);
+    sw->w.status = at<int>(workspace_dev, W.status);
+    sw->w.done = at<unsigned>(workspace_dev, W.done);
+    sw->w.pairs = at<unsigned long long>(workspace_dev, W.pairs);
+    sw->Cs0 = at<float>(workspace_dev, L.Cs0);
+    sw->Cs1 = at<float>(workspace_dev, L.Cs1);
+    sw->pstats = at<double>(workspace_dev, L.pstats);
+    double D[9];
+    bool iso = false;
+    rc = plume_constants(&pp, n, L.d, D, &sw->dt, sw->inc, sw->inc_half, &sw->rp, &iso);
+    if (rc) {
+        delete sw;
+        return rc;
+    }
+    sw->rp.variant = 0;
+    sw->theta.assign(theta_host, theta_host + 3 * ntheta);
+    // Dcal = a u + b per set (uniform v, K = 2D)
+    const int dm = pp.dim;
+    double vabs = 0.0;
+    for (int i = 0; i < dm; ++i) vabs += pp.v[i] * pp.v[i];
+    vabs = sqrt(vabs);
+    const double gamma = pp.gamma > 0.0 ? pp.gamma : dm + 2.0;
+    ade::SweepParams base;
+    memset(&base, 0, sizeof(base));
+    for (int i = 0; i < 3; ++i) base.vh[i] = vabs > 0.0 ? (float)(i < dm ? pp.v[i] / vabs : 0.0) : (i == 0 ? 1.f : 0.f);
+    base.P4 = sw->P4;
+    for (int g0 = 0; g0 < ntheta;) {
+        int nt = ade::kSweepGroup;
+        while (nt > ntheta - g0) nt >>= 1;
+        ade::SweepParams g = base;
+        g.g0 = g0;
+        g.nt = nt;
+        for (int k = 0; k < nt; ++k) {
+            const double aL = theta_host[3 * (g0 + k)], aT = theta_host[3 * (g0 + k) + 1],
+                         Dm = theta_host[3 * (g0 + k) + 2];
+            g.a[k] = (float)(2.0 * gamma * (aL - aT) * vabs);
+            g.b[k] = (float)(2.0 * (gamma - dm) * (aT * vabs + Dm) - 2.0 * (aL - aT) * vabs);
+        }
+        sw->groups.push_back(g);
+        g0 += nt;
+    }
+    *out = sw;
+    return ADE_OK;
+}
+
+int ade_sweep_get_info(const ade_sweep *sw, ade_info *info)
+{
+    if (!sw || !info) return fail(ADE_ERR_ARG, "NULL argument");
+    memset(info, 0, sizeof(*info));
+    info->support = sw->p.kernel == ADE_WENDLAND_C2 ? 2.0 * sw->p.h : sw->p.h;
+    info->dt = sw->dt;
+    for (int i = 0; i < 3; ++i) info->nc[i] = sw->nc[i];
+    info->ncells = sw->ncells;
+    info->cell_subdiv = sw->rp.k;
+    info->stencil_rows = sw->rp.nrows;
+    info->sort_passes = 1;
+    info->tile[0] = (int)sw->groups.size();   // launches per evaluation
+    return ADE_OK;
+}
+
+int ade_sweep_rate(ade_sweep *sw, float *dCdt_dev, void *stream)
+{
+    if (!sw) return fail(ADE_ERR_ARG, "sweep is NULL");
+    if (sw->n > 0 && !dCdt_dev) return fail(ADE_ERR_ARG, "dCdt_dev is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = sweep_cells(sw, s);
+    if (rc || sw->n == 0) return rc;
+    ade::SweepOut out;
+    memset(&out, 0, sizeof(out));
+    out.rate = dCdt_dev;
+    for (const ade::SweepParams &g : sw->groups)
+        ADE_CK(ade::launch_rate_sweep(sw->dim, sw->p.kernel, ade::EPI_RATE, false, sw->w.P0, sw->Cs0,
+                                      sw->w.cell_start, sw->w.perm, sw->rp, g, out, s));
+    return ADE_OK;
+}
+
+int ade_sweep_count_pairs(ade_sweep *sw, long long *pairs_host, void *stream)
+{
+    if (!sw || !pairs_host) return fail(ADE_ERR_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    *pairs_host = 0;
+    int rc = sweep_cells(sw, s);
+    if (rc || sw->n == 0) return rc;
+    ADE_CK(cudaMemsetAsync(sw->w.pairs, 0, 8, s));
+    ade::SweepOut out;
+    memset(&out, 0, sizeof(out));
+    out.pairs = sw->w.pairs;
+    ADE_CK(ade::launch_rate_sweep(sw->dim, sw->p.kernel, ade::EPI_RATE, true, sw->w.P0, sw->Cs0, sw->w.cell_start,
+                                  sw->w.perm, sw->rp, sw->groups[0], out, s));
+    unsigned long long v = 0;
+    ADE_CK(cudaMemcpyAsync(&v, sw->w.pairs, 8, cudaMemcpyDeviceToHost, s));
+    ADE_CK(cudaStreamSynchronize(s));
+    sw->pairs = (long long)v;
+    *pairs_host = (long long)v;
+    return ADE_OK;
+}
+
+int ade_sweep_step(ade_sweep *sw, int nsteps, void *stream)
+{
+    if (!sw) return fail(ADE_ERR_ARG, "sweep is NULL");
+    if (nsteps < 0) return fail(ADE_ERR_ARG, "nsteps must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = sweep_clear_status_once(sw, s);
+    if (rc) return rc;
+    for (int k = 0; k < nsteps; ++k) {
+        rc = sweep_step(sw, s);
+        if (rc) return rc;
+    }
+    sw->step += nsteps;
+    sw->t += nsteps * sw->dt;
+    return ADE_OK;
+}
+
+int ade_sweep_run(ade_sweep *sw, int nsteps, void *stream)
+{
+    if (!sw) return fail(ADE_ERR_ARG, "sweep is NULL");
+    if (nsteps < 0) return fail(ADE_ERR_ARG, "nsteps must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = sweep_clear_status_once(sw, s);
+    if (rc) return rc;
+    if (!sw->graph_exec && nsteps > 0) {
+        if (!sw->cap_stream) ADE_CK(cudaStreamCreateWithFlags(&sw->cap_stream, cudaStreamNonBlocking));
+        ADE_CK(cudaStreamBeginCapture(sw->cap_stream, cudaStreamCaptureModeThreadLocal));
+        rc = sweep_step(sw, sw->cap_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(sw->cap_stream, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        ADE_CK(e);
+        cudaError_t ei = cudaGraphInstantiate(&sw->graph_exec, g, 0);
+        if (ei != cudaSuccess) {
+            cudaGraphDestroy(g);
+            sw->graph_exec = nullptr;
+            return fail(ADE_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ei));
+        }
+        sw->graph = g;
+    }
+    for (int k = 0; k < nsteps; ++k) ADE_CK(cudaGraphLaunch(sw->graph_exec, s));
+    sw->step += nsteps;
+    sw->t += nsteps * sw->dt;
+    return ADE_OK;
+}
+
+int ade_sweep_step_timed(ade_sweep *sw, double *phase_ms, void *stream)
+{
+    if (!sw || !phase_ms) return fail(ADE_ERR_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = sweep_clear_status_once(sw, s);
+    if (rc) return rc;
+    if (!sw->ev_ready) {
+        for (int k = 0; k < 4; ++k) ADE_CK(cudaEventCreate(&sw->ev[k]));
+        sw->ev_ready = true;
+    }
+    ADE_CK(cudaEventRecord(sw->ev[0], s));
+    rc = sweep_cells(sw, s);
+    if (rc) return rc;
+    ADE_CK(cudaEventRecord(sw->ev[1], s));
+    if (sw->n > 0) {
+        rc = sweep_evals(sw, 1, s);
+        if (rc) return rc;
+    }
+    ADE_CK(cudaEventRecord(sw->ev[2], s));
+    if (sw->n > 0) {
+        rc = sweep_evals(sw, 2, s);
+        if (rc) return rc;
+    }
+    ADE_CK(cudaEventRecord(sw->ev[3], s));
+    ADE_CK(cudaEventSynchronize(sw->ev[3]));
+    for (int k = 0; k < 3; ++k) {
+        float ms = 0.f;
+        ADE_CK(cudaEventElapsedTime(&ms, sw->ev[k], sw->ev[k + 1]));
+        phase_ms[k] = ms;
+    }
+    phase_ms[3] = 0.0;
+    sw->step += 1;
+    sw->t += sw->dt;
+    return ADE_OK;
+}
+
+int ade_sweep_launches_per_step(const ade_sweep *sw, int *launches)
+{
+    if (!sw || !launches) return fail(ADE_ERR_ARG, "NULL argument");
+    // count, 3 scan launches, place, order, gather; one predictor and one corrector per group
+    *launches = sw->n > 0 ? 7 + 2 * (int)sw->groups.size() : 4;
+    return ADE_OK;
+}
+
+int ade_sweep_stats(ade_sweep *sw, ade_stats *st, void *stream)
+{
+    if (!sw || !st) return fail(ADE_ERR_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = sweep_clear_status_once(sw, s);
+    if (rc) return rc;
+    for (int k = 0; k < sw->P; ++k)
+        ADE_CK(ade::launch_state_stats(sw->C + (size_t)k * sw->n, sw->n, sw->w.partials, sw->pstats + 3 * k, s));
+    std::vector<double> h(3 * (size_t)sw->P);
+    int status = 0;
+    ADE_CK(cudaMemcpyAsync(h.data(), sw->pstats, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    ADE_CK(cudaMemcpyAsync(&status, sw->w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ADE_CK(cudaStreamSynchronize(s));
+    for (int k = 0; k < sw->P; ++k) {
+        st[k].mass = h[3 * k] * sw->p.mass;
+        st[k].c_min = h[3 * k + 1];
+        st[k].c_max = h[3 * k + 2];
+        st[k].t = sw->t;
+        st[k].step = sw->step;
+        st[k].pairs = sw->pairs;
+        st[k].status = status ? ADE_ERR_NUMERIC : ADE_OK;
+    }
+    return status ? fail(ADE_ERR_NUMERIC, "non-finite concentration produced") : ADE_OK;
+}
+
+void ade_sweep_destroy(ade_sweep *sw)
+{
+    if (!sw) return;
+    if (sw->graph_exec) cudaGraphExecDestroy(sw->graph_exec);
+    if (sw->graph) cudaGraphDestroy(sw->graph);
+    if (sw->cap_stream) cudaStreamDestroy(sw->cap_stream);
+    if (sw->ev_ready)
+        for (int k = 0; k < 4; ++k) cudaEventDestroy(sw->ev[k]);
+    delete sw;
+}
+
+}  // extern "C"

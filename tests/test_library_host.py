@@ -205,3 +205,41 @@ def test_velocity_field_mode_call_order(adelib):
         adelib.batch_workspace_bytes([adelib.params_for(q, vmax=0.2) for q in plumes],
                                      [q.n for q in plumes])
     assert e.value.code == -1
+
+
+def test_sweep_host_validation_and_info(adelib, orc):
+    """Sweep set-up without device work: argument checks, the common time step (the smallest of
+    the oracle's rule over the sets) and the grouping of sets into launches."""
+    import ctypes
+    plume = inputs.ladder_2d(256, 10)
+    p = adelib.params_for(plume)
+    for bad_n in (0, 65):
+        with pytest.raises(adelib.AdeError):
+            adelib.sweep_workspace_bytes(p, plume.n, bad_n)
+    with pytest.raises(adelib.AdeError):
+        adelib.sweep_workspace_bytes(adelib.params_for(plume, vmax=0.2), plume.n, 3)
+    with pytest.raises(adelib.AdeError):
+        adelib.sweep_workspace_bytes(adelib.params_for(plume, flags=2), plume.n, 3)
+    theta = np.array([[1e-2, 1e-3, 1e-6], [5e-2, 1e-3, 1e-6], [1e-3, 1e-3, 0.0]] * 4)   # 12 sets
+    nbytes = adelib.sweep_workspace_bytes(p, plume.n, len(theta))
+    assert nbytes >= 2 * 4 * 12 * plume.n
+    lib = adelib.load()
+    ctx = ctypes.c_void_p()
+    th = (ctypes.c_double * theta.size)(*theta.ravel().tolist())
+    assert lib.ade_sweep_init(ctypes.byref(ctx), ctypes.byref(p), plume.n, len(theta), th, FAKE,
+                              FAKE + (1 << 30), FAKE + (2 << 30), nbytes) == 0
+    try:
+        info = adelib.Info()
+        assert lib.ade_sweep_get_info(ctx, ctypes.byref(info)) == 0
+        dts = [orc.dt_rule(orc.dispersion_tensor(plume.velocity, *t), plume.h) for t in theta]
+        assert info.dt == pytest.approx(min(dts), rel=1e-14)
+        assert info.tile[0] == 2                      # 12 sets = one group of 8 + one of 4
+        v = ctypes.c_int(0)
+        assert lib.ade_sweep_launches_per_step(ctx, ctypes.byref(v)) == 0 and v.value == 7 + 4
+    finally:
+        lib.ade_sweep_destroy(ctx)
+    bad = theta.copy()
+    bad[3, 1] = -1.0
+    th = (ctypes.c_double * bad.size)(*bad.ravel().tolist())
+    assert lib.ade_sweep_init(ctypes.byref(ctx), ctypes.byref(p), plume.n, len(bad), th, FAKE,
+                              FAKE + (1 << 30), FAKE + (2 << 30), nbytes) == -1
