@@ -75,6 +75,9 @@ def _load():
             lib.orc_rate_sel.restype = _ll
             lib.orc_step.argtypes = [_i, _i, _p, _p, _p, _p, _p, _p, _i, _d, _d, _d, _d, _d, _d, _i]
             lib.orc_step.restype = _ll
+            lib.orc_step_cattaneo.argtypes = [_i, _i, _p, _p, _p, _p, _p, _p, _p, _i, _d, _d, _d, _d,
+                                              _d, _d, _d, _i]
+            lib.orc_step_cattaneo.restype = _ll
             lib.orc_cell_keys.argtypes = [_i, _i, _p, _p, _p]
             lib.orc_sort_cells.argtypes = [_i, _p, _i, _p, _p]
             lib.orc_sort_cells.restype = _i
@@ -230,6 +233,27 @@ def step(x, v, C, m, rho, box, kind, H, gamma, alpha_L, alpha_T, D_m, dt, nsteps
         pairs += lib.orc_step(dim, n, _ptr(x), _ptr(v), _ptr(C), _ptr(m), _ptr(rho), _ptr(box),
                               kind, H, gamma, alpha_L, alpha_T, D_m, dt, int(brute))
     return x, C, pairs
+
+
+def step_cattaneo(x, v, C, Q, m, rho, box, kind, H, gamma, alpha_L, alpha_T, D_m, dt, tau,
+                  nsteps=1, brute=False):
+    """Eq. 14 (Cattaneo's hyperbolic form) as the system dC/dt = Q, tau dQ/dt = R(C) - Q, advanced
+    by the midpoint rule of Eq. 8-9.  Returns new (x, C, Q, pairs)."""
+    x = _f64(x).copy()
+    n, dim = x.shape
+    v = _per_particle(v, n, dim)
+    C = _f64(C).ravel().copy()
+    Q = _f64(Q).ravel().copy()
+    m = _per_particle(m, n)
+    rho = _per_particle(rho, n)
+    box = _f64(box).ravel()
+    pairs = 0
+    lib = _load()
+    for _ in range(nsteps):
+        pairs += lib.orc_step_cattaneo(dim, n, _ptr(x), _ptr(v), _ptr(C), _ptr(Q), _ptr(m), _ptr(rho),
+                                       _ptr(box), kind, H, gamma, alpha_L, alpha_T, D_m, dt, tau,
+                                       int(brute))
+    return x, C, Q, pairs
 
 
 # --------------------------------------------------------------------------------------------

@@ -410,6 +410,50 @@ long long orc_step(int dim, int n, double *x, const double *v, double *C, const 
 }
 
 /* ------------------------------------------------------------------------- */
+/* Eq. 14 (Sec. 5): Cattaneo's hyperbolic form                               */
+/*   tau d2C/dt2 + dC/dt = R(C),  R = the right-hand side of Eq. 1 (Eq. 4).  */
+/* Written as the first-order system dC/dt = Q, tau dQ/dt = R(C) - Q and     */
+/* advanced by the midpoint rule of Eq. 8-9 applied to (C, Q):               */
+/*   C^{l+1/2} = C^l + dt/2 Q^l,   Q^{l+1/2} = Q^l + dt/2 (R(C^l) - Q^l)/tau  */
+/*   C^{l+1}   = C^l + dt Q^{l+1/2},                                        */
+/*   Q^{l+1}   = Q^l + dt (R(C^{l+1/2}) - Q^{l+1/2})/tau                     */
+/* with R evaluated at x^l and x^{l+1/2} as in orc_step.  In place on x, C,   */
+/* Q.  Returns the in-support pairs of the two evaluations.                  */
+/* ------------------------------------------------------------------------- */
+long long orc_step_cattaneo(int dim, int n, double *x, const double *v, double *C, double *Q,
+                            const double *m, const double *rho, const double *box, int kind,
+                            double H, double gamma, double aL, double aT, double Dm, double dt,
+                            double tau, int use_brute)
+{
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    double *r = (double *)malloc(sizeof(double) * nn);
+    double *Ch = (double *)malloc(sizeof(double) * nn);
+    double *Qh = (double *)malloc(sizeof(double) * nn);
+    double *xh = (double *)malloc(sizeof(double) * nn * dim);
+    long long pairs = orc_rate(dim, n, x, v, C, m, rho, box, kind, H, gamma, aL, aT, Dm,
+                               use_brute, r, NULL, NULL);
+    for (int a = 0; a < n; ++a) {
+        Ch[a] = C[a] + 0.5 * dt * Q[a];
+        Qh[a] = Q[a] + 0.5 * dt * (r[a] - Q[a]) / tau;
+        for (int i = 0; i < dim; ++i)
+            xh[(size_t)a * dim + i] = wrap(x[(size_t)a * dim + i] + 0.5 * dt * v[(size_t)a * dim + i], box[i]);
+    }
+    pairs += orc_rate(dim, n, xh, v, Ch, m, rho, box, kind, H, gamma, aL, aT, Dm, use_brute, r,
+                      NULL, NULL);
+    for (int a = 0; a < n; ++a) {
+        C[a] = C[a] + dt * Qh[a];
+        Q[a] = Q[a] + dt * (r[a] - Qh[a]) / tau;
+        for (int i = 0; i < dim; ++i)
+            x[(size_t)a * dim + i] = wrap(x[(size_t)a * dim + i] + dt * v[(size_t)a * dim + i], box[i]);
+    }
+    free(r);
+    free(Ch);
+    free(Qh);
+    free(xh);
+    return pairs;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Cell list on fixed-point positions (integer only, so the result is exact). */
 /* A position u in [0, L) is stored as xq = round(u / L * 2^32) mod 2^32.     */
 /* Cell index along an axis with nc cells: (xq * nc) >> 32.                  */
