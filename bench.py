@@ -46,6 +46,7 @@ WORKLOADS = {
     "paper-4m-n80k-c4": lambda: inputs.paper_plume(2000, 0.1),
     "batched-64": None,          # 64 uneven 2D plumes in one batch (inputs.batched_2d)
     "sweep-512-8": None,         # 8 dispersivity sets on the 512^2 rung sharing one cell list
+    "cattaneo-1024-n120-r10": lambda: inputs.ladder_2d(1024, 10),   # Eq. 14 with tau = 2 dt
     "adjoint-512": None,         # gradient of the misfit: 512^2, 400 steps, checkpoints every 40
 }
 # velocity-field workloads: vmax of the smooth seeded field (inputs.velocity_field, speed 0.1,
@@ -681,9 +682,16 @@ def run_ours(args):
     plume = WORKLOADS[args.workload]()
     xq, C = plume.initial_state()
     v, vmax, plume = field_setup(args.workload, plume, xq)
-    sim = ade.Simulation(ade.params_for(plume, vmax=vmax), xq, C, device=device)
+    tau = 0.0
+    if args.workload.startswith("cattaneo-"):
+        # relaxation time of Eq. 14: twice the parabolic step 0.1 h^2 / lambda_max(D)
+        lam = max(plume.alpha_L, plume.alpha_T) * plume.speed + plume.D_m
+        tau = 2.0 * 0.1 * plume.h ** 2 / lam
+    sim = ade.Simulation(ade.params_for(plume, vmax=vmax, tau=tau), xq, C, device=device)
     if v is not None:
         sim.set_velocity_field(v)
+    if tau > 0.0:
+        sim.set_flux()            # Q(0) = R(C(0)); the flux stays resident between e2e steps
     tune_ms = sim.autotune()
     pairs = sim.count_pairs()
     launches = ade.launches_per_step(sim.ctx)

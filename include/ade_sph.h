@@ -79,6 +79,10 @@ typedef struct ade_params {
                           its own constant velocity (ade_set_velocity_field), |v_a| <= vmax; v is
                           then unused, the dt rules take |v| = vmax, and the cell grid is sized for
                           H + dt vmax (see ade_set_velocity_field). */
+    double tau;        /* 0: Eq. 1 (Fick).  > 0: Cattaneo's form, Eq. 14 (Sec. 5), with relaxation
+                          time tau: tau d2C/dt2 + dC/dt = R(C), advanced as dC/dt = Q,
+                          tau dQ/dt = R - Q by the midpoint rule of Eq. 8-9 (see ade_set_flux); the
+                          dt rules are capped at tau.  Uniform velocity, single plume only. */
 } ade_params;
 
 /* FP64 diagnostics of the current state. */
@@ -193,6 +197,18 @@ int ade_set_dispersivity(ade_ctx *ctx, double alpha_L, double alpha_T, double D_
  *   (ADE_ERR_ARG otherwise; the context then has no field).  Waits for the stream.  Until a field
  *   is set, rate, pair-count and step calls return ADE_ERR_STATE. */
 int ade_set_velocity_field(ade_ctx *ctx, const float *v_dev, void *stream);
+
+/* ---- Cattaneo form (Eq. 14) ---------------------------------------------------------------------
+ * For a context created with tau > 0 the state is (x, C, Q), Q = dC/dt the relaxing flux; a step
+ * is C^{l+1/2} = C^l + dt/2 Q^l, Q^{l+1/2} = Q^l + dt/2 (R(C^l) - Q^l)/tau, then
+ * C^{l+1} = C^l + dt Q^{l+1/2}, Q^{l+1} = Q^l + dt (R(C^{l+1/2}) - Q^{l+1/2})/tau, with positions as
+ * in Eq. 8-9.  The flux lives in the workspace (caller order).  ade_set_flux sets it from
+ * Q_dev [n] (device, caller order, copied) or, with Q_dev NULL, to R(C) at the current state (the
+ * Fickian flux: the parabolic solution's initial rate, and sum Q = 0 so sum m C is conserved).
+ * Steps return ADE_ERR_STATE until a flux is set.  ade_get_flux copies it to Q_dev [n].  Neither
+ * waits. */
+int ade_set_flux(ade_ctx *ctx, const float *Q_dev, void *stream);
+int ade_get_flux(ade_ctx *ctx, float *Q_dev, void *stream);
 
 /* ---- Adjoint (dispersivity inversion) ---------------------------------------------------------
  * The paper has no adjoint; it is derived from Eq. 3-5 and Eq. 8-9 for the uniform-velocity case.

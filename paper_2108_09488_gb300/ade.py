@@ -40,7 +40,8 @@ EXPORTS = ("ade_workspace_bytes", "ade_init_particles", "ade_get_info", "ade_bui
            "ade_adjoint", "ade_autotune", "ade_set_velocity_field", "ade_alu_peaks",
            "ade_sweep_workspace_bytes", "ade_sweep_init", "ade_sweep_get_info", "ade_sweep_rate",
            "ade_sweep_count_pairs", "ade_sweep_step", "ade_sweep_run", "ade_sweep_step_timed",
-           "ade_sweep_launches_per_step", "ade_sweep_stats", "ade_sweep_destroy")
+           "ade_sweep_launches_per_step", "ade_sweep_stats", "ade_sweep_destroy", "ade_set_flux",
+           "ade_get_flux")
 NOALLOC_MAX_PARTICLES = 1 << 20
 NOALLOC_MAX_CELLS = 1 << 20
 
@@ -57,7 +58,8 @@ class Params(ctypes.Structure):
                 ("D_m", ctypes.c_double), ("v", ctypes.c_double * 3), ("mass", ctypes.c_double),
                 ("rho", ctypes.c_double), ("gamma", ctypes.c_double), ("dt", ctypes.c_double),
                 ("dt_rule", ctypes.c_int), ("dt_coef", ctypes.c_double),
-                ("cell_subdiv", ctypes.c_int), ("flags", ctypes.c_uint), ("vmax", ctypes.c_double)]
+                ("cell_subdiv", ctypes.c_int), ("flags", ctypes.c_uint), ("vmax", ctypes.c_double),
+                ("tau", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -119,6 +121,8 @@ def load():
         "ade_batch_step_timed": (I, [P, ctypes.POINTER(ctypes.c_double), V]),
         "ade_set_dispersivity": (I, [P, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
         "ade_set_velocity_field": (I, [P, P, V]),
+        "ade_set_flux": (I, [P, P, V]),
+        "ade_get_flux": (I, [P, P, V]),
         "ade_alu_peaks": (I, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), V]),
         "ade_sweep_workspace_bytes": (I, [ctypes.POINTER(Params), I, I, ctypes.POINTER(SZ)]),
         "ade_sweep_init": (I, [ctypes.POINTER(P), ctypes.POINTER(Params), I, I,
@@ -155,7 +159,8 @@ def _check(rc):
 
 
 def params(dim, h, alpha_L, alpha_T, D_m, v, mass, rho=1.0, box=1.0, kernel=WENDLAND_C2,
-           gamma=0.0, dt=0.0, dt_rule=DT_LAMBDA_MAX, dt_coef=0.0, cell_subdiv=0, flags=0, vmax=0.0):
+           gamma=0.0, dt=0.0, dt_rule=DT_LAMBDA_MAX, dt_coef=0.0, cell_subdiv=0, flags=0, vmax=0.0,
+           tau=0.0):
     p = Params()
     p.dim = dim
     p.kernel = kernel
@@ -168,6 +173,7 @@ def params(dim, h, alpha_L, alpha_T, D_m, v, mass, rho=1.0, box=1.0, kernel=WEND
     p.mass, p.rho, p.gamma, p.dt = mass, rho, gamma, dt
     p.dt_rule, p.dt_coef, p.cell_subdiv, p.flags = dt_rule, dt_coef, cell_subdiv, flags
     p.vmax = vmax
+    p.tau = tau
     return p
 
 
@@ -347,6 +353,24 @@ class Simulation:
 
     def set_dispersivity(self, alpha_L, alpha_T, D_m):
         _check(load().ade_set_dispersivity(self.ctx, alpha_L, alpha_T, D_m))
+
+    def set_flux(self, Q=None):
+        """Cattaneo form (tau > 0): set the flux Q = dC/dt (float32 [n], caller order), or with
+        None the Fickian flux R(C) of the current state (ade_set_flux)."""
+        t = self.torch
+        if Q is None:
+            _check(load().ade_set_flux(self.ctx, None, self.stream))
+            return
+        q = t.as_tensor(np.ascontiguousarray(Q, dtype=np.float32) if not t.is_tensor(Q) else Q,
+                        dtype=t.float32, device=self.C.device).contiguous()
+        _check(load().ade_set_flux(self.ctx, q.data_ptr() if self.n else None, self.stream))
+        t.cuda.current_stream().synchronize()
+
+    def flux(self):
+        """The current flux Q (Cattaneo form) as a torch tensor [n]."""
+        out = self.torch.empty(max(self.n, 1), dtype=self.torch.float32, device=self.C.device)
+        _check(load().ade_get_flux(self.ctx, out.data_ptr(), self.stream))
+        return out[: self.n]
 
     def set_velocity_field(self, v):
         """Per-particle velocities (float32 [dim][n], caller order) of a context created with

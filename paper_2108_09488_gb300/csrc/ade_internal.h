@@ -112,6 +112,9 @@ struct EpiOut {
     unsigned *done;           // EPI_CORRECT: blocks finished (the last block resets it to 0)
     int *status;              // EPI_CORRECT: set to 1 on a non-finite C
     unsigned long long *pairs; // optional in-support pair counter
+    float *Q;                 // Eq. 14 (NULL: Eq. 1): flux dC/dt in caller order, updated by the corrector
+    float *Qh;                // Eq. 14: sorted half-step flux (predictor writes, corrector reads)
+    float tau_inv;            // Eq. 14: 1 / tau
 };
 
 enum Epilogue { EPI_RATE = 0, EPI_PREDICT = 1, EPI_CORRECT = 2 };
@@ -224,6 +227,11 @@ struct ade_ctx {
     bool field;
     bool field_set;       // a valid field has been copied in
     bool field_dirty;     // tensors must be re-formed (dispersivities changed)
+    // Cattaneo form (Eq. 14, p.tau > 0)
+    bool catt;
+    bool flux_set;        // Q holds a flux (ade_set_flux)
+    float *Q;             // [n] caller order
+    float *Qh;            // [n] sorted half-step flux
     double Hgrid;         // radius the cell grid is built for: H, or H + skin in field mode
     double skin;
     ade::FieldParams fp;  // constants (scales set per use)

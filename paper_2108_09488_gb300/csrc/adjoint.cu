@@ -336,6 +336,7 @@ extern "C" int ade_adjoint(ade_ctx *c, const float *C_target_dev, int nsteps, in
     if (!c || !C_target_dev || nsteps < 1 || ckpt_every < 1 || !aws)
         return ade::report_error(ADE_ERR_ARG, "bad argument");
     if (c->field) return ade::report_error(ADE_ERR_STATE, "the adjoint is for a uniform velocity (vmax = 0)");
+    if (c->catt) return ade::report_error(ADE_ERR_STATE, "the adjoint is for Eq. 1 (tau = 0)");
     const AdjLayout L = adj_layout(c->n, nsteps, ckpt_every);
     if (aws_bytes < L.total || ((uintptr_t)aws & 255u)) return ade::report_error(ADE_ERR_CAPACITY, "adjoint workspace too small or misaligned");
     const int n = c->n;

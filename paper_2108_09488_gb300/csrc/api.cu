@@ -112,6 +112,8 @@ int time_step(const ade_params *p, const double *D, double *dt_out)
         }
         if (!(den > 0.0)) return fail(ADE_ERR_ARG, "dispersion tensor is zero: give dt explicitly");
         dt = coef * p->h * p->h / den;
+        // Eq. 14: the flux relaxes with rate 1/tau; the explicit midpoint rule needs dt <= ~2 tau
+        if (p->tau > 0.0) dt = fmin(dt, p->tau);
     }
     *dt_out = dt;
     return ADE_OK;
@@ -234,6 +236,9 @@ int validate(const ade_params *p, int n)
     if (!(p->vmax >= 0.0) || !isfinite(p->vmax)) return fail(ADE_ERR_ARG, "vmax must be finite and >= 0");
     if (p->vmax > 0.0 && p->flags != 0u && p->flags != ADE_FLAG_DIRECT)
         return fail(ADE_ERR_ARG, "velocity-field mode uses the direct walk: flags must be 0 or ADE_FLAG_DIRECT");
+    if (!(p->tau >= 0.0) || !isfinite(p->tau)) return fail(ADE_ERR_ARG, "tau must be finite and >= 0");
+    if (p->tau > 0.0 && p->vmax > 0.0)
+        return fail(ADE_ERR_ARG, "the Cattaneo form (tau > 0) is available with a uniform velocity only");
     const double H = p->kernel == ADE_WENDLAND_C2 ? 2.0 * p->h : p->h;
     for (int i = 0; i < p->dim; ++i)
         if (!(H < 0.5 * p->box[i])) return fail(ADE_ERR_ARG, "support radius must be < box/2 (minimum image)");
@@ -290,11 +295,11 @@ void choose_tiles(int dim, int n, const Grid &g, bool iso, unsigned flags, ade::
 
 struct Layout {
     size_t keys, rank, count, block_sums, perm_tmp, perm, cell_start, P0, P1, partials, stats,
-        cf_partials, status, done, pairs, fVc, fDAc, fDBc, fIncC, fV, fDA, fDB, fInc, fbits, total;
+        cf_partials, status, done, pairs, fVc, fDAc, fDBc, fIncC, fV, fDA, fDB, fInc, fbits, Q, Qh, total;
 };
 
 // field_dim: 0 for a uniform velocity, else dim (velocity-field buffers are added at the end).
-Layout layout(int n, int ncells, int nb_partials, int field_dim = 0)
+Layout layout(int n, int ncells, int nb_partials, int field_dim = 0, bool catt = false)
 {
     Layout L;
     size_t off = 0;
@@ -330,6 +335,11 @@ Layout layout(int n, int ncells, int nb_partials, int field_dim = 0)
         L.fDB = take(rec3);
         L.fInc = take(rec);
         L.fbits = take(64);
+    }
+    L.Q = L.Qh = 0;
+    if (catt) {
+        L.Q = take((size_t)n * 4);
+        L.Qh = take((size_t)n * 4);
     }
     L.total = off;
     return L;
@@ -391,7 +401,7 @@ int derive(const ade_params *p, int n, Derived *d)
         }
     }
     d->ncells_cap = ncells_cap;
-    d->L = layout(n, ncells_cap, d->nb_partials, p->vmax > 0.0 ? p->dim : 0);
+    d->L = layout(n, ncells_cap, d->nb_partials, p->vmax > 0.0 ? p->dim : 0, p->tau > 0.0);
     return ADE_OK;
 }
 
@@ -406,6 +416,13 @@ uint32_t fixed_increment(double v, double dt, double L)
 int need_field(const ade_ctx *c)
 {
     if (c->field && !c->field_set) return fail(ADE_ERR_STATE, "velocity-field mode: call ade_set_velocity_field first");
+    return ADE_OK;
+}
+
+// Steps of the Cattaneo form need the flux Q = dC/dt of the current state.
+int need_flux(const ade_ctx *c)
+{
+    if (c->catt && !c->flux_set) return fail(ADE_ERR_STATE, "Cattaneo form (tau > 0): call ade_set_flux first");
     return ADE_OK;
 }
 
@@ -454,6 +471,11 @@ int enqueue_eval(ade_ctx *c, Phase ph, ade::EpiOut out, cudaStream_t s)
     for (int i = 0; i < 3; ++i) {
         rp.inc[i] = ph == PREDICTOR ? c->inc_half[i] : (ph == CORRECTOR ? c->inc[i] : 0u);
         rp.back[i] = ph == CORRECTOR ? c->inc_half[i] : 0u;
+    }
+    if (c->catt && ph != AT_BUILD) {
+        out.Q = c->Q;
+        out.Qh = c->Qh;
+        out.tau_inv = (float)(1.0 / c->p.tau);
     }
     if (c->field) {
         ADE_CK(ade::launch_rate_field(c->dim, c->p.kernel, epi, Pe, c->w.cell_start, c->w.perm, c->fw, rp, c->fp,
@@ -689,6 +711,12 @@ int ade_init_particles(ade_ctx **out, const ade_params *p, int n, uint32_t *xq_d
         field_constants(c);
         c->field_set = n == 0;
     }
+    c->catt = p->tau > 0.0;
+    if (c->catt) {
+        c->Q = at<float>(workspace_dev, d.L.Q);
+        c->Qh = at<float>(workspace_dev, d.L.Qh);
+        c->flux_set = n == 0;
+    }
     *out = c;
     return ADE_OK;
 }
@@ -819,6 +847,40 @@ int ade_set_velocity_field(ade_ctx *c, const float *v_dev, void *stream)
     return ADE_OK;
 }
 
+int ade_set_flux(ade_ctx *c, const float *Q_dev, void *stream)
+{
+    if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
+    if (!c->catt) return fail(ADE_ERR_STATE, "context was created with tau = 0 (Eq. 1 has no flux variable)");
+    cudaStream_t s = (cudaStream_t)stream;
+    c->flux_set = false;
+    if (c->n > 0) {
+        if (Q_dev) {
+            ADE_CK(cudaMemcpyAsync(c->Q, Q_dev, (size_t)c->n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        } else {
+            // Q^0 = R(C^0): the flux of Eq. 1 at the current state
+            int rc = enqueue_cells(c, s);
+            if (rc) return rc;
+            ade::EpiOut out = epi_none();
+            out.rate = c->Q;
+            rc = enqueue_eval(c, AT_BUILD, out, s);
+            if (rc) return rc;
+        }
+    }
+    c->flux_set = true;
+    return ADE_OK;
+}
+
+int ade_get_flux(ade_ctx *c, float *Q_dev, void *stream)
+{
+    if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
+    if (!c->catt) return fail(ADE_ERR_STATE, "context was created with tau = 0 (Eq. 1 has no flux variable)");
+    if (c->n > 0 && !Q_dev) return fail(ADE_ERR_ARG, "Q_dev is NULL");
+    if (c->n > 0)
+        ADE_CK(cudaMemcpyAsync(Q_dev, c->Q, (size_t)c->n * sizeof(float), cudaMemcpyDeviceToDevice,
+                               (cudaStream_t)stream));
+    return ADE_OK;
+}
+
 int ade_set_dispersivity(ade_ctx *c, double alpha_L, double alpha_T, double D_m)
 {
     if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
@@ -924,7 +986,7 @@ int ade_step(ade_ctx *c, int nsteps, void *stream)
 {
     if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
     if (nsteps < 0) return fail(ADE_ERR_ARG, "nsteps must be >= 0");
-    if (need_field(c)) return ADE_ERR_STATE;
+    if (need_field(c) || need_flux(c)) return ADE_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
     int rc0 = clear_status_once(c, s);
     if (rc0) return rc0;
@@ -963,7 +1025,7 @@ int ade_run(ade_ctx *c, int nsteps, ade_stats *st, void *stream)
 {
     if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
     if (nsteps < 0) return fail(ADE_ERR_ARG, "nsteps must be >= 0");
-    if (need_field(c)) return ADE_ERR_STATE;
+    if (need_field(c) || need_flux(c)) return ADE_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
     int rc0 = clear_status_once(c, s);
     if (rc0) return rc0;
@@ -998,7 +1060,7 @@ int ade_run(ade_ctx *c, int nsteps, ade_stats *st, void *stream)
 int ade_step_timed(ade_ctx *c, double *phase_ms, void *stream)
 {
     if (!c || !phase_ms) return fail(ADE_ERR_ARG, "NULL argument");
-    if (need_field(c)) return ADE_ERR_STATE;
+    if (need_field(c) || need_flux(c)) return ADE_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
     int rc = clear_status_once(c, s);
     if (rc) return rc;
@@ -1194,6 +1256,7 @@ int batch_validate(int P, const ade_params *p, const int *n)
         if (!(p[i].box[1] == p[i].box[0] && (p[i].dim == 2 || p[i].box[2] == p[i].box[0])))
             return fail(ADE_ERR_ARG, "batched plumes need a cubic box (equal sides)");
         if (p[i].vmax > 0.0) return fail(ADE_ERR_ARG, "batched plumes have a uniform velocity (vmax must be 0)");
+        if (p[i].tau > 0.0) return fail(ADE_ERR_ARG, "batched plumes follow Eq. 1 (tau must be 0)");
         N += n[i];
     }
     if (N > (1ll << 28)) return fail(ADE_ERR_ARG, "total particles exceed 2^28");
@@ -1732,6 +1795,7 @@ int sweep_layout(const ade_params *p, int n, int P, const double *theta, ade_par
     if (!p) return fail(ADE_ERR_ARG, "params is NULL");
     if (P < 1 || P > ade::kSweepMax) return fail(ADE_ERR_ARG, "ntheta must be in 1..%d", ade::kSweepMax);
     if (p->vmax > 0.0) return fail(ADE_ERR_ARG, "a sweep has a uniform velocity (vmax must be 0)");
+    if (p->tau > 0.0) return fail(ADE_ERR_ARG, "a sweep follows Eq. 1 (tau must be 0)");
     if (p->flags != 0u && p->flags != ADE_FLAG_DIRECT) return fail(ADE_ERR_ARG, "a sweep uses the direct walk");
     ade_params pp = *p;
     pp.flags = ADE_FLAG_DIRECT;

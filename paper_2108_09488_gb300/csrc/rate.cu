@@ -184,21 +184,38 @@ __device__ __forceinline__ void epilogue(int gi, float rate, const uint4 &pe,
             if (a - (uint32_t)prm.goff < (uint32_t)prm.n) out.rate[a] = rate;
         }
     } else if (EPI == EPI_PREDICT) {
-        // C^{l+1/2} = C^l + dt/2 r^l, x^{l+1/2} = x^l + dt/2 v
+        // C^{l+1/2} = C^l + dt/2 r^l, x^{l+1/2} = x^l + dt/2 v.  Eq. 14 (out.Q set): the flux
+        // Q = dC/dt relaxes to r over tau, C^{l+1/2} = C^l + dt/2 Q^l and
+        // Q^{l+1/2} = Q^l + dt/2 (r^l - Q^l) / tau, kept in sorted order for the corrector.
+        float dC = rate;
+        if (out.Q) {
+            const uint32_t a = __ldg(perm + gi);
+            const float q = a - (uint32_t)prm.goff < (uint32_t)prm.n ? out.Q[a] : 0.f;
+            out.Qh[gi] = fmaf(prm.dt, (rate - q) * out.tau_inv, q);
+            dC = q;
+        }
         uint4 q;
         q.x = pe.x + prm.inc[0];
         q.y = pe.y + prm.inc[1];
         q.z = pe.z + prm.inc[2];
-        q.w = __float_as_uint(fmaf(prm.dt, rate, __uint_as_float(pe.w)));
+        q.w = __float_as_uint(fmaf(prm.dt, dC, __uint_as_float(pe.w)));
         out.Pout[gi] = q;
     } else {
         // C^{l+1} = C^l + dt r^{l+1/2}, x^{l+1} = x^l + dt v, in the caller's order.  x^l is the
         // evaluation position minus the half-step drift (exact in fixed point); C^l is still in
-        // the caller's array, read just before this thread overwrites it.
+        // the caller's array, read just before this thread overwrites it.  Eq. 14:
+        // C^{l+1} = C^l + dt Q^{l+1/2}, Q^{l+1} = Q^l + dt (r^{l+1/2} - Q^{l+1/2}) / tau.
         const uint32_t a = __ldg(perm + gi);
         float Cn = 0.f;
         if (a - (uint32_t)prm.goff < (uint32_t)prm.n) {
-            Cn = fmaf(prm.dt, rate, out.C[a]);
+            float dC = rate;
+            if (out.Q) {
+                const float qh = out.Qh[gi];
+                const float q = out.Q[a];
+                out.Q[a] = fmaf(prm.dt, (rate - qh) * out.tau_inv, q);
+                dC = qh;
+            }
+            Cn = fmaf(prm.dt, dC, out.C[a]);
             out.C[a] = Cn;
             out.xq[a] = pe.x - prm.back[0] + prm.inc[0];
             out.xq[(size_t)prm.n + a] = pe.y - prm.back[1] + prm.inc[1];

@@ -243,3 +243,41 @@ def test_sweep_host_validation_and_info(adelib, orc):
     th = (ctypes.c_double * bad.size)(*bad.ravel().tolist())
     assert lib.ade_sweep_init(ctypes.byref(ctx), ctypes.byref(p), plume.n, len(bad), th, FAKE,
                               FAKE + (1 << 30), FAKE + (2 << 30), nbytes) == -1
+
+
+def test_cattaneo_host_validation(adelib, orc):
+    """tau: finite and >= 0; the dt rule is capped at tau; the flux needs a Cattaneo context and
+    steps wait for one; field mode, batches and sweeps refuse tau > 0 (all before device work)."""
+    import ctypes
+    plume = inputs.lattice_2d_64()
+    for bad in (-1.0, float("nan")):
+        with pytest.raises(adelib.AdeError) as e:
+            adelib.workspace_bytes(adelib.params_for(plume, tau=bad), plume.n)
+        assert e.value.code == -1
+    with pytest.raises(adelib.AdeError):
+        adelib.workspace_bytes(adelib.params_for(plume, tau=1.0, vmax=0.2), plume.n)
+    D = orc.dispersion_tensor(plume.velocity, plume.alpha_L, plume.alpha_T, plume.D_m)
+    dt_rule = orc.dt_rule(D, plume.h)
+    lib = adelib.load()
+    for tau, want in ((0.25 * dt_rule, 0.25 * dt_rule), (4 * dt_rule, dt_rule)):
+        p = adelib.params_for(plume, tau=tau)
+        ctx, nbytes = _ctx(adelib, p, plume.n)
+        try:
+            assert adelib.get_info(ctx).dt == pytest.approx(want, rel=1e-14)
+            assert nbytes >= adelib.workspace_bytes(adelib.params_for(plume), plume.n) + 8 * plume.n
+            with pytest.raises(adelib.AdeError) as e:
+                adelib.step(ctx, 1)
+            assert e.value.code == -6
+        finally:
+            adelib.destroy(ctx)
+    ctx, _ = _ctx(adelib, adelib.params_for(plume), plume.n)
+    try:
+        assert lib.ade_set_flux(ctx, None, None) == -6
+        assert lib.ade_get_flux(ctx, FAKE, None) == -6
+    finally:
+        adelib.destroy(ctx)
+    plumes = inputs.batched_2d(nplumes=2, side_lo=16, side_hi=32)
+    with pytest.raises(adelib.AdeError):
+        adelib.batch_workspace_bytes([adelib.params_for(q, tau=1.0) for q in plumes], [q.n for q in plumes])
+    with pytest.raises(adelib.AdeError):
+        adelib.sweep_workspace_bytes(adelib.params_for(plume, tau=1.0), plume.n, 2)
