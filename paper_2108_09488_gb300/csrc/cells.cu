@@ -14,7 +14,9 @@
 //   k_order   one thread per cell sorts its segment by caller index (insertion sort; cells hold a
 //             handful of particles) and writes the sorted copy {x, y, z, C}; cells of more than
 //             kSmallCell particles (wide kernels: hundreds to thousands per cell) are ordered by
-//             the whole warp instead, each element placed at its rank among the cell's indices
+//             the whole warp instead, each element placed at its rank among the cell's indices;
+//             grids averaging 16 or more particles per cell use k_order_block (one block per cell,
+//             the same ranking spread over 256 threads)
 // The result is the stable order (key, caller index) regardless of the order the atomics took,
 // so the permutation and cell table are identical on every run and bit-exact against a stable
 // counting sort.
@@ -250,6 +252,54 @@ __global__ __launch_bounds__(kThreads) void k_order(const uint32_t *__restrict__
     order_big_cells(valid && e - s > kSmallCell, s, e, perm_tmp, perm, P, rec);
 }
 
+// One block per cell, for grids whose cells hold many particles on average (wide kernels, coarse
+// subdivisions): every thread ranks kRankItems elements at a time against the whole segment,
+// streamed through shared memory kRankChunk values at a time; the element goes to s + rank.
+constexpr int kRankChunk = 2048;
+constexpr int kRankItems = 4;
+
+__global__ __launch_bounds__(kThreads) void k_order_block(const uint32_t *__restrict__ start, int ncells,
+                                                          const uint32_t *__restrict__ perm_tmp,
+                                                          const uint32_t *__restrict__ xq,
+                                                          const float *__restrict__ C, int n, int dim,
+                                                          uint32_t *__restrict__ perm, uint4 *__restrict__ P)
+{
+    __shared__ uint32_t chunk[kRankChunk];
+    const int c = blockIdx.x;
+    if (c >= ncells) return;
+    const uint32_t s = __ldg(start + c), e = __ldg(start + c + 1);
+    if (e <= s || e > (uint32_t)n) return;                       // uniform over the block
+    const PlainRec rec{xq, C, n, dim};
+    for (uint32_t k0 = s; k0 < e; k0 += kThreads * kRankItems) {
+        uint32_t v[kRankItems], rank[kRankItems];
+#pragma unroll
+        for (int r = 0; r < kRankItems; ++r) {
+            const uint32_t k = k0 + threadIdx.x + r * kThreads;
+            v[r] = k < e ? __ldg(perm_tmp + k) : 0xffffffffu;
+            rank[r] = 0u;
+        }
+        for (uint32_t t0 = s; t0 < e; t0 += kRankChunk) {
+            const uint32_t len = e - t0 < (uint32_t)kRankChunk ? e - t0 : (uint32_t)kRankChunk;
+            __syncthreads();
+            for (uint32_t t = threadIdx.x; t < len; t += kThreads) chunk[t] = __ldg(perm_tmp + t0 + t);
+            __syncthreads();
+            for (uint32_t t = 0; t < len; ++t) {
+                const uint32_t u = chunk[t];
+#pragma unroll
+                for (int r = 0; r < kRankItems; ++r) rank[r] += u < v[r] ? 1u : 0u;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kRankItems; ++r) {
+            const uint32_t k = k0 + threadIdx.x + r * kThreads;
+            if (k < e && s + rank[r] < e) {
+                perm[s + rank[r]] = v[r];
+                P[s + rank[r]] = rec(v[r]);
+            }
+        }
+    }
+}
+
 // Batched plumes: caller particle i belongs to plume p = plume_of[i], whose positions are the
 // [dim][n_p] block starting at xq + dim * goff_p; its key is coff_p + the plume-local key.
 __global__ __launch_bounds__(kThreads) void k_count_batch(const uint32_t *__restrict__ xq, int n, int dim,
@@ -348,8 +398,12 @@ cudaError_t launch_build_cells(int dim, const uint32_t *xq, const float *C, int 
     k_scan_apply<<<sb, kThreads, 0, s>>>(w.count, ncells, w.block_sums, w.cell_start);
     if (nb > 0) {
         k_place<<<nb, kThreads, 0, s>>>(w.keys, w.rank, n, w.cell_start, w.perm_tmp);
-        k_order<<<(ncells + kThreads - 1) / kThreads, kThreads, 0, s>>>(w.cell_start, ncells, w.perm_tmp,
-                                                                         xq, C, n, dim, w.perm, w.P0);
+        if ((long long)n >= 16ll * ncells)   // many particles per cell: one block per cell
+            k_order_block<<<ncells, kThreads, 0, s>>>(w.cell_start, ncells, w.perm_tmp, xq, C, n, dim, w.perm,
+                                                      w.P0);
+        else
+            k_order<<<(ncells + kThreads - 1) / kThreads, kThreads, 0, s>>>(w.cell_start, ncells, w.perm_tmp,
+                                                                             xq, C, n, dim, w.perm, w.P0);
     }
     return cudaGetLastError();
 }
