@@ -95,7 +95,7 @@ __device__ __forceinline__ void pair_range_direct(const uint4 *__restrict__ P, i
                                                   const uint4 &pa, float Ca, const PairConst &k,
                                                   const RateParams &prm, float &rs, unsigned &cnt)
 {
-#pragma unroll 2
+#pragma unroll 8
     for (int j = j0; j < j1; ++j) {
         const uint4 pb = __ldg(P + j);
         if (COUNT) cnt += in_support_fp64<DIM>((int)(pa.x - pb.x), (int)(pa.y - pb.y), (int)(pa.z - pb.z), prm);

@@ -209,7 +209,7 @@ __global__ __launch_bounds__(kT) void k_rate_field(const uint4 *__restrict__ Pe,
         }
         float rd = 0.f, rc = 0.f;
         for (int piece = 0; piece < 2; ++piece)
-#pragma unroll 2
+#pragma unroll 4
             for (int j = r0[piece]; j < r1[piece]; ++j) {
                 const uint4 pb = __ldg(Pe + j);
                 const int ix = (int)(pa.x - pb.x), iy = (int)(pa.y - pb.y), iz = (int)(pa.z - pb.z);

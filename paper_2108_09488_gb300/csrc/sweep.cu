@@ -110,6 +110,7 @@ __global__ __launch_bounds__(kT) void k_rate_sweep(const uint4 *__restrict__ Pe,
 #pragma unroll
         for (int k = 0; k < NT; ++k) rs[k] = 0.f;
         for (int piece = 0; piece < 2; ++piece)
+#pragma unroll 4
             for (int j = r0[piece]; j < r1[piece]; ++j) {
                 const uint4 pb = __ldg(Pe + j);
                 const int ix = (int)(pa.x - pb.x), iy = (int)(pa.y - pb.y), iz = (int)(pa.z - pb.z);
