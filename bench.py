@@ -84,7 +84,7 @@ MUFU_LANES_PER_SM = 16
 # of the current kernels (profiles/k_rate_ladder1024.md, profiles/k_rate_batch_batched64.md,
 # profiles/k_rate_field_field1024.md, profiles/k_rate_paper1m.md, profiles/k_rate_sweep_sweep512.md).
 # Set an entry to None whenever the kernel changes until it is captured again.
-TRAFFIC_PER_LAUNCH = {"ladder-1024-n120-r10": 22.81e6, "batched-64": 45.16e6,
+TRAFFIC_PER_LAUNCH = {"ladder-1024-n120-r10": 22.81e6, "batched-64": 42.12e6,
                       "field-1024-n120-r10": 82.75e6, "paper-1m-n31k-c4": 20.05e6,
                       "sweep-512-8": 18.77e6}
 FP32_LANES_PER_SM = 128
