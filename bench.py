@@ -795,7 +795,8 @@ def run_ours(args):
         "grid": {"cell_subdiv": sim.info.cell_subdiv, "cells": sim.info.ncells,
                  "stencil_rows": sim.info.stencil_rows, "sort_passes": sim.info.sort_passes,
                  "variant": ("velocity-field-direct" if v is not None else
-                             {0: "direct-branch-free", 1: "tiled", 2: "direct-branched"}[sim.info.variant]),
+                             {0: "direct-branch-free", 1: "tiled", 2: "direct-branched", 3: "direct-branch-free-trimmed",
+                              4: "direct-branched-trimmed"}[sim.info.variant]),
                  "autotune_best_ms": tune_ms, "dt": sim.info.dt, "skin": sim.info.skin},
         "steps_per_s": 1e3 / ms_per_step * world,
         "interactions_per_step": 2 * pairs,

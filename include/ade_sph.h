@@ -51,6 +51,10 @@ extern "C" {
 #define ADE_FLAG_DIRECT 1u /* interaction kernel: direct walk over global memory (default) */
 #define ADE_FLAG_TILED 2u  /* interaction kernel: shared-memory tiles where the grid allows */
 #define ADE_FLAG_BRANCHED 4u /* interaction kernel: direct walk branching on the support test */
+#define ADE_FLAG_TRIMMED 8u  /* with DIRECT or BRANCHED (or alone = DIRECT): each particle visits only
+                                the stencil cells within (1 + 2^-12) H of itself; the skipped
+                                candidates contribute exactly 0, so results are bitwise unchanged
+                                (square or cubic boxes; other boxes walk the full stencil) */
 
 #define ADE_DT_LAMBDA_MAX 0 /* dt = coef h^2 / lambda_max(D) */
 #define ADE_DT_TRACE 1      /* Eq. 10: dt = coef h^2 / (D_xx + D_yy [+ D_zz]) */
@@ -74,7 +78,8 @@ typedef struct ade_params {
     int dt_rule;       /* ADE_DT_LAMBDA_MAX or ADE_DT_TRACE */
     double dt_coef;    /* coefficient of the rule; <= 0 selects 0.1 (Eq. 10) */
     int cell_subdiv;   /* cells per support radius along each axis, 1..6; 0 = automatic */
-    unsigned flags;    /* 0 (library's choice), ADE_FLAG_DIRECT, ADE_FLAG_TILED or ADE_FLAG_BRANCHED */
+    unsigned flags;    /* 0 (library's choice), ADE_FLAG_DIRECT, ADE_FLAG_TILED, ADE_FLAG_BRANCHED,
+                          or ADE_FLAG_TRIMMED alone or with DIRECT or BRANCHED */
     double vmax;       /* 0: uniform velocity v.  > 0: velocity-field mode -- each particle carries
                           its own constant velocity (ade_set_velocity_field), |v_a| <= vmax; v is
                           then unused, the dt rules take |v| = vmax, and the cell grid is sized for
@@ -107,7 +112,8 @@ typedef struct ade_info {
     int stencil_rows; /* rows of cells visited per particle */
     int sort_passes;  /* radix-sort passes per cell build */
     int variant;      /* interaction kernel: 0 direct walk (branch-free), 1 shared-memory tiles,
-                         2 direct walk branching on the support test */
+                         2 direct walk branching on the support test, 3 and 4 the two direct
+                         walks with per-particle trimmed rows */
     int tile[3];      /* target cells per tile (tiled variant) */
     int tile_capacity;/* staged particles per tile (tiled variant) */
     size_t workspace_bytes;
@@ -175,8 +181,10 @@ int ade_closed_form_error(ade_ctx *ctx, const double *x0_host, double w, double 
 
 /* Autotuner for a context created with cell_subdiv = 0 and flags = 0: times the cell build plus
  * one evaluation of Eq. 4 for every cell subdivision (1..6 cells per support radius) and every
- * interaction variant (branch-free direct walk, branched direct walk, shared-memory tiles), keeps
- * the fastest; results change only in summation order.  The particle state is not modified; waits; best_ms_host may be NULL. */
+ * interaction variant (branch-free or branched direct walk, each with full or trimmed rows, and
+ * shared-memory tiles), keeps the fastest; results change only in summation order (not at all
+ * between full and trimmed rows).  The particle state is not modified; waits; best_ms_host may be
+ * NULL. */
 int ade_autotune(ade_ctx *ctx, double *best_ms_host, void *stream);
 
 /* Change alpha_L, alpha_T and D_m (Eq. 3) of a context, keeping its time step, grid and state. */

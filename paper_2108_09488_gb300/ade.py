@@ -25,6 +25,7 @@ WENDLAND_C4 = 1
 FLAG_DIRECT = 1
 FLAG_TILED = 2
 FLAG_BRANCHED = 4
+FLAG_TRIMMED = 8
 DT_LAMBDA_MAX = 0
 DT_TRACE = 1
 

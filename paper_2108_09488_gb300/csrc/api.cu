@@ -231,7 +231,8 @@ int validate(const ade_params *p, int n)
     if (p->dt_rule != ADE_DT_LAMBDA_MAX && p->dt_rule != ADE_DT_TRACE) return fail(ADE_ERR_ARG, "unknown dt_rule");
     if (p->cell_subdiv < 0 || p->cell_subdiv > ade::kMaxSubdiv) return fail(ADE_ERR_ARG, "cell_subdiv must be 0..6");
     if (p->flags != 0u && p->flags != ADE_FLAG_DIRECT && p->flags != ADE_FLAG_TILED &&
-        p->flags != ADE_FLAG_BRANCHED)
+        p->flags != ADE_FLAG_BRANCHED && p->flags != ADE_FLAG_TRIMMED &&
+        p->flags != (ADE_FLAG_TRIMMED | ADE_FLAG_DIRECT) && p->flags != (ADE_FLAG_TRIMMED | ADE_FLAG_BRANCHED))
         return fail(ADE_ERR_ARG, "unknown or conflicting flags");
     if (!(p->vmax >= 0.0) || !isfinite(p->vmax)) return fail(ADE_ERR_ARG, "vmax must be finite and >= 0");
     if (p->vmax > 0.0 && p->flags != 0u && p->flags != ADE_FLAG_DIRECT)
@@ -590,7 +591,8 @@ int plume_constants(const ade_params *p, int n, const Derived &d, double *D, dou
     const int dm = p->dim;
     ade::pair_coeffs(dm, gamma, D, rp.Kc, &rp.c0);
     rp.pf = (float)(0.5 * (p->mass / p->rho) * kernel_kc(p->kernel, dm, d.H));
-    rp.variant = d.tiles.variant == 1 ? 1 : (p->flags == ADE_FLAG_BRANCHED ? 2 : 0);
+    rp.variant = d.tiles.variant == 1 ? 1 : ((p->flags & ADE_FLAG_BRANCHED) ? 2 : 0);
+    if (rp.variant != 1 && (p->flags & ADE_FLAG_TRIMMED)) rp.variant = rp.variant == 2 ? 4 : 3;  // trimmed rows
     rp.k = d.tiles.k;
     rp.tx = d.tiles.tx;
     rp.ty = d.tiles.ty;
@@ -791,7 +793,7 @@ int ade_autotune(ade_ctx *c, double *best_ms_host, void *stream)
     int best_variant = c->rp.variant;
     int rc = ADE_OK;
     for (int k = 1; rc == ADE_OK && k <= ade::kMaxSubdiv; ++k)
-        for (int variant = 0; variant < 3; ++variant) {
+        for (int variant = 0; variant < 5; ++variant) {
             if (c->field && variant != 0) continue;  // one interaction kernel in velocity-field mode
             if (apply_config(c, k, variant) != ADE_OK) continue;
             double ms = 1e30;

@@ -123,8 +123,9 @@ __device__ __forceinline__ void pair_range_direct(const uint4 *__restrict__ P, i
     }
 }
 
-// Eq. 4 at one particle by the direct walk; (cx, cy, cz) is its cell.
-template <int DIM, int KERNEL, bool ISO, bool COUNT, bool BF = true>
+// Eq. 4 at one particle by the direct walk; (cx, cy, cz) is its cell.  TRIM: visit only the
+// stencil cells within reach of the particle itself (see below).
+template <int DIM, int KERNEL, bool ISO, bool COUNT, bool BF = true, bool TRIM = false>
 __device__ float rate_direct(const uint4 *__restrict__ Pe, const uint32_t *__restrict__ cs,
                              const uint4 &pa, int cx, int cy, int cz, const RateParams &prm,
                              unsigned &cnt)
@@ -133,8 +134,41 @@ __device__ float rate_direct(const uint4 *__restrict__ Pe, const uint32_t *__res
     const PairConst kc(prm);
     const float Ca = __uint_as_float(pa.w);
     float acc = 0.f, comp = 0.f;
+    // Per-particle trimming of the stencil (TRIM).  The stencil row (dy, dz, w) holds every
+    // neighbour of any point of the cell; for this particle only the cells within H of its own
+    // position are
+    // needed.  Its fractional position in its build cell is the low word of x nc (umulhi gives the
+    // cell, the low 32 bits the offset within it exactly), so the row's distance e (in x-axis
+    // units) and the x cell range [floor(f_x - xe), floor(f_x + xe)], xe = sqrt(H^2 - e^2) / width,
+    // follow in FP32.  The radius is widened by 2^-12 H (far above the FP32 rounding of these
+    // bounds), so a skipped candidate lies beyond H by more than the evaluation's rounding and its
+    // term is exactly 0: the sums are bitwise those of the full stencil.
+    const float two32 = 4294967296.f;
+    const float fx = (float)((pa.x - prm.back[0]) * (uint32_t)ncx) * (1.f / two32);
+    const float fy = (float)((pa.y - prm.back[1]) * (uint32_t)ncy) * (1.f / two32);
+    const float fz = DIM == 3 ? (float)((pa.z - prm.back[2]) * (uint32_t)ncz) * (1.f / two32) : 0.f;
+    const float inv_wx = (float)ncx * (1.f / two32);              // cells per x unit
+    const float chy = two32 / (float)ncy * kc.sy, chz = DIM == 3 ? two32 / (float)ncz * kc.sz : 0.f;
+    const float Hm2 = kc.H2 * (1.f + 1.f / 2048.f);                // (H (1 + 2^-12))^2, rounded up
     for (int ri = 0; ri < nrows; ++ri) {
         const StencilRow row = prm.rows[ri];
+        float e2 = 0.f;
+        if (TRIM) {
+            const float ey = fmaxf(fmaxf((float)row.dy - fy, fy - (float)(row.dy + 1)), 0.f) * chy;
+            e2 = ey * ey;
+            if (DIM == 3) {
+                const float ez = fmaxf(fmaxf((float)row.dz - fz, fz - (float)(row.dz + 1)), 0.f) * chz;
+                e2 = fmaf(ez, ez, e2);
+            }
+        }
+        int dlo = -(int)row.w, dhi = row.w;
+        if (TRIM) {
+            if (!(e2 < Hm2)) continue;                              // the whole row is out of reach
+            const float t = Hm2 - e2;
+            const float xe = t * rsqrtf(t) * inv_wx + 1.f / 4096.f;  // half-extent in cells
+            dlo = max(__float2int_rd(fx - xe), dlo);
+            dhi = min(__float2int_rd(fx + xe), dhi);
+        }
         int yy = cy + row.dy;
         yy += (yy < 0) ? ncy : 0;
         yy -= (yy >= ncy) ? ncy : 0;
@@ -145,7 +179,7 @@ __device__ float rate_direct(const uint4 *__restrict__ Pe, const uint32_t *__res
             zz -= (zz >= ncz) ? ncz : 0;
         }
         const int base = (zz * ncy + yy) * ncx;
-        const int lo = cx - row.w, hi = cx + row.w + 1;
+        const int lo = cx + dlo, hi = cx + dhi + 1;
         int s0, e0, s1 = 0, e1 = 0;
         if (lo < 0) {
             s0 = __ldg(cs + base + lo + ncx);
@@ -231,7 +265,7 @@ __device__ __forceinline__ void epilogue(int gi, float rate, const uint4 &pe,
 // ---------------------------------------------------------------------------------------------
 // direct kernel
 // ---------------------------------------------------------------------------------------------
-template <int DIM, int KERNEL, int EPI, bool ISO, bool COUNT, bool BF>
+template <int DIM, int KERNEL, int EPI, bool ISO, bool COUNT, bool BF, bool TRIM>
 __global__ __launch_bounds__(kRateThreads) void k_rate(const uint4 *__restrict__ Pe,
                                                        const uint4 *__restrict__ Pc,
                                                        const uint32_t *__restrict__ cs,
@@ -248,7 +282,7 @@ __global__ __launch_bounds__(kRateThreads) void k_rate(const uint4 *__restrict__
     const int cz = DIM == 3 ? (int)__umulhi(pa.z - prm.back[2], (uint32_t)prm.ncz) : 0;
     Acc acc{0.f, 0.f, __int_as_float(0x7f800000), __int_as_float(0xff800000), 0u};
     unsigned cnt = 0u;
-    const float rate = rate_direct<DIM, KERNEL, ISO, COUNT, BF>(Pe, cs, pa, cx, cy, cz, prm, cnt);
+    const float rate = rate_direct<DIM, KERNEL, ISO, COUNT, BF, TRIM>(Pe, cs, pa, cx, cy, cz, prm, cnt);
     if (valid) {
         acc.cnt = cnt;
         epilogue<DIM, EPI>(i, rate, pa, perm, prm, out, acc);
@@ -531,17 +565,25 @@ cudaError_t launch_variant(bool iso, const uint4 *Pe, const uint4 *Pc, const uin
         return cudaGetLastError();
     }
     const int blocks = rate_blocks(prm.n);
-    const bool bf = prm.variant != 2;   // 2: branched direct walk
+    const bool bf = prm.variant != 2 && prm.variant != 4;   // 2, 4: branched direct walk
+    // 3, 4: trimmed rows (square or cubic boxes; the pair count is the same either way)
+    const bool trim = (prm.variant == 3 || prm.variant == 4) && iso && !COUNT;
     if (iso) {
-        if (bf)
-            k_rate<DIM, KERNEL, EPI, true, COUNT, true><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
-        else
-            k_rate<DIM, KERNEL, EPI, true, COUNT, false><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
+        if (trim) {
+            if (bf)
+                k_rate<DIM, KERNEL, EPI, true, false, true, true><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
+            else
+                k_rate<DIM, KERNEL, EPI, true, false, false, true><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
+        } else if (bf) {
+            k_rate<DIM, KERNEL, EPI, true, COUNT, true, false><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
+        } else {
+            k_rate<DIM, KERNEL, EPI, true, COUNT, false, false><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
+        }
     } else {
         if (bf)
-            k_rate<DIM, KERNEL, EPI, false, COUNT, true><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
+            k_rate<DIM, KERNEL, EPI, false, COUNT, true, false><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
         else
-            k_rate<DIM, KERNEL, EPI, false, COUNT, false><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
+            k_rate<DIM, KERNEL, EPI, false, COUNT, false, false><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
     }
     return cudaGetLastError();
 }

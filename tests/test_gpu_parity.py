@@ -97,7 +97,8 @@ def test_cells_bit_exact_every_subdivision(lib, orc, k):
     assert np.array_equal(perm, perm_o) and np.array_equal(cs, cs_o)
 
 
-VARIANTS = {"tiled": 2, "direct": 1, "branched": 4}   # ADE_FLAG_TILED, _DIRECT, _BRANCHED
+# ADE_FLAG_TILED, _DIRECT, _BRANCHED, and the two direct walks with _TRIMMED rows
+VARIANTS = {"tiled": 2, "direct": 1, "branched": 4, "direct-trimmed": 9, "branched-trimmed": 12}
 
 
 @pytest.mark.parametrize("variant", sorted(VARIANTS))
@@ -123,6 +124,35 @@ def test_tiled_variant_is_used_and_deterministic(lib):
     r1 = a.rate().cpu().numpy()
     r2 = a.rate().cpu().numpy()
     assert np.array_equal(r1.view(np.uint32), r2.view(np.uint32))
+
+
+@pytest.mark.parametrize("name", ["256sq-n28-r100", "jitter-100sq", "c4-96sq"])
+def test_trimmed_direct_walk_equals_full_stencil_bitwise(lib, name):
+    """With trimmed rows the direct walks visit, per particle, only the stencil cells within
+    (1 + 2^-12) H of the particle; without, and in the shared-memory tiled walk, every cell of the
+    stencil.  The skipped candidates contribute exactly 0, so all give the same bits (same row
+    order, same pair arithmetic), for the rate and for a step."""
+    plume = CASES[name]()
+    xq, C = plume.initial_state()
+    for k in (2, 4):
+        f = _sim(lib, plume, xq, C, cell_subdiv=k, flags=lib.FLAG_DIRECT)
+        d = _sim(lib, plume, xq, C, cell_subdiv=k, flags=lib.FLAG_DIRECT | lib.FLAG_TRIMMED)
+        assert d.info.variant == 3
+        rf = f.rate().cpu().numpy()
+        rd = d.rate().cpu().numpy()
+        assert np.array_equal(rd.view(np.uint32), rf.view(np.uint32)), k
+        t = _sim(lib, plume, xq, C, cell_subdiv=k, flags=lib.FLAG_TILED)
+        if t.info.variant == 1:
+            rt = t.rate().cpu().numpy()
+            assert np.array_equal(rd.view(np.uint32), rt.view(np.uint32)), k
+        b = _sim(lib, plume, xq, C, cell_subdiv=k, flags=lib.FLAG_BRANCHED)
+        bt = _sim(lib, plume, xq, C, cell_subdiv=k, flags=lib.FLAG_BRANCHED | lib.FLAG_TRIMMED)
+        assert bt.info.variant == 4
+        assert np.array_equal(b.rate().cpu().numpy().view(np.uint32), bt.rate().cpu().numpy().view(np.uint32))
+        # one step with trimmed rows equals one with the full stencil
+        f.step(1)
+        d.step(1)
+        assert np.array_equal(f.state()[1].view(np.uint32), d.state()[1].view(np.uint32))
 
 
 def test_rate_parity_clustered_overflow(lib, orc):
