@@ -218,6 +218,21 @@ int ade_set_velocity_field(ade_ctx *ctx, const float *v_dev, void *stream);
 int ade_set_flux(ade_ctx *ctx, const float *Q_dev, void *stream);
 int ade_get_flux(ade_ctx *ctx, float *Q_dev, void *stream);
 
+/* ---- Checkpoint and resume ---------------------------------------------------------------------
+ * No counterpart in the paper (its runs are single jobs); long runs on shared machines need to stop
+ * and continue.  A snapshot of a single-plume context is one host buffer: a header (format magic
+ * and version, dim, n, mode, step, simulated time, dt and the parameters), the state -- xq [dim][n],
+ * C [n], the Cattaneo flux Q [n] when tau > 0, the velocity field v [dim][n] when vmax > 0 -- and a
+ * CRC-32 (IEEE 802.3 polynomial) of all of it.  The caller owns the buffer (pageable or pinned host
+ * memory of at least ade_checkpoint_bytes bytes) and writes it wherever it likes.
+ * ade_checkpoint_save copies the state out and waits for the stream.  ade_checkpoint_load checks the
+ * magic, size, checksum and that n, mode, parameters and dt equal the context's (ADE_ERR_ARG
+ * otherwise, before any device copy), then copies the state in, restores step and time, and waits;
+ * stepping on from a restored context gives the same bits as the original run. */
+int ade_checkpoint_bytes(const ade_ctx *ctx, size_t *bytes);
+int ade_checkpoint_save(ade_ctx *ctx, void *host_buf, size_t bytes, void *stream);
+int ade_checkpoint_load(ade_ctx *ctx, const void *host_buf, size_t bytes, void *stream);
+
 /* ---- Adjoint (dispersivity inversion) ---------------------------------------------------------
  * The paper has no adjoint; it is derived from Eq. 3-5 and Eq. 8-9 for the uniform-velocity case.
  * With the rate r = L(theta) C linear in C, theta = (alpha_L, alpha_T, D_m), L symmetric and the

@@ -42,7 +42,7 @@ EXPORTS = ("ade_workspace_bytes", "ade_init_particles", "ade_get_info", "ade_bui
            "ade_sweep_workspace_bytes", "ade_sweep_init", "ade_sweep_get_info", "ade_sweep_rate",
            "ade_sweep_count_pairs", "ade_sweep_step", "ade_sweep_run", "ade_sweep_step_timed",
            "ade_sweep_launches_per_step", "ade_sweep_stats", "ade_sweep_destroy", "ade_set_flux",
-           "ade_get_flux")
+           "ade_get_flux", "ade_checkpoint_bytes", "ade_checkpoint_save", "ade_checkpoint_load")
 NOALLOC_MAX_PARTICLES = 1 << 20
 NOALLOC_MAX_CELLS = 1 << 20
 
@@ -123,6 +123,9 @@ def load():
         "ade_set_dispersivity": (I, [P, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
         "ade_set_velocity_field": (I, [P, P, V]),
         "ade_set_flux": (I, [P, P, V]),
+        "ade_checkpoint_bytes": (I, [P, ctypes.POINTER(SZ)]),
+        "ade_checkpoint_save": (I, [P, P, SZ, V]),
+        "ade_checkpoint_load": (I, [P, P, SZ, V]),
         "ade_get_flux": (I, [P, P, V]),
         "ade_alu_peaks": (I, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), V]),
         "ade_sweep_workspace_bytes": (I, [ctypes.POINTER(Params), I, I, ctypes.POINTER(SZ)]),
@@ -278,6 +281,19 @@ def alu_peaks(stream=None):
     return f.value, r.value
 
 
+def checkpoint_save(ctx, stream=None):
+    nb = ctypes.c_size_t(0)
+    _check(load().ade_checkpoint_bytes(ctx, ctypes.byref(nb)))
+    buf = ctypes.create_string_buffer(nb.value)
+    _check(load().ade_checkpoint_save(ctx, buf, nb.value, stream))
+    return buf.raw
+
+
+def checkpoint_load(ctx, blob, stream=None):
+    buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+    _check(load().ade_checkpoint_load(ctx, buf, len(blob), stream))
+
+
 def destroy(ctx):
     if ctx:
         load().ade_destroy(ctx)
@@ -354,6 +370,14 @@ class Simulation:
 
     def set_dispersivity(self, alpha_L, alpha_T, D_m):
         _check(load().ade_set_dispersivity(self.ctx, alpha_L, alpha_T, D_m))
+
+    def checkpoint(self):
+        """Snapshot of the state (ade_checkpoint_save) as bytes."""
+        return checkpoint_save(self.ctx, self.stream)
+
+    def restore(self, blob):
+        """Resume from a snapshot taken of a context with the same parameters (ade_checkpoint_load)."""
+        checkpoint_load(self.ctx, blob, self.stream)
 
     def set_flux(self, Q=None):
         """Cattaneo form (tau > 0): set the flux Q = dC/dt (float32 [n], caller order), or with

@@ -281,3 +281,33 @@ def test_cattaneo_host_validation(adelib, orc):
         adelib.batch_workspace_bytes([adelib.params_for(q, tau=1.0) for q in plumes], [q.n for q in plumes])
     with pytest.raises(adelib.AdeError):
         adelib.sweep_workspace_bytes(adelib.params_for(plume, tau=1.0), plume.n, 2)
+
+
+def test_checkpoint_format_and_validation(adelib):
+    """Snapshots of an empty context need no device: the trailing CRC-32 equals zlib's over header
+    and payload; a flipped byte, a truncated buffer, a foreign buffer and other parameters are
+    refused (ADE_ERR_ARG) before any copy."""
+    import zlib
+    plume = inputs.lattice_2d_64()
+    p = adelib.params_for(plume)
+    ctx, _ = _ctx(adelib, p, 0)
+    try:
+        blob = adelib.checkpoint_save(ctx)
+        assert blob[:8] == b"ADECKPT1"
+        assert int.from_bytes(blob[-4:], "little") == zlib.crc32(blob[:-4])
+        adelib.checkpoint_load(ctx, blob)
+        bad = bytearray(blob)
+        bad[40] ^= 0x01
+        for b in (bytes(bad), blob[:-1], b"x" * len(blob)):
+            with pytest.raises(adelib.AdeError) as e:
+                adelib.checkpoint_load(ctx, b)
+            assert e.value.code == -1
+    finally:
+        adelib.destroy(ctx)
+    other, _ = _ctx(adelib, adelib.params_for(plume, alpha_L=2e-2), 0)
+    try:
+        with pytest.raises(adelib.AdeError) as e:
+            adelib.checkpoint_load(other, blob)
+        assert e.value.code == -1 and "parameters" in str(e.value)
+    finally:
+        adelib.destroy(other)
