@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/ade_sph.h"
@@ -136,6 +137,14 @@ struct Work {
     int *status;           // non-finite flag
     unsigned *done;        // last-block counter of the corrector
     unsigned long long *pairs;
+};
+
+// NVTX range for the duration of a host call (visible in Nsight timelines; no cost without a tool).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 // Records msg as the calling thread's last error (read by ade_last_error) and returns code.

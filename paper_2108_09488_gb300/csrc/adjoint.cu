@@ -333,6 +333,7 @@ extern "C" int ade_adjoint(ade_ctx *c, const float *C_target_dev, int nsteps, in
                            size_t aws_bytes, float *dJdC0_dev, double *dJdtheta_host, double *J_host,
                            float *C_final_dev, void *stream)
 {
+    ade::NvtxRange nvtx_("ade_adjoint");
     if (!c || !C_target_dev || nsteps < 1 || ckpt_every < 1 || !aws)
         return ade::report_error(ADE_ERR_ARG, "bad argument");
     if (c->field) return ade::report_error(ADE_ERR_STATE, "the adjoint is for a uniform velocity (vmax = 0)");

@@ -777,6 +777,7 @@ extern "C" {
 
 int ade_autotune(ade_ctx *c, double *best_ms_host, void *stream)
 {
+    ade::NvtxRange nvtx_("ade_autotune");
     if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
     if (c->p.cell_subdiv != 0 || c->p.flags != 0u)
         return fail(ADE_ERR_STATE, "autotuning needs cell_subdiv = 0 and flags = 0");
@@ -826,6 +827,7 @@ int ade_autotune(ade_ctx *c, double *best_ms_host, void *stream)
 
 int ade_set_velocity_field(ade_ctx *c, const float *v_dev, void *stream)
 {
+    ade::NvtxRange nvtx_("ade_set_velocity_field");
     if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
     if (!c->field) return fail(ADE_ERR_STATE, "context was created with vmax = 0 (uniform velocity)");
     if (c->n > 0 && !v_dev) return fail(ADE_ERR_ARG, "v_dev is NULL");
@@ -851,6 +853,7 @@ int ade_set_velocity_field(ade_ctx *c, const float *v_dev, void *stream)
 
 int ade_set_flux(ade_ctx *c, const float *Q_dev, void *stream)
 {
+    ade::NvtxRange nvtx_("ade_set_flux");
     if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
     if (!c->catt) return fail(ADE_ERR_STATE, "context was created with tau = 0 (Eq. 1 has no flux variable)");
     cudaStream_t s = (cudaStream_t)stream;
@@ -936,6 +939,7 @@ int ade_get_info(const ade_ctx *c, ade_info *info)
 
 int ade_build_cells(ade_ctx *c, void *stream)
 {
+    ade::NvtxRange nvtx_("ade_build_cells");
     if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
     return enqueue_cells(c, (cudaStream_t)stream);
 }
@@ -954,6 +958,7 @@ int ade_get_cells(ade_ctx *c, uint32_t *perm_dev, uint32_t *cell_start_dev, void
 
 int ade_dispersion_rate(ade_ctx *c, float *dCdt_dev, void *stream)
 {
+    ade::NvtxRange nvtx_("ade_dispersion_rate");
     if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
     if (c->n > 0 && !dCdt_dev) return fail(ADE_ERR_ARG, "dCdt_dev is NULL");
     cudaStream_t s = (cudaStream_t)stream;
@@ -966,6 +971,7 @@ int ade_dispersion_rate(ade_ctx *c, float *dCdt_dev, void *stream)
 
 int ade_count_pairs(ade_ctx *c, long long *pairs_host, void *stream)
 {
+    ade::NvtxRange nvtx_("ade_count_pairs");
     if (!c || !pairs_host) return fail(ADE_ERR_ARG, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
     *pairs_host = 0;
@@ -986,6 +992,7 @@ int ade_count_pairs(ade_ctx *c, long long *pairs_host, void *stream)
 
 int ade_step(ade_ctx *c, int nsteps, void *stream)
 {
+    ade::NvtxRange nvtx_("ade_step");
     if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
     if (nsteps < 0) return fail(ADE_ERR_ARG, "nsteps must be >= 0");
     if (need_field(c) || need_flux(c)) return ADE_ERR_STATE;
@@ -1025,6 +1032,7 @@ int ade_get_stats(ade_ctx *c, ade_stats *st, void *stream)
 
 int ade_run(ade_ctx *c, int nsteps, ade_stats *st, void *stream)
 {
+    ade::NvtxRange nvtx_("ade_run");
     if (!c) return fail(ADE_ERR_ARG, "ctx is NULL");
     if (nsteps < 0) return fail(ADE_ERR_ARG, "nsteps must be >= 0");
     if (need_field(c) || need_flux(c)) return ADE_ERR_STATE;
@@ -1061,6 +1069,7 @@ int ade_run(ade_ctx *c, int nsteps, ade_stats *st, void *stream)
 
 int ade_step_timed(ade_ctx *c, double *phase_ms, void *stream)
 {
+    ade::NvtxRange nvtx_("ade_step_timed");
     if (!c || !phase_ms) return fail(ADE_ERR_ARG, "NULL argument");
     if (need_field(c) || need_flux(c)) return ADE_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1111,6 +1120,7 @@ int ade_launches_per_step(const ade_ctx *c, int *launches)
 int ade_closed_form_error(ade_ctx *c, const double *x0, double w, double C0, int nimg, double *outh,
                           void *stream)
 {
+    ade::NvtxRange nvtx_("ade_closed_form_error");
     if (!c || !x0 || !outh) return fail(ADE_ERR_ARG, "NULL argument");
     if (!(w > 0.0) || nimg < 0 || nimg > 8) return fail(ADE_ERR_ARG, "need w > 0 and 0 <= nimg <= 8");
     if (c->field) return fail(ADE_ERR_STATE, "the closed form of Eq. 12-13 is for a uniform velocity");
@@ -1522,6 +1532,7 @@ int ade_batch_init(ade_batch **out, int nplumes, const ade_params *p, const int 
 
 int ade_batch_step(ade_batch *b, int nsteps, void *stream)
 {
+    ade::NvtxRange nvtx_("ade_batch_step");
     if (!b || nsteps < 0) return fail(ADE_ERR_ARG, "bad argument");
     cudaStream_t s = (cudaStream_t)stream;
     int rc = batch_clear_status_once(b, s);
@@ -1533,6 +1544,7 @@ int ade_batch_step(ade_batch *b, int nsteps, void *stream)
 
 int ade_batch_run(ade_batch *b, int nsteps, void *stream)
 {
+    ade::NvtxRange nvtx_("ade_batch_run");
     if (!b || nsteps < 0) return fail(ADE_ERR_ARG, "bad argument");
     cudaStream_t s = (cudaStream_t)stream;
     int rc = batch_clear_status_once(b, s);
@@ -1629,6 +1641,7 @@ int ade_batch_get_plume_info(const ade_batch *b, int plume, ade_info *info)
 
 int ade_batch_autotune(ade_batch *b, double *best_ms_host, void *stream)
 {
+    ade::NvtxRange nvtx_("ade_batch_autotune");
     if (!b) return fail(ADE_ERR_ARG, "batch is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
@@ -1703,6 +1716,7 @@ int ade_batch_autotune(ade_batch *b, double *best_ms_host, void *stream)
 
 int ade_batch_step_timed(ade_batch *b, double *phase_ms, void *stream)
 {
+    ade::NvtxRange nvtx_("ade_batch_step_timed");
     if (!b || !phase_ms) return fail(ADE_ERR_ARG, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
     int rc = batch_clear_status_once(b, s);
@@ -2026,6 +2040,7 @@ int ade_sweep_get_info(const ade_sweep *sw, ade_info *info)
 
 int ade_sweep_rate(ade_sweep *sw, float *dCdt_dev, void *stream)
 {
+    ade::NvtxRange nvtx_("ade_sweep_rate");
     if (!sw) return fail(ADE_ERR_ARG, "sweep is NULL");
     if (sw->n > 0 && !dCdt_dev) return fail(ADE_ERR_ARG, "dCdt_dev is NULL");
     cudaStream_t s = (cudaStream_t)stream;
@@ -2063,6 +2078,7 @@ int ade_sweep_count_pairs(ade_sweep *sw, long long *pairs_host, void *stream)
 
 int ade_sweep_step(ade_sweep *sw, int nsteps, void *stream)
 {
+    ade::NvtxRange nvtx_("ade_sweep_step");
     if (!sw) return fail(ADE_ERR_ARG, "sweep is NULL");
     if (nsteps < 0) return fail(ADE_ERR_ARG, "nsteps must be >= 0");
     cudaStream_t s = (cudaStream_t)stream;
@@ -2079,6 +2095,7 @@ int ade_sweep_step(ade_sweep *sw, int nsteps, void *stream)
 
 int ade_sweep_run(ade_sweep *sw, int nsteps, void *stream)
 {
+    ade::NvtxRange nvtx_("ade_sweep_run");
     if (!sw) return fail(ADE_ERR_ARG, "sweep is NULL");
     if (nsteps < 0) return fail(ADE_ERR_ARG, "nsteps must be >= 0");
     cudaStream_t s = (cudaStream_t)stream;
@@ -2111,6 +2128,7 @@ int ade_sweep_run(ade_sweep *sw, int nsteps, void *stream)
 
 int ade_sweep_step_timed(ade_sweep *sw, double *phase_ms, void *stream)
 {
+    ade::NvtxRange nvtx_("ade_sweep_step_timed");
     if (!sw || !phase_ms) return fail(ADE_ERR_ARG, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
     int rc = sweep_clear_status_once(sw, s);
