@@ -224,6 +224,36 @@ def cpu_oracle_rate(plume, xq, C, sample, min_seconds, max_steps=None, v=None):
     return pairs / el, steps, el, int(sel.size)
 
 
+def host_cpu_model():
+    """CPU model string of this host (for the CPU-baseline record)."""
+    import platform
+    try:
+        fields = {}
+        for line in open("/proc/cpuinfo"):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                fields.setdefault(k.strip(), v.strip())
+        name = fields.get("model name") or fields.get("Model") or (
+            f"implementer {fields.get('CPU implementer', '?')} part {fields.get('CPU part', '?')}")
+    except OSError:
+        name = platform.processor() or "unknown"
+    return f"{name} ({platform.machine()})"
+
+
+def single_core_baseline(plume, xq, C, sample, seconds=3.0, v=None):
+    """The oracle on one host thread (a smaller sample), next to the all-core figure."""
+    import oracle
+    oracle.build()
+    threads = oracle.max_threads()
+    oracle.set_threads(1)
+    try:
+        value, steps, secs, ns = cpu_oracle_rate(plume, xq, C, max(256, sample // 16), seconds, v=v)
+    finally:
+        oracle.set_threads(threads)
+    return {"value": value, "unit": UNIT, "cores": 1,
+            "sample": f"Eq. 4 evaluated twice per step on {ns} particles; {steps} steps in {secs:.1f} s"}
+
+
 def cpu_oracle_batch(plumes, states, per_plume, min_seconds, max_steps=None):
     """Oracle timing for a batch: Eq. 4 twice per step on a fixed sample of each plume."""
     import oracle
@@ -295,6 +325,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": workload_config(plume),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "cpu_model": host_cpu_model(),
                          "sample": f"Eq. 4 evaluated twice per step on {ns} of {plume.n} particles"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -809,7 +840,10 @@ def run_ours(args):
                                               args.cpu_seconds, v=v)
         line["cpu_baseline"] = {"value": cv, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"Eq. 4 evaluated twice per step on a fixed sample of {ns} "
-                                          f"of {plume.n} particles; {steps} steps in {secs:.1f} s"}
+                                          f"of {plume.n} particles; {steps} steps in {secs:.1f} s",
+                                "cpu_model": host_cpu_model(),
+                                "single_core": single_core_baseline(plume, xq, C, oracle_sample(plume, args.cpu_sample),
+                                                                    v=v)}
     sim.close()
     if rank == 0:
         print(json.dumps(line))

@@ -82,6 +82,10 @@ def _load():
             lib.orc_sort_cells.argtypes = [_i, _p, _i, _p, _p]
             lib.orc_sort_cells.restype = _i
             lib.orc_closed_form.argtypes = [_i, _i, _p, _p, _p, _p, _p, _d, _d, _d, _i, _p]
+            lib.orc_set_threads.argtypes = [_i]
+            lib.orc_set_threads.restype = None
+            lib.orc_max_threads.argtypes = []
+            lib.orc_max_threads.restype = _i
             _lib = lib
     return _lib
 
@@ -311,6 +315,15 @@ def images_needed(box, D, w, t, v=None, tol_sigma=12.0):
     lam = float(np.max(np.linalg.eigvalsh(D)))
     sigma = np.sqrt(w * w + 2.0 * lam * t)
     return int(np.ceil(tol_sigma * sigma / float(np.min(box)))) + 1
+
+
+def set_threads(n):
+    """Host threads of the oracle's OpenMP loops (n <= 0 leaves the setting)."""
+    _load().orc_set_threads(int(n))
+
+
+def max_threads():
+    return int(_load().orc_max_threads())
 
 
 def dt_rule(D, h, rule="lambda_max", coef=0.1):

@@ -566,3 +566,28 @@ void orc_closed_form(int dim, int n, const double *x, const double *box, const d
         C[a] = C0 * s;
     }
 }
+
+/* ------------------------------------------------------------------------- */
+/* Host threads used by the OpenMP loops (for timing on one core or all).    */
+/* ------------------------------------------------------------------------- */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
