@@ -16,6 +16,34 @@ constexpr int kTileThreads = 256;                              // tiled variant
 constexpr int kMaxCellBits = 24;                                // ncells <= 2^24
 constexpr int kScanTileCells = 2048;                            // cells per scan block (cells.cu)
 
+// Programmatic dependent launch (griddepcontrol, sm_90 and later).  A kernel launched by
+// launch_pdl may have its CTAs scheduled while the kernel before it on the stream is still
+// running; it calls pdl_wait() before its first access to memory that earlier work on the stream
+// writes or reads (the wait returns once those grids have completed and their writes are visible;
+// without a programmatic predecessor it returns at once), then pdl_trigger(), which lets the next
+// kernel's CTAs be scheduled once every CTA of this grid has started.  Every kernel of a step
+// starts with both calls, so each launch gap overlaps the tail of the previous kernel and no data
+// dependency changes.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                       Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(block, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // One row of the neighbour-cell stencil: cells (cx - w .. cx + w, cy + dy, cz + dz).
 struct StencilRow {
     signed char dy, dz, w, pad;
@@ -108,9 +136,7 @@ struct EpiOut {
     uint4 *Pout;              // EPI_PREDICT: sorted half-step state
     uint32_t *xq;             // EPI_CORRECT: caller state, updated in place
     float *C;                 // EPI_CORRECT
-    double *partials;         // EPI_CORRECT: per-block {sum C, min C, max C}
-    double *stats;            // EPI_CORRECT: final {sum C, min C, max C}, by the last block
-    unsigned *done;           // EPI_CORRECT: blocks finished (the last block resets it to 0)
+    float4 *wpart;            // EPI_CORRECT: per-warp {sum C as FP32 hi + lo, min C, max C}
     int *status;              // EPI_CORRECT: set to 1 on a non-finite C
     unsigned long long *pairs; // optional in-support pair counter
     float *Q;                 // Eq. 14 (NULL: Eq. 1): flux dC/dt in caller order, updated by the corrector
@@ -131,11 +157,11 @@ struct Work {
     uint32_t *cell_start;  // [ncells + 1]
     uint4 *P0;             // [n] sorted {x, y, z, C} at level l
     uint4 *P1;             // [n] sorted state at level l + 1/2
-    double *partials;      // per-block reduction partials
+    double *partials;      // per-block reduction partials (state statistics)
+    float4 *wpart;         // per-warp partials of the corrector (EpiOut::wpart)
     double *stats;         // {sum C, min C, max C, -, closed-form slots}
     double *cf_partials;   // closed-form error partials
     int *status;           // non-finite flag
-    unsigned *done;        // last-block counter of the corrector
     unsigned long long *pairs;
 };
 
@@ -155,8 +181,10 @@ void pair_coeffs(int dim, double gamma, const double *D, float *Kc, float *c0);
 
 // Launchers (cells.cu, rate.cu, reduce.cu).  All return cudaGetLastError() of the launches.
 int scan_blocks(int m);
+// count_zero: w.count[0, ncells) is known to be zero (every build leaves it zero), so the memset
+// that otherwise starts the build is skipped.
 cudaError_t launch_build_cells(int dim, const uint32_t *xq, const float *C, int n, const int *nc,
-                               int ncells, const Work &w, cudaStream_t s);
+                               int ncells, const Work &w, cudaStream_t s, bool count_zero = false);
 // Batched plumes: keys are coff_p + local key; plume_of[i] gives the plume of caller particle i.
 cudaError_t launch_build_cells_batch(int dim, const uint32_t *xq, const float *C, int n, int ncells,
                                      const RateParams *descs, const uint16_t *plume_of,
@@ -169,7 +197,10 @@ cudaError_t launch_batch_stats(const float *C, const int *offsets, int nplumes, 
 cudaError_t launch_rate(int dim, int kernel, bool iso, int epi, const uint4 *Pe, const uint4 *Pc,
                         const uint32_t *cell_start, const uint32_t *perm, const RateParams &prm,
                         const EpiOut &out, cudaStream_t s);
-cudaError_t launch_reduce_final(const double *partials, int nblocks, double *stats, cudaStream_t s);
+// Fixed-order fold of the corrector's m per-warp partials into stats[0..2] = {sum C (FP64),
+// min C, max C}: one thread-block cluster of up to kFoldMaxCtas CTAs (reduce.cu).
+constexpr int kFoldMaxCtas = 8;
+cudaError_t launch_fold_warp_partials(const float4 *wpart, int m, double *stats, cudaStream_t s);
 cudaError_t launch_closed_form_error(int dim, const uint32_t *xq, const float *C, int n,
                                      const double *box, const double *center, const double *Sinv,
                                      double amp, double C0, double vol, int nimg,
@@ -197,6 +228,8 @@ cudaError_t launch_rate_sweep(int dim, int kernel, int epi, bool count, const ui
 
 int rate_blocks(int n);
 int rate_launch_blocks(int dim, const RateParams &prm, bool iso);
+// Warps of one uniform-velocity rate launch (= per-warp partials its corrector writes).
+int rate_launch_warps(int dim, const RateParams &prm, bool iso);
 size_t tiled_smem_bytes(int dim, const RateParams &prm);
 int closed_form_blocks(int n);
 
@@ -211,6 +244,8 @@ struct ade_ctx {
     int subdiv;
     int ncells_cap;       // workspace capacity in cells (every grid the autotuner may pick)
     int partials_cap;     // workspace capacity in reduction partials
+    int wpart_cap;        // workspace capacity in per-warp corrector partials
+    bool count_clean;     // w.count[0, ncells_cap) is zero (cleared once; every cell build leaves it so)
     uint32_t *xq;
     float *C;
     void *ws;

@@ -295,12 +295,13 @@ void choose_tiles(int dim, int n, const Grid &g, bool iso, unsigned flags, ade::
 }
 
 struct Layout {
-    size_t keys, rank, count, block_sums, perm_tmp, perm, cell_start, P0, P1, partials, stats,
-        cf_partials, status, done, pairs, fVc, fDAc, fDBc, fIncC, fV, fDA, fDB, fInc, fbits, Q, Qh, total;
+    size_t keys, rank, count, block_sums, perm_tmp, perm, cell_start, P0, P1, partials, wpart, stats,
+        cf_partials, status, pairs, fVc, fDAc, fDBc, fIncC, fV, fDA, fDB, fInc, fbits, Q, Qh, total;
 };
 
 // field_dim: 0 for a uniform velocity, else dim (velocity-field buffers are added at the end).
-Layout layout(int n, int ncells, int nb_partials, int field_dim = 0, bool catt = false)
+// nw_partials: per-warp corrector partials of the widest rate launch.
+Layout layout(int n, int ncells, int nb_partials, int nw_partials, int field_dim = 0, bool catt = false)
 {
     Layout L;
     size_t off = 0;
@@ -319,10 +320,10 @@ Layout layout(int n, int ncells, int nb_partials, int field_dim = 0, bool catt =
     L.P0 = take((size_t)n * 16);
     L.P1 = take((size_t)n * 16);
     L.partials = take((size_t)3 * (nb_partials > 0 ? nb_partials : 1) * 8);
+    L.wpart = take((size_t)(nw_partials > 0 ? nw_partials : 1) * 16);
     L.stats = take(8 * 8);
     L.cf_partials = take((size_t)3 * (nb_partials > 0 ? nb_partials : 1) * 8);
     L.status = take(64);
-    L.done = take(64);
     L.pairs = take(64);
     L.fVc = L.fDAc = L.fDBc = L.fIncC = L.fV = L.fDA = L.fDB = L.fInc = L.fbits = 0;
     if (field_dim) {
@@ -354,6 +355,7 @@ struct Derived {
     double Hgrid;    // radius the grid and stencil are built for: H + skin
     Grid g;
     int nb_partials;
+    int nw_partials;
     int ncells_cap;
     ade::RateParams tiles;
     Layout L;
@@ -387,6 +389,7 @@ int derive(const ade_params *p, int n, Derived *d)
     int nbt = ade::rate_launch_blocks(p->dim, d->tiles, iso);
     d->nb_partials = nbr > nbc ? nbr : nbc;
     if (nbt > d->nb_partials) d->nb_partials = nbt;
+    d->nw_partials = std::max(nbr * (ade::kRateThreads / 32), ade::rate_launch_warps(p->dim, d->tiles, iso));
     int ncells_cap = d->g.ncells;
     if (p->cell_subdiv == 0 && p->flags == 0u) {
         // automatic grid: size the workspace for every configuration the autotuner may pick
@@ -399,10 +402,11 @@ int derive(const ade_params *p, int n, Derived *d)
             t.n = n;
             choose_tiles(p->dim, n, g, iso, ADE_FLAG_TILED, &t);
             d->nb_partials = std::max(d->nb_partials, ade::rate_launch_blocks(p->dim, t, iso));
+            d->nw_partials = std::max(d->nw_partials, ade::rate_launch_warps(p->dim, t, iso));
         }
     }
     d->ncells_cap = ncells_cap;
-    d->L = layout(n, ncells_cap, d->nb_partials, p->vmax > 0.0 ? p->dim : 0, p->tau > 0.0);
+    d->L = layout(n, ncells_cap, d->nb_partials, d->nw_partials, p->vmax > 0.0 ? p->dim : 0, p->tau > 0.0);
     return ADE_OK;
 }
 
@@ -438,6 +442,17 @@ int refresh_field(ade_ctx *c, cudaStream_t s)
     return ADE_OK;
 }
 
+// The cell counts arrive uninitialised: clear the whole capacity once (before any graph capture);
+// from then on every cell build leaves them zero.
+int clean_counts(ade_ctx *c, cudaStream_t s)
+{
+    if (!c->count_clean) {
+        ADE_CK(cudaMemsetAsync(c->w.count, 0, (size_t)c->ncells_cap * sizeof(uint32_t), s));
+        c->count_clean = true;
+    }
+    return ADE_OK;
+}
+
 // Enqueue one cell build; in velocity-field mode followed by the permutation of the v and D
 // records into the sorted order.
 int enqueue_cells(ade_ctx *c, cudaStream_t s)
@@ -446,7 +461,13 @@ int enqueue_cells(ade_ctx *c, cudaStream_t s)
     if (rc) return rc;
     rc = refresh_field(c, s);
     if (rc) return rc;
-    ADE_CK(ade::launch_build_cells(c->dim, c->xq, c->C, c->n, c->nc, c->ncells, c->w, s));
+    rc = clean_counts(c, s);
+    if (rc) return rc;
+    cudaError_t e = ade::launch_build_cells(c->dim, c->xq, c->C, c->n, c->nc, c->ncells, c->w, s, true);
+    if (e != cudaSuccess) {
+        c->count_clean = false;   // a build that did not run to the end may leave counts behind
+        return fail(ADE_ERR_CUDA, "%s", cudaGetErrorString(e));
+    }
     if (c->field) ADE_CK(ade::launch_field_permute(c->dim, c->w.perm, c->n, c->fw, s));
     return ADE_OK;
 }
@@ -493,14 +514,23 @@ ade::EpiOut epi_corrector(ade_ctx *c)
     ade::EpiOut out = epi_none();
     out.xq = c->xq;
     out.C = c->C;
-    out.partials = c->w.partials;
-    out.stats = c->w.stats;
-    out.done = c->w.done;
+    out.wpart = c->w.wpart;
     out.status = c->w.status;
     return out;
 }
 
-// Enqueue one predictor-corrector step (Eq. 8-9).
+// FP64 {sum C, min C, max C} of the state the corrector just wrote, folded from its per-warp
+// partials into w.stats (the step's diagnostics of Eq. 9).
+int enqueue_fold(ade_ctx *c, cudaStream_t s)
+{
+    const int m = c->field ? ade::rate_blocks(c->n) * (ade::kRateThreads / 32)
+                           : ade::rate_launch_warps(c->dim, c->rp, c->iso);
+    if (m > c->wpart_cap) return fail(ADE_ERR_CAPACITY, "corrector partials exceed the workspace");
+    ADE_CK(ade::launch_fold_warp_partials(c->w.wpart, m, c->w.stats, s));
+    return ADE_OK;
+}
+
+// Enqueue one predictor-corrector step (Eq. 8-9) and the fold of its diagnostics.
 int enqueue_step(ade_ctx *c, cudaStream_t s)
 {
     int rc = enqueue_cells(c, s);
@@ -510,18 +540,20 @@ int enqueue_step(ade_ctx *c, cudaStream_t s)
     out.Pout = c->w.P1;
     rc = enqueue_eval(c, PREDICTOR, out, s);
     if (rc) return rc;
-    return enqueue_eval(c, CORRECTOR, epi_corrector(c), s);
+    rc = enqueue_eval(c, CORRECTOR, epi_corrector(c), s);
+    if (rc) return rc;
+    return enqueue_fold(c, s);
 }
 
-// The workspace arrives uninitialised: clear the status word once, before the first step.
+// The workspace arrives uninitialised: clear the status word once, before the first step (and
+// the cell counts, so that a step captured into a graph holds no memset).
 int clear_status_once(ade_ctx *c, cudaStream_t s)
 {
     if (!c->status_cleared) {
         ADE_CK(cudaMemsetAsync(c->w.status, 0, sizeof(int), s));
-        ADE_CK(cudaMemsetAsync(c->w.done, 0, sizeof(unsigned), s));
         c->status_cleared = true;
     }
-    return ADE_OK;
+    return clean_counts(c, s);
 }
 
 // kc of W'(r)/r = kc f(q) for support H: Wendland C2 (support 2h, f = (1-q)^3) kc = -20 B / H^2;
@@ -670,6 +702,7 @@ int ade_init_particles(ade_ctx **out, const ade_params *p, int n, uint32_t *xq_d
     c->subdiv = d.g.subdiv;
     c->ncells_cap = d.ncells_cap;
     c->partials_cap = d.nb_partials;
+    c->wpart_cap = d.nw_partials;
     c->xq = xq_dev;
     c->C = C_dev;
     c->ws = workspace_dev;
@@ -685,10 +718,10 @@ int ade_init_particles(ade_ctx **out, const ade_params *p, int n, uint32_t *xq_d
     c->w.P0 = at<uint4>(workspace_dev, d.L.P0);
     c->w.P1 = at<uint4>(workspace_dev, d.L.P1);
     c->w.partials = at<double>(workspace_dev, d.L.partials);
+    c->w.wpart = at<float4>(workspace_dev, d.L.wpart);
     c->w.stats = at<double>(workspace_dev, d.L.stats);
     c->w.cf_partials = at<double>(workspace_dev, d.L.cf_partials);
     c->w.status = at<int>(workspace_dev, d.L.status);
-    c->w.done = at<unsigned>(workspace_dev, d.L.done);
     c->w.pairs = at<unsigned long long>(workspace_dev, d.L.pairs);
 
     rc = plume_constants(p, n, d, c->D, &c->dt, c->inc, c->inc_half, &c->rp, &c->iso);
@@ -740,7 +773,8 @@ int apply_config(ade_ctx *c, int k, int variant)
     t.n = c->n;
     choose_tiles(c->dim, c->n, g, c->iso, tiled ? ADE_FLAG_TILED : ADE_FLAG_DIRECT, &t);
     if (tiled && t.variant != 1) return fail(ADE_ERR_ARG, "tiles do not fit this grid");
-    if (ade::rate_launch_blocks(c->dim, t, c->iso) > c->partials_cap)
+    if (ade::rate_launch_blocks(c->dim, t, c->iso) > c->partials_cap ||
+        ade::rate_launch_warps(c->dim, t, c->iso) > c->wpart_cap)
         return fail(ADE_ERR_CAPACITY, "tiles exceed the workspace");
     for (int i = 0; i < 3; ++i) c->nc[i] = g.nc[i];
     c->ncells = g.ncells;
@@ -1008,13 +1042,9 @@ int ade_step(ade_ctx *c, int nsteps, void *stream)
     return ADE_OK;
 }
 
-int ade_get_stats(ade_ctx *c, ade_stats *st, void *stream)
+// Copies {sum C, min C, max C} from w.stats and the status word out (waits for the stream).
+static int read_stats(ade_ctx *c, ade_stats *st, cudaStream_t s)
 {
-    if (!c || !st) return fail(ADE_ERR_ARG, "NULL argument");
-    cudaStream_t s = (cudaStream_t)stream;
-    int rc0 = clear_status_once(c, s);
-    if (rc0) return rc0;
-    ADE_CK(ade::launch_state_stats(c->C, c->n, c->w.partials, c->w.stats, s));
     double h[3];
     int status = 0;
     ADE_CK(cudaMemcpyAsync(h, c->w.stats, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -1028,6 +1058,16 @@ int ade_get_stats(ade_ctx *c, ade_stats *st, void *stream)
     st->pairs = c->pairs;
     st->status = status ? ADE_ERR_NUMERIC : ADE_OK;
     return status ? fail(ADE_ERR_NUMERIC, "non-finite concentration produced") : ADE_OK;
+}
+
+int ade_get_stats(ade_ctx *c, ade_stats *st, void *stream)
+{
+    if (!c || !st) return fail(ADE_ERR_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc0 = clear_status_once(c, s);
+    if (rc0) return rc0;
+    ADE_CK(ade::launch_state_stats(c->C, c->n, c->w.partials, c->w.stats, s));
+    return read_stats(c, st, s);
 }
 
 int ade_run(ade_ctx *c, int nsteps, ade_stats *st, void *stream)
@@ -1063,8 +1103,10 @@ int ade_run(ade_ctx *c, int nsteps, ade_stats *st, void *stream)
     for (int k = 0; k < nsteps; ++k) ADE_CK(cudaGraphLaunch(c->graph_exec, s));
     c->step += nsteps;
     c->t += nsteps * c->dt;
-    if (st) return ade_get_stats(c, st, stream);
-    return ADE_OK;
+    if (!st) return ADE_OK;
+    // the last step folded the diagnostics of the state it wrote (the current state)
+    if (nsteps > 0 && c->n > 0) return read_stats(c, st, s);
+    return ade_get_stats(c, st, stream);
 }
 
 int ade_step_timed(ade_ctx *c, double *phase_ms, void *stream)
@@ -1092,6 +1134,8 @@ int ade_step_timed(ade_ctx *c, double *phase_ms, void *stream)
         rc = enqueue_eval(c, CORRECTOR, epi_corrector(c), s);
         if (rc) return rc;
         ADE_CK(cudaEventRecord(c->ev[3], s));
+        rc = enqueue_fold(c, s);
+        if (rc) return rc;
     } else {
         ADE_CK(cudaEventRecord(c->ev[2], s));
         ADE_CK(cudaEventRecord(c->ev[3], s));
@@ -1111,9 +1155,9 @@ int ade_step_timed(ade_ctx *c, double *phase_ms, void *stream)
 int ade_launches_per_step(const ade_ctx *c, int *launches)
 {
     if (!c || !launches) return fail(ADE_ERR_ARG, "NULL argument");
-    // count, 3 scan launches, place, order, [velocity-field gather,] predictor, corrector (the
-    // memset is not a kernel)
-    *launches = c->n > 0 ? 8 + (c->field ? 1 : 0) : 4;
+    // count, 3 scan launches, place, order, [velocity-field gather,] predictor, corrector, fold
+    // of the corrector's partials (the memset is not a kernel)
+    *launches = c->n > 0 ? 9 + (c->field ? 1 : 0) : 4;
     return ADE_OK;
 }
 
@@ -1977,10 +2021,10 @@ int ade_sweep_init(ade_sweep **out, const ade_params *p, int n, int ntheta, cons
     sw->w.P0 = at<uint4>(workspace_dev, W.P0);
     sw->w.P1 = at<uint4>(workspace_dev, W.P1);
     sw->w.partials = at<double>(workspace_dev, W.partials);
+    sw->w.wpart = at<float4>(workspace_dev, W.wpart);
     sw->w.stats = at<double>(workspace_dev, W.stats);
     sw->w.cf_partials = at<double>(workspace_dev, W.cf_partials);
     sw->w.status = at<int>(workspace_dev, W.status);
-    sw->w.done = at<unsigned>(workspace_dev, W.done);
     sw->w.pairs = at<unsigned long long>(workspace_dev, W.pairs);
     sw->Cs0 = at<float>(workspace_dev, L.Cs0);
     sw->Cs1 = at<float>(workspace_dev, L.Cs1);

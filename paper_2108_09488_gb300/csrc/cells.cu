@@ -46,6 +46,8 @@ __global__ __launch_bounds__(kThreads) void k_count(const uint32_t *__restrict__
                                                     uint32_t *__restrict__ rank,
                                                     uint32_t *__restrict__ count)
 {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * kThreads + threadIdx.x;
     if (i >= n) return;
     const uint32_t key = cell_key(xq, n, i, dim, ncx, ncy, ncz);
@@ -88,6 +90,8 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *t
 __global__ __launch_bounds__(kThreads) void k_scan_blocks(const uint32_t *__restrict__ count, int m,
                                                           uint32_t *__restrict__ block_sums)
 {
+    pdl_wait();
+    pdl_trigger();
     const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
     uint32_t s = 0u;
 #pragma unroll
@@ -107,6 +111,8 @@ __global__ __launch_bounds__(kThreads) void k_scan_blocks(const uint32_t *__rest
 // One block: exclusive scan of the block sums in place, kScanTile at a time with a carry.
 __global__ __launch_bounds__(kThreads) void k_scan_top(uint32_t *__restrict__ block_sums, int nb)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t total;
     uint32_t carry = 0u;
     for (int chunk = 0; chunk < nb; chunk += kScanTile) {
@@ -129,17 +135,24 @@ __global__ __launch_bounds__(kThreads) void k_scan_top(uint32_t *__restrict__ bl
     }
 }
 
-__global__ __launch_bounds__(kThreads) void k_scan_apply(const uint32_t *__restrict__ count, int m,
+// Also clears count (each entry is read here once, by one thread), so the next build finds it zero.
+__global__ __launch_bounds__(kThreads) void k_scan_apply(uint32_t *__restrict__ count, int m,
                                                          const uint32_t *__restrict__ block_off,
                                                          uint32_t *__restrict__ start)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t total;
     const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
     uint32_t v[kScanItems];
     uint32_t s = 0u;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        v[k] = base + k < m ? __ldg(count + base + k) : 0u;
+        v[k] = 0u;
+        if (base + k < m) {
+            v[k] = count[base + k];
+            count[base + k] = 0u;
+        }
         s += v[k];
     }
     uint32_t run = block_exclusive_scan(s, &total) + __ldg(block_off + blockIdx.x);
@@ -156,6 +169,8 @@ __global__ __launch_bounds__(kThreads) void k_place(const uint32_t *__restrict__
                                                     const uint32_t *__restrict__ start,
                                                     uint32_t *__restrict__ perm_tmp)
 {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * kThreads + threadIdx.x;
     if (i >= n) return;
     const uint32_t pos = __ldg(start + __ldg(keys + i)) + __ldg(rank + i);
@@ -240,6 +255,8 @@ __global__ __launch_bounds__(kThreads) void k_order(const uint32_t *__restrict__
                                                     uint32_t *__restrict__ perm,
                                                     uint4 *__restrict__ P)
 {
+    pdl_wait();
+    pdl_trigger();
     const int c = blockIdx.x * kThreads + threadIdx.x;
     uint32_t s = 0u, e = 0u;
     if (c < ncells) {
@@ -264,6 +281,8 @@ __global__ __launch_bounds__(kThreads) void k_order_block(const uint32_t *__rest
                                                           const float *__restrict__ C, int n, int dim,
                                                           uint32_t *__restrict__ perm, uint4 *__restrict__ P)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t chunk[kRankChunk];
     const int c = blockIdx.x;
     if (c >= ncells) return;
@@ -385,27 +404,29 @@ cudaError_t launch_build_cells_batch(int dim, const uint32_t *xq, const float *C
 }
 
 cudaError_t launch_build_cells(int dim, const uint32_t *xq, const float *C, int n, const int *nc,
-                               int ncells, const Work &w, cudaStream_t s)
+                               int ncells, const Work &w, cudaStream_t s, bool count_zero)
 {
-    cudaError_t e = cudaMemsetAsync(w.count, 0, (size_t)ncells * sizeof(uint32_t), s);
+    cudaError_t e = count_zero ? cudaSuccess : cudaMemsetAsync(w.count, 0, (size_t)ncells * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     const int nb = (n + kThreads - 1) / kThreads;
-    if (nb > 0)
-        k_count<<<nb, kThreads, 0, s>>>(xq, n, dim, nc[0], nc[1], nc[2], w.keys, w.rank, w.count);
+    if (nb > 0 && e == cudaSuccess)
+        e = launch_pdl(k_count, nb, kThreads, 0, s, xq, n, dim, nc[0], nc[1], nc[2], w.keys, w.rank, w.count);
     const int sb = scan_blocks(ncells);
-    k_scan_blocks<<<sb, kThreads, 0, s>>>(w.count, ncells, w.block_sums);
-    k_scan_top<<<1, kThreads, 0, s>>>(w.block_sums, sb);
-    k_scan_apply<<<sb, kThreads, 0, s>>>(w.count, ncells, w.block_sums, w.cell_start);
-    if (nb > 0) {
-        k_place<<<nb, kThreads, 0, s>>>(w.keys, w.rank, n, w.cell_start, w.perm_tmp);
+    if (e == cudaSuccess) e = launch_pdl(k_scan_blocks, sb, kThreads, 0, s, w.count, ncells, w.block_sums);
+    if (e == cudaSuccess) e = launch_pdl(k_scan_top, 1, kThreads, 0, s, w.block_sums, sb);
+    if (e == cudaSuccess)
+        e = launch_pdl(k_scan_apply, sb, kThreads, 0, s, w.count, ncells, w.block_sums, w.cell_start);
+    if (nb > 0 && e == cudaSuccess) {
+        e = launch_pdl(k_place, nb, kThreads, 0, s, w.keys, w.rank, n, w.cell_start, w.perm_tmp);
+        if (e != cudaSuccess) return e;
         if ((long long)n >= 16ll * ncells)   // many particles per cell: one block per cell
-            k_order_block<<<ncells, kThreads, 0, s>>>(w.cell_start, ncells, w.perm_tmp, xq, C, n, dim, w.perm,
-                                                      w.P0);
+            e = launch_pdl(k_order_block, ncells, kThreads, 0, s, w.cell_start, ncells, w.perm_tmp, xq, C, n,
+                           dim, w.perm, w.P0);
         else
-            k_order<<<(ncells + kThreads - 1) / kThreads, kThreads, 0, s>>>(w.cell_start, ncells, w.perm_tmp,
-                                                                             xq, C, n, dim, w.perm, w.P0);
+            e = launch_pdl(k_order, (ncells + kThreads - 1) / kThreads, kThreads, 0, s, w.cell_start, ncells,
+                           w.perm_tmp, xq, C, n, dim, w.perm, w.P0);
     }
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace ade

@@ -207,10 +207,13 @@ __device__ float rate_direct(const uint4 *__restrict__ Pe, const uint32_t *__res
 // epilogue and block reductions
 // ---------------------------------------------------------------------------------------------
 // Writes of one particle at sorted position gi; pe = evaluation state {x, y, z, C}.
-template <int DIM, int EPI>
+// PRE (corrector): the caller index a_pre = perm[gi] and C^l = C[a_pre] were loaded before the
+// pair loop, so their latency hides behind it.
+template <int DIM, int EPI, bool PRE = false>
 __device__ __forceinline__ void epilogue(int gi, float rate, const uint4 &pe,
                                          const uint32_t *__restrict__ perm, const RateParams &prm,
-                                         const EpiOut &out, Acc &acc)
+                                         const EpiOut &out, Acc &acc, uint32_t a_pre = 0u,
+                                         float C_pre = 0.f)
 {
     if (EPI == EPI_RATE) {
         if (out.rate) {
@@ -239,7 +242,7 @@ __device__ __forceinline__ void epilogue(int gi, float rate, const uint4 &pe,
         // evaluation position minus the half-step drift (exact in fixed point); C^l is still in
         // the caller's array, read just before this thread overwrites it.  Eq. 14:
         // C^{l+1} = C^l + dt Q^{l+1/2}, Q^{l+1} = Q^l + dt (r^{l+1/2} - Q^{l+1/2}) / tau.
-        const uint32_t a = __ldg(perm + gi);
+        const uint32_t a = PRE ? a_pre : __ldg(perm + gi);
         float Cn = 0.f;
         if (a - (uint32_t)prm.goff < (uint32_t)prm.n) {
             float dC = rate;
@@ -249,7 +252,7 @@ __device__ __forceinline__ void epilogue(int gi, float rate, const uint4 &pe,
                 out.Q[a] = fmaf(prm.dt, (rate - qh) * out.tau_inv, q);
                 dC = qh;
             }
-            Cn = fmaf(prm.dt, dC, out.C[a]);
+            Cn = fmaf(prm.dt, dC, PRE ? C_pre : out.C[a]);
             out.C[a] = Cn;
             out.xq[a] = pe.x - prm.back[0] + prm.inc[0];
             out.xq[(size_t)prm.n + a] = pe.y - prm.back[1] + prm.inc[1];
@@ -272,6 +275,8 @@ __global__ __launch_bounds__(kRateThreads) void k_rate(const uint4 *__restrict__
                                                        const uint32_t *__restrict__ perm,
                                                        const RateParams prm, const EpiOut out)
 {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * kRateThreads + threadIdx.x;
     const bool valid = i < prm.n;
     const int ii = valid ? i : prm.n - 1;
@@ -282,12 +287,21 @@ __global__ __launch_bounds__(kRateThreads) void k_rate(const uint4 *__restrict__
     const int cz = DIM == 3 ? (int)__umulhi(pa.z - prm.back[2], (uint32_t)prm.ncz) : 0;
     Acc acc{0.f, 0.f, __int_as_float(0x7f800000), __int_as_float(0xff800000), 0u};
     unsigned cnt = 0u;
+    // Corrector: the caller index and C^l are loaded ahead of the pair loop (not in the trimmed
+    // walk, where the two live registers cost more occupancy than the hidden latency gains).
+    constexpr bool PRE = EPI == EPI_CORRECT && !TRIM;
+    uint32_t a_pre = 0u;
+    float C_pre = 0.f;
+    if (PRE) {
+        a_pre = __ldg(perm + ii);
+        if (a_pre - (uint32_t)prm.goff < (uint32_t)prm.n) C_pre = out.C[a_pre];
+    }
     const float rate = rate_direct<DIM, KERNEL, ISO, COUNT, BF, TRIM>(Pe, cs, pa, cx, cy, cz, prm, cnt);
     if (valid) {
         acc.cnt = cnt;
-        epilogue<DIM, EPI>(i, rate, pa, perm, prm, out, acc);
+        epilogue<DIM, EPI, PRE>(i, rate, pa, perm, prm, out, acc, a_pre, C_pre);
     }
-    block_finish<EPI, COUNT, kRateThreads>(acc, out);
+    warp_finish<EPI, COUNT, kRateThreads>(acc, out);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -310,6 +324,8 @@ __global__ __launch_bounds__(kTileThreads, 2) void k_rate_tiled(const uint4 *__r
                                                              const uint32_t *__restrict__ perm,
                                                              const RateParams prm, const EpiOut out)
 {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ float4 smem[];
     __shared__ int s_total;
     __shared__ int wsum[kTileThreads / 32];
@@ -468,7 +484,7 @@ __global__ __launch_bounds__(kTileThreads, 2) void k_rate_tiled(const uint4 *__r
         acc.cnt += cnt;
         epilogue<DIM, EPI>(gi, rate, pe, perm, prm, out, acc);
     }
-    block_finish<EPI, COUNT, kTileThreads>(acc, out);
+    warp_finish<EPI, COUNT, kTileThreads>(acc, out);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -561,8 +577,7 @@ cudaError_t launch_variant(bool iso, const uint4 *Pe, const uint4 *Pc, const uin
         auto fn = k_rate_tiled<DIM, KERNEL, EPI, COUNT>;
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        fn<<<blocks, kTileThreads, smem, s>>>(Pe, Pc, cs, perm, prm, out);
-        return cudaGetLastError();
+        return launch_pdl(fn, blocks, kTileThreads, smem, s, Pe, Pc, cs, perm, prm, out);
     }
     const int blocks = rate_blocks(prm.n);
     const bool bf = prm.variant != 2 && prm.variant != 4;   // 2, 4: branched direct walk
@@ -571,19 +586,19 @@ cudaError_t launch_variant(bool iso, const uint4 *Pe, const uint4 *Pc, const uin
     if (iso) {
         if (trim) {
             if (bf)
-                k_rate<DIM, KERNEL, EPI, true, false, true, true><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
+                return launch_pdl(k_rate<DIM, KERNEL, EPI, true, false, true, true>, blocks, kRateThreads, 0, s, Pe, Pc, cs, perm, prm, out);
             else
-                k_rate<DIM, KERNEL, EPI, true, false, false, true><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
+                return launch_pdl(k_rate<DIM, KERNEL, EPI, true, false, false, true>, blocks, kRateThreads, 0, s, Pe, Pc, cs, perm, prm, out);
         } else if (bf) {
-            k_rate<DIM, KERNEL, EPI, true, COUNT, true, false><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
+            return launch_pdl(k_rate<DIM, KERNEL, EPI, true, COUNT, true, false>, blocks, kRateThreads, 0, s, Pe, Pc, cs, perm, prm, out);
         } else {
-            k_rate<DIM, KERNEL, EPI, true, COUNT, false, false><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
+            return launch_pdl(k_rate<DIM, KERNEL, EPI, true, COUNT, false, false>, blocks, kRateThreads, 0, s, Pe, Pc, cs, perm, prm, out);
         }
     } else {
         if (bf)
-            k_rate<DIM, KERNEL, EPI, false, COUNT, true, false><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
+            return launch_pdl(k_rate<DIM, KERNEL, EPI, false, COUNT, true, false>, blocks, kRateThreads, 0, s, Pe, Pc, cs, perm, prm, out);
         else
-            k_rate<DIM, KERNEL, EPI, false, COUNT, false, false><<<blocks, kRateThreads, 0, s>>>(Pe, Pc, cs, perm, prm, out);
+            return launch_pdl(k_rate<DIM, KERNEL, EPI, false, COUNT, false, false>, blocks, kRateThreads, 0, s, Pe, Pc, cs, perm, prm, out);
     }
     return cudaGetLastError();
 }
@@ -616,6 +631,12 @@ int rate_launch_blocks(int dim, const RateParams &prm, bool iso)
 {
     if (prm.variant == 1 && iso) return prm.ntx * prm.nty * (dim == 3 ? prm.ntz : 1);
     return rate_blocks(prm.n);
+}
+
+int rate_launch_warps(int dim, const RateParams &prm, bool iso)
+{
+    if (prm.variant == 1 && iso) return rate_launch_blocks(dim, prm, iso) * (kTileThreads / 32);
+    return rate_blocks(prm.n) * (kRateThreads / 32);
 }
 
 size_t tiled_smem_bytes(int dim, const RateParams &prm)

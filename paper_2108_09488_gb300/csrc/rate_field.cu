@@ -138,6 +138,8 @@ __global__ __launch_bounds__(kT) void k_field_permute(const uint32_t *__restrict
                                                       float4 *__restrict__ V, float4 *__restrict__ DA,
                                                       float4 *__restrict__ DB, uint4 *__restrict__ Inc)
 {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * kT + threadIdx.x;
     if (i >= n) return;
     const uint32_t a = __ldg(perm + i);
@@ -154,6 +156,8 @@ __global__ __launch_bounds__(kT) void k_rate_field(const uint4 *__restrict__ Pe,
                                                    const float4 *__restrict__ DB, const uint4 *__restrict__ Inc,
                                                    const RateParams prm, const FieldParams fp, const EpiOut out)
 {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * kT + threadIdx.x;
     const bool valid = i < prm.n;
     const int ii = valid ? i : prm.n - 1;
@@ -301,7 +305,7 @@ __global__ __launch_bounds__(kT) void k_rate_field(const uint4 *__restrict__ Pe,
             acc.mx = fmaxf(acc.mx, Cn);
         }
     }
-    block_finish<EPI, COUNT, kT>(acc, out);
+    warp_finish<EPI, COUNT, kT>(acc, out);
 }
 
 template <int DIM, int KERNEL, bool COUNT>
@@ -311,16 +315,13 @@ void launch_field_epi(int epi, int blocks, const uint4 *Pe, const uint32_t *cs, 
 {
     switch (epi) {
     case EPI_RATE:
-        k_rate_field<DIM, KERNEL, EPI_RATE, COUNT>
-            <<<blocks, kT, 0, s>>>(Pe, cs, perm, fw.V, fw.DA, fw.DB, fw.Inc, prm, fp, out);
+        launch_pdl(k_rate_field<DIM, KERNEL, EPI_RATE, COUNT>, blocks, kT, 0, s, Pe, cs, perm, fw.V, fw.DA, fw.DB, fw.Inc, prm, fp, out);
         break;
     case EPI_PREDICT:
-        k_rate_field<DIM, KERNEL, EPI_PREDICT, COUNT>
-            <<<blocks, kT, 0, s>>>(Pe, cs, perm, fw.V, fw.DA, fw.DB, fw.Inc, prm, fp, out);
+        launch_pdl(k_rate_field<DIM, KERNEL, EPI_PREDICT, COUNT>, blocks, kT, 0, s, Pe, cs, perm, fw.V, fw.DA, fw.DB, fw.Inc, prm, fp, out);
         break;
     default:
-        k_rate_field<DIM, KERNEL, EPI_CORRECT, COUNT>
-            <<<blocks, kT, 0, s>>>(Pe, cs, perm, fw.V, fw.DA, fw.DB, fw.Inc, prm, fp, out);
+        launch_pdl(k_rate_field<DIM, KERNEL, EPI_CORRECT, COUNT>, blocks, kT, 0, s, Pe, cs, perm, fw.V, fw.DA, fw.DB, fw.Inc, prm, fp, out);
         break;
     }
 }
@@ -362,9 +363,9 @@ cudaError_t launch_field_permute(int dim, const uint32_t *perm, int n, const Fie
     if (n == 0) return cudaSuccess;
     const int blocks = (n + kT - 1) / kT;
     if (dim == 2)
-        k_field_permute<2><<<blocks, kT, 0, s>>>(perm, n, fw.Vc, fw.DAc, fw.DBc, fw.IncC, fw.V, fw.DA, fw.DB, fw.Inc);
+        launch_pdl(k_field_permute<2>, blocks, kT, 0, s, perm, n, fw.Vc, fw.DAc, fw.DBc, fw.IncC, fw.V, fw.DA, fw.DB, fw.Inc);
     else
-        k_field_permute<3><<<blocks, kT, 0, s>>>(perm, n, fw.Vc, fw.DAc, fw.DBc, fw.IncC, fw.V, fw.DA, fw.DB, fw.Inc);
+        launch_pdl(k_field_permute<3>, blocks, kT, 0, s, perm, n, fw.Vc, fw.DAc, fw.DBc, fw.IncC, fw.V, fw.DA, fw.DB, fw.Inc);
     return cudaGetLastError();
 }
 

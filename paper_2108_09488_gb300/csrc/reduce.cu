@@ -1,12 +1,15 @@
 // reduce.cu -- FP64 reductions of the particle state and the closed-form error norms.
 //
-//   * k_reduce_final: deterministic fixed-order reduction of per-block partials written by the
-//     corrector epilogue: sum C (the host multiplies by m for sum m C), min C, max C.
+//   * k_fold_warp_partials: deterministic fixed-order fold of the per-warp partials written by
+//     the corrector epilogue: sum C (the host multiplies by m for sum m C), min C, max C.
+//   * k_state_partials + k_reduce_final: the same statistics of any concentration array.
 //   * k_closed_form_err: the closed form of Sec. 3 (Eq. 12-13 in 2D; the same Gaussian in 3D) at
 //     every particle, C_an = C0 w^d / sqrt(det S) sum_images exp(-1/2 xi^T S^-1 xi),
 //     S = w^2 I + 2 t D, xi = x - (x0 + v t) + image shift, and the per-block partials of
 //     sum (C - C_an)^2, max |C - C_an| and max |C_an| (error norms of Table 2 and Figs. 5, 7).
 // Both run in FP64: they are off the per-pair path and read each particle once.
+#include <cooperative_groups.h>
+
 #include "ade_internal.h"
 
 namespace ade {
@@ -48,6 +51,91 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce_final(const double *__re
         out[1] = sh[1][0];
         out[2] = sh[2][0];
     }
+}
+
+// Fold of the corrector's m per-warp partials {hi, lo, min, max} by one thread-block cluster of
+// G <= 8 CTAs (G fixed by m alone).  CTA r folds the contiguous chunk [r chunk, (r + 1) chunk):
+// thread t takes partials t, t + T, ... in order (up to eight loads in flight) with the error-free
+// two-sum in FP32, then a fixed shuffle tree per warp; warp 0 of the CTA folds its warps' results
+// by the same tree; CTA 0 reads the G CTA results through distributed shared memory and folds
+// them in CTA order.  Only the final hi + lo is formed in FP64: dependent FP64 operations are slow
+// on this part.  No fence or atomic; the order does not depend on timing.
+constexpr int kFoldThreads = 1024;
+constexpr int kFoldPerCta = 1024;   // partials per CTA before another CTA of the cluster is used
+static_assert(kFoldMaxCtas <= 32, "CTA 0 folds one CTA result per lane of one warp");
+
+__device__ __forceinline__ void fold_two_sum(float &hi, float &lo, float x, float xlo)
+{
+    const float s = hi + x;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (x - bb);
+    hi = s;
+    lo = lo + (err + xlo);
+}
+
+// Fixed shuffle tree over the 32 lanes of {hi, lo, min, max}; lane 0 holds the result.
+__device__ __forceinline__ float4 fold_warp(float4 r)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, r.x, o);
+        const float l2 = __shfl_down_sync(0xffffffffu, r.y, o);
+        r.z = fminf(r.z, __shfl_down_sync(0xffffffffu, r.z, o));
+        r.w = fmaxf(r.w, __shfl_down_sync(0xffffffffu, r.w, o));
+        fold_two_sum(r.x, r.y, h2, l2);
+    }
+    return r;
+}
+
+__global__ __launch_bounds__(kFoldThreads) void k_fold_warp_partials(const float4 *__restrict__ wp, int m,
+                                                                     int chunk, double *__restrict__ stats)
+{
+    pdl_wait();
+    pdl_trigger();
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    __shared__ float4 wres[kFoldThreads / 32];
+    __shared__ float4 cres;
+    const float inf = __int_as_float(0x7f800000);
+    const int rank = (int)cluster.block_rank();
+    const int b0 = rank * chunk;
+    const int b1 = min(m, b0 + chunk);
+    float hi = 0.f, lo = 0.f, mn = inf, mx = -inf;
+    constexpr int U = 8;
+    for (int k0 = b0 + (int)threadIdx.x; k0 < b1; k0 += U * kFoldThreads) {
+        float4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = k0 + u * kFoldThreads;
+            v[u] = k < b1 ? __ldcg(wp + k) : make_float4(0.f, 0.f, inf, -inf);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            fold_two_sum(hi, lo, v[u].x, v[u].y);
+            mn = fminf(mn, v[u].z);
+            mx = fmaxf(mx, v[u].w);
+        }
+    }
+    const float4 w = fold_warp(make_float4(hi, lo, mn, mx));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) wres[wid] = w;
+    __syncthreads();
+    if (wid == 0) {
+        const float4 r = fold_warp(wres[lane]);   // kFoldThreads / 32 == 32 warps
+        if (lane == 0) cres = r;
+    }
+    cluster.sync();
+    if (rank == 0 && wid == 0) {
+        const int G = (int)cluster.num_blocks();
+        float4 r = make_float4(0.f, 0.f, inf, -inf);
+        if (lane < G) r = *cluster.map_shared_rank(&cres, lane);
+        r = fold_warp(r);
+        if (lane == 0) {
+            stats[0] = (double)r.x + (double)r.y;
+            stats[1] = (double)r.z;
+            stats[2] = (double)r.w;
+        }
+    }
+    cluster.sync();   // CTA 0 has read every CTA's result before any CTA exits
 }
 
 struct CFParams {
@@ -208,10 +296,27 @@ cudaError_t launch_state_stats(const float *C, int n, double *partials, double *
 
 int closed_form_blocks(int n) { return (n + kRedThreads - 1) / kRedThreads; }
 
-cudaError_t launch_reduce_final(const double *partials, int nblocks, double *stats, cudaStream_t s)
+cudaError_t launch_fold_warp_partials(const float4 *wpart, int m, double *stats, cudaStream_t s)
 {
-    k_reduce_final<<<1, kRedThreads, 0, s>>>(partials, nblocks, 0, stats);
-    return cudaGetLastError();
+    if (m <= 0) return cudaSuccess;
+    int G = (m + kFoldPerCta - 1) / kFoldPerCta;
+    if (G > kFoldMaxCtas) G = kFoldMaxCtas;
+    const int chunk = (m + G - 1) / G;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)G, 1, 1);
+    cfg.blockDim = dim3(kFoldThreads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)G;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // see pdl_wait
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, k_fold_warp_partials, wpart, m, chunk, stats);
 }
 
 cudaError_t launch_closed_form_error(int dim, const uint32_t *xq, const float *C, int n,

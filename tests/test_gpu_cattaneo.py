@@ -101,6 +101,7 @@ def test_cattaneo_graph_replay_mass_and_state_checks(lib):
     assert np.array_equal(xa, xb) and np.array_equal(Ca.view(np.uint32), Cb.view(np.uint32))
     assert np.array_equal(a.flux().cpu().numpy().view(np.uint32), b.flux().cpu().numpy().view(np.uint32))
     assert st.status == 0 and abs(st.mass - m0) <= 1e-6 * m0       # sum Q(0) = 0 conserves mass
+    assert st.c_min == Cb.astype(np.float64).min() and st.c_max == Cb.astype(np.float64).max()
 
 
 def test_cattaneo_small_tau_approaches_fick(lib):

@@ -172,6 +172,10 @@ def test_field_run_graph_equals_step_bitwise(lib):
     xb, Cb = b.state()
     assert np.array_equal(xa, xb) and np.array_equal(Ca.view(np.uint32), Cb.view(np.uint32))
     assert st.step == 5 and st.status == 0
+    # the statistics are the field corrector's folded per-warp partials
+    C64 = Cb.astype(np.float64)
+    assert st.c_min == C64.min() and st.c_max == C64.max()
+    assert st.mass == pytest.approx(b.stats().mass, rel=1e-12)
 
 
 def test_field_autotune_keeps_state_and_parity(lib, orc):

@@ -305,6 +305,41 @@ def test_nonfinite_concentration_sets_status(lib):
     assert st.status == -3
 
 
+def _check_run_stats(st, plume, C):
+    """Statistics of ade_run against the returned state: sum m C within 1e-12 (FP32 two-sum warp
+    partials folded in FP64), min and max exact."""
+    C64 = C.astype(np.float64)
+    assert st.status == 0
+    assert st.mass == pytest.approx(plume.mass * C64.sum(), rel=1e-12)
+    assert st.c_min == C64.min() and st.c_max == C64.max()
+
+
+@pytest.mark.parametrize("variant", sorted(VARIANTS))
+@pytest.mark.parametrize("side", [64, 256])
+def test_run_stats_are_the_folded_corrector_partials(lib, variant, side):
+    """ade_run's statistics are the corrector's per-warp partials folded on the device (one fold
+    block at 64^2, two at 256^2), for every interaction variant; a fresh ade_get_stats over the
+    state agrees."""
+    plume = inputs.ladder_2d(side, 10) if side > 64 else inputs.lattice_2d_64()
+    sim = _sim(lib, plume, flags=VARIANTS[variant])
+    st = sim.run(3)
+    _, C = sim.state()
+    _check_run_stats(st, plume, C)
+    ref = sim.stats()
+    assert ref.mass == pytest.approx(st.mass, rel=1e-12)
+    assert (ref.c_min, ref.c_max) == (st.c_min, st.c_max)
+
+
+def test_run_stats_fold_capped_block_count(lib):
+    """4.41 M particles (137,813 warp partials): the fold uses its maximum of 128 blocks, so each
+    block folds more than one pass of its threads."""
+    plume = _plume(side=2100, h_dx=1.3, jitter=0.2, seed=4)
+    sim = _sim(lib, plume)
+    st = sim.run(1)
+    _, C = sim.state()
+    _check_run_stats(st, plume, C)
+
+
 def test_full_size_ladder_top_rung(lib, orc):
     """The benchmark workload (1024^2, 120 neighbours, ratio 10) in the bench's launch
     configuration: full rate parity, pair count and one step."""

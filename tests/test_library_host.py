@@ -158,7 +158,7 @@ def test_velocity_field_mode_time_step_skin_and_grid(adelib, orc, rule):
         k = info.cell_subdiv
         assert info.nc[0] == math.floor(k / (info.support + info.skin))
         assert info.variant == 0
-        assert adelib.launches_per_step(ctx) == 9
+        assert adelib.launches_per_step(ctx) == 10
         assert nbytes >= (64 + 32) * plume.n   # caller-order and sorted V, D records + 2 sorted states
     finally:
         adelib.destroy(ctx)
