@@ -84,9 +84,20 @@ MUFU_LANES_PER_SM = 16
 # of the current kernels (profiles/k_rate_ladder1024.md, profiles/k_rate_batch_batched64.md,
 # profiles/k_rate_field_field1024.md, profiles/k_rate_paper1m.md, profiles/k_rate_sweep_sweep512.md).
 # Set an entry to None whenever the kernel changes until it is captured again.
-TRAFFIC_PER_LAUNCH = {"ladder-1024-n120-r10": 22.81e6, "batched-64": 42.12e6,
-                      "field-1024-n120-r10": 82.75e6, "paper-1m-n31k-c4": 20.05e6,
-                      "sweep-512-8": 18.77e6}
+# DRAM bytes (read + write) per launch of the dominant kernel, mean of one predictor and one
+# corrector launch from `ncu --set full` captures (profiles/), keyed by workload and walk; a walk
+# without a capture of the current kernel reports null
+TRAFFIC_PER_LAUNCH = {("ladder-1024-n120-r10", "direct-branch-free"): 23.84e6,
+                      ("ladder-1024-n120-r10", "direct-branch-free-trimmed"): 23.82e6,
+                      ("batched-64", None): 42.12e6,
+                      ("field-1024-n120-r10", "velocity-field-direct"): 82.21e6,
+                      ("paper-1m-n31k-c4", "direct-branch-free-trimmed"): 20.19e6,
+                      ("sweep-512-8", None): 18.77e6}
+# interaction walks (ade flags) selectable with --variant; "auto" autotunes grid and walk
+VARIANT_FLAGS = {"direct-branch-free": 1, "tiled": 2, "direct-branched": 4,
+                 "direct-branch-free-trimmed": 9, "direct-branched-trimmed": 12}
+VARIANT_NAMES = {0: "direct-branch-free", 1: "tiled", 2: "direct-branched", 3: "direct-branch-free-trimmed",
+                 4: "direct-branched-trimmed"}
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
 
@@ -412,7 +423,7 @@ def run_batched(args):
     peak = props.multi_processor_count * FP32_LANES_PER_SM * f_max * 1e6 / I_MIN[2] / 1e9
     achieved = pairs / (rate_avg_ms * 1e-3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
-                "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get("batched-64"),
+                "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(("batched-64", None)),
                 "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "kernel": "k_rate_batch (predictor + corrector)",
                 "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
@@ -629,7 +640,7 @@ def run_sweep(args):
     peak = sms * FP32_LANES_PER_SM * f_max * 1e6 / per_set / 1e9
     achieved = pairs * P / (rate_ms * 1e-3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair-sets/s",
-                "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get("sweep-512-8"),
+                "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(("sweep-512-8", None)),
                 "traffic_unit": "bytes per evaluation (ncu dram read + write, all groups)",
                 "kernel": "k_rate_sweep (predictor + corrector, one group of 8 sets)",
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {f_max:.0f} MHz / "
@@ -719,12 +730,17 @@ def run_ours(args):
         # relaxation time of Eq. 14: twice the parabolic step 0.1 h^2 / lambda_max(D)
         lam = max(plume.alpha_L, plume.alpha_T) * plume.speed + plume.D_m
         tau = 2.0 * 0.1 * plume.h ** 2 / lam
-    sim = ade.Simulation(ade.params_for(plume, vmax=vmax, tau=tau), xq, C, device=device)
+    pinned = args.variant != "auto" or args.cell_subdiv > 0
+    if pinned and v is not None and args.variant not in ("auto", "direct-branch-free"):
+        raise SystemExit("velocity-field mode has one walk (direct-branch-free)")
+    extra = {} if not pinned else {"flags": VARIANT_FLAGS.get(args.variant, 0), "cell_subdiv": args.cell_subdiv}
+    sim = ade.Simulation(ade.params_for(plume, vmax=vmax, tau=tau, **extra), xq, C, device=device)
     if v is not None:
         sim.set_velocity_field(v)
     if tau > 0.0:
         sim.set_flux()            # Q(0) = R(C(0)); the flux stays resident between e2e steps
-    tune_ms = sim.autotune()
+    tune_ms = None if pinned else sim.autotune()
+    walk = "velocity-field-direct" if v is not None else VARIANT_NAMES[sim.info.variant]
     pairs = sim.count_pairs()
     launches = ade.launches_per_step(sim.ctx)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
@@ -785,7 +801,7 @@ def run_ours(args):
         kname = "k_rate_field (predictor + corrector)"
     achieved = pairs / (rate_avg_ms * 1e-3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
-                "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(args.workload),
+                "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get((args.workload, walk)),
                 "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "kernel": kname,
                 "peak_basis": basis,
@@ -842,9 +858,7 @@ def run_ours(args):
                              "times from ade_step_timed"},
         "grid": {"cell_subdiv": sim.info.cell_subdiv, "cells": sim.info.ncells,
                  "stencil_rows": sim.info.stencil_rows, "sort_passes": sim.info.sort_passes,
-                 "variant": ("velocity-field-direct" if v is not None else
-                             {0: "direct-branch-free", 1: "tiled", 2: "direct-branched", 3: "direct-branch-free-trimmed",
-                              4: "direct-branched-trimmed"}[sim.info.variant]),
+                 "variant": walk,
                  "autotune_best_ms": tune_ms, "dt": sim.info.dt, "skin": sim.info.skin},
         "steps_per_s": 1e3 / ms_per_step * world,
         "interactions_per_step": 2 * pairs,
@@ -878,6 +892,10 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=131072)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant", choices=("auto",) + tuple(VARIANT_FLAGS), default="auto",
+                    help="interaction walk of the single-plume workloads (default: autotuned)")
+    ap.add_argument("--cell-subdiv", type=int, default=0,
+                    help="cells per support radius with --variant (0: the library's choice)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)       # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -331,8 +331,8 @@ def test_run_stats_are_the_folded_corrector_partials(lib, variant, side):
 
 
 def test_run_stats_fold_capped_block_count(lib):
-    """4.41 M particles (137,813 warp partials): the fold uses its maximum of 128 blocks, so each
-    block folds more than one pass of its threads."""
+    """4.41 M particles (137,813 warp partials): the fold uses its maximum of 8 CTAs, so each
+    thread folds several passes of eight partials."""
     plume = _plume(side=2100, h_dx=1.3, jitter=0.2, seed=4)
     sim = _sim(lib, plume)
     st = sim.run(1)
