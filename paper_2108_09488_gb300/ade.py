@@ -26,6 +26,7 @@ FLAG_DIRECT = 1
 FLAG_TILED = 2
 FLAG_BRANCHED = 4
 FLAG_TRIMMED = 8
+FLAG_PAIRED = 16
 DT_LAMBDA_MAX = 0
 DT_TRACE = 1
 

@@ -67,7 +67,8 @@ struct RateParams {
     uint32_t inc[3]; // fixed-point position increment used by the epilogue
     uint32_t back[3];// evaluation position minus cell-build position (0, or the half-step drift)
     int variant;     // 0 = direct walk (branch-free), 1 = shared-memory tiles, 2 = direct walk
-                     // branching on the support test, 3 / 4 = 0 / 2 with per-particle trimmed rows
+                     // branching on the support test, 3 / 4 = 0 / 2 with per-particle trimmed rows,
+                     // 5 / 6 = 0 / 3 with two targets per thread (packed FP32x2)
     int k;           // halo width in cells (cells per support radius)
     int tx, ty, tz;  // target cells per tile
     int ntx, nty, ntz;  // tiles per axis

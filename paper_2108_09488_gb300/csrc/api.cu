@@ -120,13 +120,17 @@ int time_step(const ade_params *p, const double *D, double *dt_out)
 }
 
 // Neighbour-cell stencil for cells of side s[] and support H: every row (dy, dz) whose cells can
-// hold a point within H of a point in the centre cell, with the x half-width w of that row.
-// Two cells offset by o are at least sum_i (max(|o_i| - 1, 0) s_i)^2 apart (squared).
+// hold a point within H (1 + 2^-12) of a point in the centre cell, with the x half-width w of that
+// row.  Two cells offset by o are at least sum_i (max(|o_i| - 1, 0) s_i)^2 apart (squared).  The
+// margin puts every particle of a cell outside a row beyond H by far more than the FP32 rounding
+// of a pair's distance, so a walk that visits such a particle (the paired walk does) adds an
+// exactly zero term.
 int build_rows(int dim, int k, const double *s, double H, ade::StencilRow *rows)
 {
     int nr = 0;
     const int kz = dim == 3 ? k : 0;
-    const double H2 = H * H;
+    const double Hm = H * (1.0 + 1.0 / 4096.0);
+    const double H2 = Hm * Hm;
     for (int dz = -kz; dz <= kz; ++dz)
         for (int dy = -k; dy <= k; ++dy) {
             double ey = fmax(fabs((double)dy) - 1.0, 0.0) * s[1];
@@ -230,9 +234,11 @@ int validate(const ade_params *p, int n)
     if (!isfinite(p->dt) || !isfinite(p->gamma)) return fail(ADE_ERR_ARG, "dt and gamma must be finite");
     if (p->dt_rule != ADE_DT_LAMBDA_MAX && p->dt_rule != ADE_DT_TRACE) return fail(ADE_ERR_ARG, "unknown dt_rule");
     if (p->cell_subdiv < 0 || p->cell_subdiv > ade::kMaxSubdiv) return fail(ADE_ERR_ARG, "cell_subdiv must be 0..6");
+    const unsigned pf = p->flags & ~(ADE_FLAG_DIRECT | ADE_FLAG_TRIMMED);
     if (p->flags != 0u && p->flags != ADE_FLAG_DIRECT && p->flags != ADE_FLAG_TILED &&
         p->flags != ADE_FLAG_BRANCHED && p->flags != ADE_FLAG_TRIMMED &&
-        p->flags != (ADE_FLAG_TRIMMED | ADE_FLAG_DIRECT) && p->flags != (ADE_FLAG_TRIMMED | ADE_FLAG_BRANCHED))
+        p->flags != (ADE_FLAG_TRIMMED | ADE_FLAG_DIRECT) && p->flags != (ADE_FLAG_TRIMMED | ADE_FLAG_BRANCHED) &&
+        pf != ADE_FLAG_PAIRED)
         return fail(ADE_ERR_ARG, "unknown or conflicting flags");
     if (!(p->vmax >= 0.0) || !isfinite(p->vmax)) return fail(ADE_ERR_ARG, "vmax must be finite and >= 0");
     if (p->vmax > 0.0 && p->flags != 0u && p->flags != ADE_FLAG_DIRECT)
@@ -625,6 +631,7 @@ int plume_constants(const ade_params *p, int n, const Derived &d, double *D, dou
     rp.pf = (float)(0.5 * (p->mass / p->rho) * kernel_kc(p->kernel, dm, d.H));
     rp.variant = d.tiles.variant == 1 ? 1 : ((p->flags & ADE_FLAG_BRANCHED) ? 2 : 0);
     if (rp.variant != 1 && (p->flags & ADE_FLAG_TRIMMED)) rp.variant = rp.variant == 2 ? 4 : 3;  // trimmed rows
+    if (p->flags & ADE_FLAG_PAIRED) rp.variant = (p->flags & ADE_FLAG_TRIMMED) ? 6 : 5;       // paired walk
     rp.k = d.tiles.k;
     rp.tx = d.tiles.tx;
     rp.ty = d.tiles.ty;
@@ -828,7 +835,7 @@ int ade_autotune(ade_ctx *c, double *best_ms_host, void *stream)
     int best_variant = c->rp.variant;
     int rc = ADE_OK;
     for (int k = 1; rc == ADE_OK && k <= ade::kMaxSubdiv; ++k)
-        for (int variant = 0; variant < 5; ++variant) {
+        for (int variant = 0; variant < 7; ++variant) {
             if (c->field && variant != 0) continue;  // one interaction kernel in velocity-field mode
             if (apply_config(c, k, variant) != ADE_OK) continue;
             double ms = 1e30;

@@ -204,6 +204,176 @@ __device__ float rate_direct(const uint4 *__restrict__ Pe, const uint32_t *__res
 }
 
 // ---------------------------------------------------------------------------------------------
+// paired direct walk: two targets per thread, packed FP32x2 arithmetic
+// ---------------------------------------------------------------------------------------------
+// Two cell-sorted particles a0, a1 of the same cell row (cx1 - cx0 <= 1) walk one candidate stream:
+// per stencil row the union of their cell ranges.  Every candidate is loaded once and both terms
+// are evaluated with the packed FP32x2 instructions of this architecture (one instruction, two
+// independent IEEE results), each half with exactly the operations of pair_range_direct<BF>.  A
+// candidate outside one target's own range lies beyond H (1 + 2^-12) of it -- the stencil rows and
+// the trimmed ranges are built for that radius -- so its branch-free term is exactly 0 and each
+// target's row sum is bitwise that of the one-target walk (same candidates, same order).
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+template <int KERNEL>
+__device__ __forceinline__ float2 shape2(float2 omq)
+{
+    if (KERNEL == ADE_WENDLAND_C2) return __fmul2_rn(__fmul2_rn(omq, omq), omq);
+    const float2 o2 = __fmul2_rn(omq, omq);
+    const float2 t = __ffma2_rn(f2(-5.f, -5.f), omq, f2(6.f, 6.f));
+    return __fmul2_rn(__fmul2_rn(__fmul2_rn(o2, o2), omq), t);
+}
+
+// Packed per-pair constants (both halves equal).
+struct PairConst2 {
+    float2 K0, K1, K3, K4, K5, c0, ninvH, sy, sz;
+    __device__ __forceinline__ explicit PairConst2(const PairConst &k)
+        : K0(f2(k.K0, k.K0)), K1(f2(k.K1, k.K1)), K3(f2(k.K3, k.K3)), K4(f2(k.K4, k.K4)),
+          K5(f2(k.K5, k.K5)), c0(f2(k.c0, k.c0)), ninvH(f2(-k.invH, -k.invH)), sy(f2(k.sy, k.sy)),
+          sz(f2(k.sz, k.sz))
+    {
+    }
+};
+
+template <int DIM, int KERNEL, bool ISO>
+__device__ __forceinline__ void pair_range_direct2(const uint4 *__restrict__ P, int j0, int j1,
+                                                   const uint4 &pa0, const uint4 &pa1, float2 Ca,
+                                                   const PairConst2 &k, float2 &rs)
+{
+#pragma unroll 4
+    for (int j = j0; j < j1; ++j) {
+        const uint4 pb = __ldg(P + j);
+        float2 dx = f2((float)(int)(pa0.x - pb.x), (float)(int)(pa1.x - pb.x));
+        float2 dy = f2((float)(int)(pa0.y - pb.y), (float)(int)(pa1.y - pb.y));
+        float2 dz = f2(0.f, 0.f);
+        if (DIM == 3) dz = f2((float)(int)(pa0.z - pb.z), (float)(int)(pa1.z - pb.z));
+        if (!ISO) {
+            dy = __fmul2_rn(dy, k.sy);
+            if (DIM == 3) dz = __fmul2_rn(dz, k.sz);
+        }
+        float2 r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+        if (DIM == 3) r2 = __ffma2_rn(dz, dz, r2);
+        const float2 rinv = f2(rsqrtf(r2.x), rsqrtf(r2.y));
+        const float2 om = __ffma2_rn(__fmul2_rn(r2, rinv), k.ninvH, f2(1.f, 1.f));
+        const float2 omq = f2(fmaxf(om.x, 0.f), fmaxf(om.y, 0.f));
+        float2 Q;
+        if (DIM == 2) {
+            Q = __fmul2_rn(dx, __ffma2_rn(k.K0, dx, __fmul2_rn(k.K3, dy)));
+        } else {
+            const float2 qx = __ffma2_rn(k.K0, dx, __ffma2_rn(k.K3, dy, __fmul2_rn(k.K4, dz)));
+            const float2 qy = __ffma2_rn(k.K1, dy, __fmul2_rn(k.K5, dz));
+            Q = __ffma2_rn(dx, qx, __fmul2_rn(dy, qy));
+        }
+        const float2 sr = __ffma2_rn(Q, __fmul2_rn(rinv, rinv), k.c0);
+        const float2 sc = f2(fmaxf(sr.x, -3.402823466e38f), fmaxf(sr.y, -3.402823466e38f));
+        const float nCb = -__uint_as_float(pb.w);
+        rs = __ffma2_rn(__fmul2_rn(shape2<KERNEL>(omq), sc), __fadd2_rn(Ca, f2(nCb, nCb)), rs);
+    }
+}
+
+// Eq. 4 at two particles of the same cell row by the paired walk; (cx0, cx1, cy, cz) their cells.
+template <int DIM, int KERNEL, bool ISO, bool TRIM>
+__device__ void rate_direct_pair(const uint4 *__restrict__ Pe, const uint32_t *__restrict__ cs,
+                                 const uint4 &pa0, const uint4 &pa1, int cx0, int cx1, int cy, int cz,
+                                 const RateParams &prm, float &r0, float &r1)
+{
+    const int ncx = prm.ncx, ncy = prm.ncy, ncz = prm.ncz, nrows = prm.nrows;
+    const PairConst kc(prm);
+    const PairConst2 k2(kc);
+    const float2 Ca = f2(__uint_as_float(pa0.w), __uint_as_float(pa1.w));
+    float acc0 = 0.f, comp0 = 0.f, acc1 = 0.f, comp1 = 0.f;
+    // the trimming of rate_direct, per target
+    const float two32 = 4294967296.f;
+    const float fx0 = (float)((pa0.x - prm.back[0]) * (uint32_t)ncx) * (1.f / two32);
+    const float fx1 = (float)((pa1.x - prm.back[0]) * (uint32_t)ncx) * (1.f / two32);
+    const float fy0 = (float)((pa0.y - prm.back[1]) * (uint32_t)ncy) * (1.f / two32);
+    const float fy1 = (float)((pa1.y - prm.back[1]) * (uint32_t)ncy) * (1.f / two32);
+    const float fz0 = DIM == 3 ? (float)((pa0.z - prm.back[2]) * (uint32_t)ncz) * (1.f / two32) : 0.f;
+    const float fz1 = DIM == 3 ? (float)((pa1.z - prm.back[2]) * (uint32_t)ncz) * (1.f / two32) : 0.f;
+    const float inv_wx = (float)ncx * (1.f / two32);
+    const float chy = two32 / (float)ncy * kc.sy, chz = DIM == 3 ? two32 / (float)ncz * kc.sz : 0.f;
+    const float Hm2 = kc.H2 * (1.f + 1.f / 2048.f);
+    for (int ri = 0; ri < nrows; ++ri) {
+        const StencilRow row = prm.rows[ri];
+        int lo0 = cx0 - (int)row.w, hi0 = cx0 + row.w, lo1 = cx1 - (int)row.w, hi1 = cx1 + row.w;
+        bool in0 = true, in1 = true;       // the target reaches the row (rate_direct does not skip it)
+        bool ne0 = true, ne1 = true;       // ... and its cell range is not empty
+        if (TRIM) {
+            float e0 = fmaxf(fmaxf((float)row.dy - fy0, fy0 - (float)(row.dy + 1)), 0.f) * chy;
+            float e1 = fmaxf(fmaxf((float)row.dy - fy1, fy1 - (float)(row.dy + 1)), 0.f) * chy;
+            e0 *= e0;
+            e1 *= e1;
+            if (DIM == 3) {
+                const float z0 = fmaxf(fmaxf((float)row.dz - fz0, fz0 - (float)(row.dz + 1)), 0.f) * chz;
+                const float z1 = fmaxf(fmaxf((float)row.dz - fz1, fz1 - (float)(row.dz + 1)), 0.f) * chz;
+                e0 = fmaf(z0, z0, e0);
+                e1 = fmaf(z1, z1, e1);
+            }
+            in0 = e0 < Hm2;
+            in1 = e1 < Hm2;
+            const float t0 = in0 ? Hm2 - e0 : 1.f, t1 = in1 ? Hm2 - e1 : 1.f;
+            const float xe0 = t0 * rsqrtf(t0) * inv_wx + 1.f / 4096.f;
+            const float xe1 = t1 * rsqrtf(t1) * inv_wx + 1.f / 4096.f;
+            lo0 = cx0 + max(__float2int_rd(fx0 - xe0), -(int)row.w);
+            hi0 = cx0 + min(__float2int_rd(fx0 + xe0), (int)row.w);
+            lo1 = cx1 + max(__float2int_rd(fx1 - xe1), -(int)row.w);
+            hi1 = cx1 + min(__float2int_rd(fx1 + xe1), (int)row.w);
+            ne0 = in0 && lo0 <= hi0;
+            ne1 = in1 && lo1 <= hi1;
+        }
+        int lo, hi;
+        if (ne0 && ne1) {
+            lo = min(lo0, lo1);
+            hi = max(hi0, hi1) + 1;
+        } else if (ne0) {
+            lo = lo0;
+            hi = hi0 + 1;
+        } else if (ne1) {
+            lo = lo1;
+            hi = hi1 + 1;
+        } else {
+            // no candidate for either target; a reached row still adds its (zero) row sum
+            if (in0) neumaier_add(acc0, comp0, 0.f);
+            if (in1) neumaier_add(acc1, comp1, 0.f);
+            continue;
+        }
+        int yy = cy + row.dy;
+        yy += (yy < 0) ? ncy : 0;
+        yy -= (yy >= ncy) ? ncy : 0;
+        int zz = 0;
+        if (DIM == 3) {
+            zz = cz + row.dz;
+            zz += (zz < 0) ? ncz : 0;
+            zz -= (zz >= ncz) ? ncz : 0;
+        }
+        const int base = (zz * ncy + yy) * ncx;
+        int s0, e0, s1 = 0, e1 = 0;
+        if (lo < 0) {
+            s0 = __ldg(cs + base + lo + ncx);
+            e0 = __ldg(cs + base + ncx);
+            s1 = __ldg(cs + base);
+            e1 = __ldg(cs + base + hi);
+        } else if (hi > ncx) {
+            s0 = __ldg(cs + base + lo);
+            e0 = __ldg(cs + base + ncx);
+            s1 = __ldg(cs + base);
+            e1 = __ldg(cs + base + hi - ncx);
+        } else {
+            s0 = __ldg(cs + base + lo);
+            e0 = __ldg(cs + base + hi);
+        }
+        float2 rs = f2(0.f, 0.f);
+        pair_range_direct2<DIM, KERNEL, ISO>(Pe, s0, e0, pa0, pa1, Ca, k2, rs);
+        pair_range_direct2<DIM, KERNEL, ISO>(Pe, s1, e1, pa0, pa1, Ca, k2, rs);
+        // a target that does not reach the row (trimmed walk) skips it, as rate_direct does
+        if (in0) neumaier_add(acc0, comp0, rs.x);
+        if (in1) neumaier_add(acc1, comp1, rs.y);
+    }
+    r0 = prm.pf * (acc0 + comp0);
+    r1 = prm.pf * (acc1 + comp1);
+}
+
+// ---------------------------------------------------------------------------------------------
 // epilogue and block reductions
 // ---------------------------------------------------------------------------------------------
 // Writes of one particle at sorted position gi; pe = evaluation state {x, y, z, C}.
@@ -302,6 +472,47 @@ __global__ __launch_bounds__(kRateThreads) void k_rate(const uint4 *__restrict__
         epilogue<DIM, EPI, PRE>(i, rate, pa, perm, prm, out, acc, a_pre, C_pre);
     }
     warp_finish<EPI, COUNT, kRateThreads>(acc, out);
+}
+
+// Paired kernel: thread t evaluates sorted particles 2t and 2t + 1.  Pairs that are not in the
+// same cell row, or more than one cell apart, or whose union of ranges could wrap onto itself
+// (fewer than 2k + 2 cells along x), take the one-target walk for each particle.  The full-row
+// walk is held to 10 resident CTAs per SM (<= 48 registers), which measured faster on the 1024^2
+// ladder; the trimmed walk measured faster without the limit.
+template <int DIM, int KERNEL, int EPI, bool ISO, bool TRIM>
+__global__ __launch_bounds__(kRateThreads, TRIM ? 0 : 10) void k_rate_pair(const uint4 *__restrict__ Pe,
+                                                            const uint4 *__restrict__ Pc,
+                                                            const uint32_t *__restrict__ cs,
+                                                            const uint32_t *__restrict__ perm,
+                                                            const RateParams prm, const EpiOut out)
+{
+    pdl_wait();
+    pdl_trigger();
+    const int t = blockIdx.x * kRateThreads + threadIdx.x;
+    const int i0 = 2 * t, i1 = 2 * t + 1;
+    const bool v0 = i0 < prm.n, v1 = i1 < prm.n;
+    const int ii0 = v0 ? i0 : prm.n - 1, ii1 = v1 ? i1 : ii0;
+    const uint4 pa0 = __ldg(Pe + ii0);
+    const uint4 pa1 = __ldg(Pe + ii1);
+    const int cx0 = (int)__umulhi(pa0.x - prm.back[0], (uint32_t)prm.ncx);
+    const int cy0 = (int)__umulhi(pa0.y - prm.back[1], (uint32_t)prm.ncy);
+    const int cz0 = DIM == 3 ? (int)__umulhi(pa0.z - prm.back[2], (uint32_t)prm.ncz) : 0;
+    const int cx1 = (int)__umulhi(pa1.x - prm.back[0], (uint32_t)prm.ncx);
+    const int cy1 = (int)__umulhi(pa1.y - prm.back[1], (uint32_t)prm.ncy);
+    const int cz1 = DIM == 3 ? (int)__umulhi(pa1.z - prm.back[2], (uint32_t)prm.ncz) : 0;
+    Acc acc{0.f, 0.f, __int_as_float(0x7f800000), __int_as_float(0xff800000), 0u};
+    unsigned cnt = 0u;
+    float r0, r1;
+    const bool paired = v1 && cy0 == cy1 && cz0 == cz1 && cx1 - cx0 <= 1 && prm.ncx >= 2 * prm.k + 2;
+    if (paired) {
+        rate_direct_pair<DIM, KERNEL, ISO, TRIM>(Pe, cs, pa0, pa1, cx0, cx1, cy0, cz0, prm, r0, r1);
+    } else {
+        r0 = rate_direct<DIM, KERNEL, ISO, false, true, TRIM>(Pe, cs, pa0, cx0, cy0, cz0, prm, cnt);
+        r1 = v1 ? rate_direct<DIM, KERNEL, ISO, false, true, TRIM>(Pe, cs, pa1, cx1, cy1, cz1, prm, cnt) : 0.f;
+    }
+    if (v0) epilogue<DIM, EPI>(i0, r0, pa0, perm, prm, out, acc);
+    if (v1) epilogue<DIM, EPI>(i1, r1, pa1, perm, prm, out, acc);
+    warp_finish<EPI, false, kRateThreads>(acc, out);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -579,6 +790,16 @@ cudaError_t launch_variant(bool iso, const uint4 *Pe, const uint4 *Pc, const uin
         if (e != cudaSuccess) return e;
         return launch_pdl(fn, blocks, kTileThreads, smem, s, Pe, Pc, cs, perm, prm, out);
     }
+    if ((prm.variant == 5 || prm.variant == 6) && !COUNT) {
+        // 5, 6: paired branch-free walk (6: trimmed rows, square or cubic boxes); the pair counter
+        // takes the one-target walk
+        const int pblocks = rate_blocks((prm.n + 1) / 2);
+        if (iso && prm.variant == 6)
+            return launch_pdl(k_rate_pair<DIM, KERNEL, EPI, true, true>, pblocks, kRateThreads, 0, s, Pe, Pc, cs, perm, prm, out);
+        if (iso)
+            return launch_pdl(k_rate_pair<DIM, KERNEL, EPI, true, false>, pblocks, kRateThreads, 0, s, Pe, Pc, cs, perm, prm, out);
+        return launch_pdl(k_rate_pair<DIM, KERNEL, EPI, false, false>, pblocks, kRateThreads, 0, s, Pe, Pc, cs, perm, prm, out);
+    }
     const int blocks = rate_blocks(prm.n);
     const bool bf = prm.variant != 2 && prm.variant != 4;   // 2, 4: branched direct walk
     // 3, 4: trimmed rows (square or cubic boxes; the pair count is the same either way)
@@ -630,13 +851,14 @@ int rate_blocks(int n) { return (n + kRateThreads - 1) / kRateThreads; }
 int rate_launch_blocks(int dim, const RateParams &prm, bool iso)
 {
     if (prm.variant == 1 && iso) return prm.ntx * prm.nty * (dim == 3 ? prm.ntz : 1);
+    if (prm.variant == 5 || prm.variant == 6) return rate_blocks((prm.n + 1) / 2);
     return rate_blocks(prm.n);
 }
 
 int rate_launch_warps(int dim, const RateParams &prm, bool iso)
 {
     if (prm.variant == 1 && iso) return rate_launch_blocks(dim, prm, iso) * (kTileThreads / 32);
-    return rate_blocks(prm.n) * (kRateThreads / 32);
+    return rate_launch_blocks(dim, prm, iso) * (kRateThreads / 32);
 }
 
 size_t tiled_smem_bytes(int dim, const RateParams &prm)

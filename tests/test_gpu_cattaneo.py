@@ -12,7 +12,7 @@ from paper_2108_09488_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 RATE_TOL = 1e-5
-VARIANTS = {"direct": 1, "tiled": 2, "branched": 4}
+VARIANTS = {"direct": 1, "tiled": 2, "branched": 4, "paired": 17}
 
 
 @pytest.fixture(scope="module")

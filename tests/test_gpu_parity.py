@@ -97,8 +97,10 @@ def test_cells_bit_exact_every_subdivision(lib, orc, k):
     assert np.array_equal(perm, perm_o) and np.array_equal(cs, cs_o)
 
 
-# ADE_FLAG_TILED, _DIRECT, _BRANCHED, and the two direct walks with _TRIMMED rows
-VARIANTS = {"tiled": 2, "direct": 1, "branched": 4, "direct-trimmed": 9, "branched-trimmed": 12}
+# ADE_FLAG_TILED, _DIRECT, _BRANCHED, the two direct walks with _TRIMMED rows, and the _PAIRED
+# branch-free walk (full and trimmed rows)
+VARIANTS = {"tiled": 2, "direct": 1, "branched": 4, "direct-trimmed": 9, "branched-trimmed": 12,
+            "paired": 17, "paired-trimmed": 25}
 
 
 @pytest.mark.parametrize("variant", sorted(VARIANTS))
@@ -111,6 +113,8 @@ def test_rate_parity(lib, orc, name, variant):
         assert sim.info.variant == 0
     if variant == "branched":
         assert sim.info.variant == 2
+    if variant.startswith("paired"):
+        assert sim.info.variant == (6 if variant.endswith("trimmed") else 5)
     r_gpu = sim.rate().cpu().numpy()
     r_orc, pairs = _oracle_rate(orc, plume, xq, C)
     assert _rel(r_gpu, r_orc) <= RATE_TOL
@@ -126,7 +130,7 @@ def test_tiled_variant_is_used_and_deterministic(lib):
     assert np.array_equal(r1.view(np.uint32), r2.view(np.uint32))
 
 
-@pytest.mark.parametrize("name", ["256sq-n28-r100", "jitter-100sq", "c4-96sq"])
+@pytest.mark.parametrize("name", ["256sq-n28-r100", "jitter-100sq", "c4-96sq", "3d-jitter-24"])
 def test_trimmed_direct_walk_equals_full_stencil_bitwise(lib, name):
     """With trimmed rows the direct walks visit, per particle, only the stencil cells within
     (1 + 2^-12) H of the particle; without, and in the shared-memory tiled walk, every cell of the
@@ -149,10 +153,57 @@ def test_trimmed_direct_walk_equals_full_stencil_bitwise(lib, name):
         bt = _sim(lib, plume, xq, C, cell_subdiv=k, flags=lib.FLAG_BRANCHED | lib.FLAG_TRIMMED)
         assert bt.info.variant == 4
         assert np.array_equal(b.rate().cpu().numpy().view(np.uint32), bt.rate().cpu().numpy().view(np.uint32))
-        # one step with trimmed rows equals one with the full stencil
+        # the paired walks (two targets per thread over the union of their ranges) add only
+        # exact zeros to each target's sums
+        pf = _sim(lib, plume, xq, C, cell_subdiv=k, flags=lib.FLAG_PAIRED)
+        pt = _sim(lib, plume, xq, C, cell_subdiv=k, flags=lib.FLAG_PAIRED | lib.FLAG_TRIMMED)
+        assert pf.info.variant == 5 and pt.info.variant == 6
+        assert np.array_equal(pf.rate().cpu().numpy().view(np.uint32), rf.view(np.uint32)), k
+        assert np.array_equal(pt.rate().cpu().numpy().view(np.uint32), rf.view(np.uint32)), k
+        # one step with trimmed rows, or paired, equals one with the full stencil
         f.step(1)
         d.step(1)
+        pf.step(1)
+        pt.step(1)
         assert np.array_equal(f.state()[1].view(np.uint32), d.state()[1].view(np.uint32))
+        assert np.array_equal(f.state()[1].view(np.uint32), pf.state()[1].view(np.uint32))
+        assert np.array_equal(f.state()[1].view(np.uint32), pt.state()[1].view(np.uint32))
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_paired_walk_clustered_odd_count_bitwise(lib, orc, k):
+    """A dense cluster on a lattice with an odd particle count: the paired walk meets pairs in
+    different cell rows or several cells apart (each target then walks alone) and a last thread
+    with one target; every rate and a step equal the one-target walk bit for bit, and the oracle."""
+    rng = np.random.default_rng(10 + k)
+    base = inputs.lattice_positions(2, 97)
+    blob = np.mod(rng.normal(0.3, 0.03, size=(3000, 2)), 1.0)
+    x = np.concatenate([base, blob])
+    n = x.shape[0]
+    assert n % 2 == 1
+    box = np.ones(2)
+    xq = inputs.to_fixed(x, box)
+    xo = inputs.from_fixed(xq, box)
+    C = inputs.gaussian_plume(xo, box, (0.35, 0.4), 0.1).astype(np.float32)
+    plume = _plume(side=97, h_dx=2.0)
+
+    def sim(flags):
+        p = lib.params(2, plume.h, plume.alpha_L, plume.alpha_T, plume.D_m, plume.velocity, mass=1.0 / n,
+                       flags=flags, cell_subdiv=k)
+        return lib.Simulation(p, xq, C)
+
+    one, two, two_t = sim(lib.FLAG_DIRECT), sim(lib.FLAG_PAIRED), sim(lib.FLAG_PAIRED | lib.FLAG_TRIMMED)
+    r1 = one.rate().cpu().numpy()
+    assert np.array_equal(r1.view(np.uint32), two.rate().cpu().numpy().view(np.uint32))
+    assert np.array_equal(r1.view(np.uint32), two_t.rate().cpu().numpy().view(np.uint32))
+    r_orc, _ = orc.rate(xo, plume.velocity, C.astype(np.float64), 1.0 / n, 1.0, box, 0,
+                        plume.support, 4.0, plume.alpha_L, plume.alpha_T, plume.D_m)
+    assert _rel(r1, r_orc) <= RATE_TOL
+    for s_ in (one, two, two_t):
+        s_.step(2)
+    for s_ in (two, two_t):
+        assert np.array_equal(one.state()[1].view(np.uint32), s_.state()[1].view(np.uint32))
+        assert np.array_equal(one.state()[0], s_.state()[0])
 
 
 def test_rate_parity_clustered_overflow(lib, orc):

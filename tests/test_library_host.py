@@ -164,8 +164,30 @@ def test_velocity_field_mode_time_step_skin_and_grid(adelib, orc, rule):
         adelib.destroy(ctx)
 
 
+@pytest.mark.parametrize("flags,variant", [(16, 5), (17, 5), (24, 6), (25, 6)])
+def test_paired_walk_flags(adelib, flags, variant):
+    """ADE_FLAG_PAIRED alone or with DIRECT selects the paired branch-free walk (5), with TRIMMED
+    its trimmed form (6)."""
+    plume = inputs.ladder_2d(256, 10)
+    ctx, _ = _ctx(adelib, adelib.params_for(plume, flags=flags), plume.n)
+    try:
+        assert adelib.get_info(ctx).variant == variant
+    finally:
+        adelib.destroy(ctx)
+
+
+@pytest.mark.parametrize("flags", [16 | 2, 16 | 4, 16 | 4 | 8, 32])
+def test_paired_walk_conflicting_flags(adelib, flags):
+    """PAIRED with the tiled or branched walks, and unknown bits, are rejected."""
+    plume = inputs.ladder_2d(256, 10)
+    with pytest.raises(adelib.AdeError) as e:
+        adelib.workspace_bytes(adelib.params_for(plume, flags=flags), plume.n)
+    assert e.value.code == -1
+
+
 @pytest.mark.parametrize("bad", [dict(vmax=-1.0), dict(vmax=float("inf")), dict(vmax=0.2, flags=2),
-                                 dict(vmax=0.2, flags=4), dict(vmax=0.2, dt=3.0)])
+                                 dict(vmax=0.2, flags=4), dict(vmax=0.2, flags=16),
+                                 dict(vmax=0.2, dt=3.0)])
 def test_velocity_field_mode_invalid(adelib, bad):
     """Negative or infinite vmax, the tiled or branched kernels, and a skin so wide that the grid
     cannot hold the stencil are rejected before any device work."""
