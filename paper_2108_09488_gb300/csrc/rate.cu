@@ -90,7 +90,10 @@ __device__ __forceinline__ float dcal(float dx, float dy, float dz, float rinv2,
 // terms leaves the sum unchanged.  The pair counter keeps an explicit FP64 test.
 // BF = false keeps the branch on r^2 < H^2 instead: a warp whose lanes all miss skips the term,
 // which pays off when warps are spatially coherent and the stencil is large (3D).
-template <int DIM, int KERNEL, bool ISO, bool COUNT, bool BF>
+// ZS = false drops the clamp of s: zero separation occurs only within the particle's own cell, so
+// rows other than the particle's own cell row (dy = dz = 0) never meet it, s is finite there and
+// the clamp changes nothing.
+template <int DIM, int KERNEL, bool ISO, bool COUNT, bool BF, bool ZS = true>
 __device__ __forceinline__ void pair_range_direct(const uint4 *__restrict__ P, int j0, int j1,
                                                   const uint4 &pa, float Ca, const PairConst &k,
                                                   const RateParams &prm, float &rs, unsigned &cnt)
@@ -112,7 +115,8 @@ __device__ __forceinline__ void pair_range_direct(const uint4 *__restrict__ P, i
         if (BF) {
             const float rinv = rsqrtf(r2);
             const float omq = fmaxf(fmaf(-(r2 * rinv), k.invH, 1.f), 0.f);
-            const float s = fmaxf(dcal<DIM>(dx, dy, dz, rinv * rinv, k), -3.402823466e38f);
+            const float sr = dcal<DIM>(dx, dy, dz, rinv * rinv, k);
+            const float s = ZS ? fmaxf(sr, -3.402823466e38f) : sr;
             rs = fmaf(shape<KERNEL>(omq) * s, Ca - __uint_as_float(pb.w), rs);
         } else if (r2 < k.H2 && r2 > 0.f) {
             const float rinv = rsqrtf(r2);
@@ -196,8 +200,13 @@ __device__ float rate_direct(const uint4 *__restrict__ Pe, const uint32_t *__res
             e0 = __ldg(cs + base + hi);
         }
         float rs = 0.f;
-        pair_range_direct<DIM, KERNEL, ISO, COUNT, BF>(Pe, s0, e0, pa, Ca, kc, prm, rs, cnt);
-        pair_range_direct<DIM, KERNEL, ISO, COUNT, BF>(Pe, s1, e1, pa, Ca, kc, prm, rs, cnt);
+        if (row.dy == 0 && (DIM == 2 || row.dz == 0)) {      // the particle's own cell row
+            pair_range_direct<DIM, KERNEL, ISO, COUNT, BF, true>(Pe, s0, e0, pa, Ca, kc, prm, rs, cnt);
+            pair_range_direct<DIM, KERNEL, ISO, COUNT, BF, true>(Pe, s1, e1, pa, Ca, kc, prm, rs, cnt);
+        } else {
+            pair_range_direct<DIM, KERNEL, ISO, COUNT, BF, false>(Pe, s0, e0, pa, Ca, kc, prm, rs, cnt);
+            pair_range_direct<DIM, KERNEL, ISO, COUNT, BF, false>(Pe, s1, e1, pa, Ca, kc, prm, rs, cnt);
+        }
         neumaier_add(acc, comp, rs);
     }
     return prm.pf * (acc + comp);
@@ -235,7 +244,7 @@ struct PairConst2 {
     }
 };
 
-template <int DIM, int KERNEL, bool ISO>
+template <int DIM, int KERNEL, bool ISO, bool ZS>
 __device__ __forceinline__ void pair_range_direct2(const uint4 *__restrict__ P, int j0, int j1,
                                                    const uint4 &pa0, const uint4 &pa1, float2 Ca,
                                                    const PairConst2 &k, float2 &rs)
@@ -265,7 +274,7 @@ __device__ __forceinline__ void pair_range_direct2(const uint4 *__restrict__ P, 
             Q = __ffma2_rn(dx, qx, __fmul2_rn(dy, qy));
         }
         const float2 sr = __ffma2_rn(Q, __fmul2_rn(rinv, rinv), k.c0);
-        const float2 sc = f2(fmaxf(sr.x, -3.402823466e38f), fmaxf(sr.y, -3.402823466e38f));
+        const float2 sc = ZS ? f2(fmaxf(sr.x, -3.402823466e38f), fmaxf(sr.y, -3.402823466e38f)) : sr;
         const float nCb = -__uint_as_float(pb.w);
         rs = __ffma2_rn(__fmul2_rn(shape2<KERNEL>(omq), sc), __fadd2_rn(Ca, f2(nCb, nCb)), rs);
     }
@@ -363,8 +372,13 @@ __device__ void rate_direct_pair(const uint4 *__restrict__ Pe, const uint32_t *_
             e0 = __ldg(cs + base + hi);
         }
         float2 rs = f2(0.f, 0.f);
-        pair_range_direct2<DIM, KERNEL, ISO>(Pe, s0, e0, pa0, pa1, Ca, k2, rs);
-        pair_range_direct2<DIM, KERNEL, ISO>(Pe, s1, e1, pa0, pa1, Ca, k2, rs);
+        if (row.dy == 0 && (DIM == 2 || row.dz == 0)) {      // the targets' own cell row
+            pair_range_direct2<DIM, KERNEL, ISO, true>(Pe, s0, e0, pa0, pa1, Ca, k2, rs);
+            pair_range_direct2<DIM, KERNEL, ISO, true>(Pe, s1, e1, pa0, pa1, Ca, k2, rs);
+        } else {
+            pair_range_direct2<DIM, KERNEL, ISO, false>(Pe, s0, e0, pa0, pa1, Ca, k2, rs);
+            pair_range_direct2<DIM, KERNEL, ISO, false>(Pe, s1, e1, pa0, pa1, Ca, k2, rs);
+        }
         // a target that does not reach the row (trimmed walk) skips it, as rate_direct does
         if (in0) neumaier_add(acc0, comp0, rs.x);
         if (in1) neumaier_add(acc1, comp1, rs.y);
