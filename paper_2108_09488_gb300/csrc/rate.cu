@@ -488,9 +488,16 @@ __global__ __launch_bounds__(kRateThreads) void k_rate(const uint4 *__restrict__
     warp_finish<EPI, COUNT, kRateThreads>(acc, out);
 }
 
-// Paired kernel: thread t evaluates sorted particles 2t and 2t + 1.  Pairs that are not in the
-// same cell row, or more than one cell apart, or whose union of ranges could wrap onto itself
-// (fewer than 2k + 2 cells along x), take the one-target walk for each particle.  The full-row
+// Whether sorted particles a0, a1 (cells cx0 <= cx1 in row cy, cz) can share one candidate stream:
+// the same cell row, at most one cell apart, and a grid wide enough that the union of their
+// ranges (<= 2 kMaxSubdiv + 2 cells) never wraps onto itself.
+__device__ __forceinline__ bool can_pair(int cx0, int cy0, int cz0, int cx1, int cy1, int cz1, int ncx)
+{
+    return cy0 == cy1 && cz0 == cz1 && cx1 - cx0 <= 1 && ncx >= 2 * kMaxSubdiv + 2;
+}
+
+// Paired kernel: thread t evaluates sorted particles 2t and 2t + 1; a pair that cannot share a
+// candidate stream (can_pair) takes the one-target walk for each particle.  The full-row
 // walk is held to 10 resident CTAs per SM (<= 48 registers), which measured faster on the 1024^2
 // ladder; the trimmed walk measured faster without the limit.
 template <int DIM, int KERNEL, int EPI, bool ISO, bool TRIM>
@@ -517,7 +524,7 @@ __global__ __launch_bounds__(kRateThreads, TRIM ? 0 : 10) void k_rate_pair(const
     Acc acc{0.f, 0.f, __int_as_float(0x7f800000), __int_as_float(0xff800000), 0u};
     unsigned cnt = 0u;
     float r0, r1;
-    const bool paired = v1 && cy0 == cy1 && cz0 == cz1 && cx1 - cx0 <= 1 && prm.ncx >= 2 * prm.k + 2;
+    const bool paired = v1 && can_pair(cx0, cy0, cz0, cx1, cy1, cz1, prm.ncx);
     if (paired) {
         rate_direct_pair<DIM, KERNEL, ISO, TRIM>(Pe, cs, pa0, pa1, cx0, cx1, cy0, cz0, prm, r0, r1);
     } else {
