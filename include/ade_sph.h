@@ -186,11 +186,13 @@ int ade_closed_form_error(ade_ctx *ctx, const double *x0_host, double w, double 
                           int nimg, double *out_host, void *stream);
 
 /* Autotuner for a context created with cell_subdiv = 0 and flags = 0: times the cell build plus
- * one evaluation of Eq. 4 for every cell subdivision (1..6 cells per support radius) and every
- * interaction variant (branch-free or branched direct walk, each with full or trimmed rows, and
- * shared-memory tiles), keeps the fastest; results change only in summation order (not at all
- * between full and trimmed rows).  The particle state is not modified; waits; best_ms_host may be
- * NULL. */
+ * two evaluations of Eq. 4 (the work of a step) for every cell subdivision (1..6 cells per
+ * support radius) and every interaction variant (branch-free or branched direct walk, each with
+ * full or trimmed rows, the paired branch-free walk with full or trimmed rows, and shared-memory
+ * tiles), then re-times the three fastest in three interleaved rounds and keeps the fastest;
+ * results change only in summation order (not at all between the full, trimmed and paired
+ * walks).  The particle state is not modified; waits; best_ms_host (the time of a build plus two
+ * evaluations) may be NULL. */
 int ade_autotune(ade_ctx *ctx, double *best_ms_host, void *stream);
 
 /* Change alpha_L, alpha_T and D_m (Eq. 3) of a context, keeping its time step, grid and state. */

@@ -831,11 +831,13 @@ int ade_autotune(ade_ctx *c, double *best_ms_host, void *stream)
     ADE_CK(cudaEventCreate(&e0));
     ADE_CK(cudaEventCreate(&e1));
     int rc = ADE_OK;
-    // one timed cell build + rate evaluation of configuration (k, variant); false if it does not fit
+    // one timed cell build + two rate evaluations (the work of a step) of configuration
+    // (k, variant); false if it does not fit
     auto time_once = [&](int k, int variant, double *ms) -> bool {
         if (apply_config(c, k, variant) != ADE_OK) return false;
         cudaError_t e = cudaEventRecord(e0, s);
         if (e == cudaSuccess) rc = enqueue_cells(c, s);
+        if (rc == ADE_OK && e == cudaSuccess) rc = enqueue_eval(c, AT_BUILD, epi_none(), s);
         if (rc == ADE_OK && e == cudaSuccess) rc = enqueue_eval(c, AT_BUILD, epi_none(), s);
         if (rc != ADE_OK) return false;
         if (e == cudaSuccess) e = cudaEventRecord(e1, s);

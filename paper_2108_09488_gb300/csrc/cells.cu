@@ -180,22 +180,69 @@ __global__ __launch_bounds__(kThreads) void k_place(const uint32_t *__restrict__
 constexpr uint32_t kSmallCell = 32;   // cells up to this size are ordered by one thread
 
 // Orders one cell segment [s, e) of perm_tmp by caller index into perm and writes the sorted copy
-// P[k] = rec(perm[k]), for the calling thread's cell when it is small (insertion sort); cells
-// larger than kSmallCell are handled by order_big_cells.
+// P[k] = rec(perm[k]), for the calling thread's cell when it is small; cells larger than
+// kSmallCell are handled by order_big_cells.  The sort runs in registers (a 4-element sorting
+// network, for the cells of up to four particles that dominate fine grids) or in a thread-local
+// array (insertion sort), so the only global traffic is one read of the segment, the record
+// gathers and the writes.
+__device__ __forceinline__ void cswap(uint32_t &a, uint32_t &b)
+{
+    const uint32_t lo = min(a, b), hi = max(a, b);
+    a = lo;
+    b = hi;
+}
+
 template <class Rec>
 __device__ __forceinline__ void order_small_cell(uint32_t s, uint32_t e, const uint32_t *__restrict__ perm_tmp,
                                                  uint32_t *__restrict__ perm, uint4 *__restrict__ P, Rec rec)
 {
-    for (uint32_t k = s; k < e; ++k) {
-        uint32_t v = __ldg(perm_tmp + k);
+    const uint32_t m = e - s;
+    if (m <= 4) {
+        uint32_t v0 = __ldg(perm_tmp + s);
+        uint32_t v1 = m > 1 ? __ldg(perm_tmp + s + 1) : 0xffffffffu;
+        uint32_t v2 = m > 2 ? __ldg(perm_tmp + s + 2) : 0xffffffffu;
+        uint32_t v3 = m > 3 ? __ldg(perm_tmp + s + 3) : 0xffffffffu;
+        cswap(v0, v1);
+        cswap(v2, v3);
+        cswap(v0, v2);
+        cswap(v1, v3);
+        cswap(v1, v2);
+        const uint4 r0 = rec(v0);
+        uint4 r1 = r0, r2 = r0, r3 = r0;
+        if (m > 1) r1 = rec(v1);
+        if (m > 2) r2 = rec(v2);
+        if (m > 3) r3 = rec(v3);
+        perm[s] = v0;
+        P[s] = r0;
+        if (m > 1) {
+            perm[s + 1] = v1;
+            P[s + 1] = r1;
+        }
+        if (m > 2) {
+            perm[s + 2] = v2;
+            P[s + 2] = r2;
+        }
+        if (m > 3) {
+            perm[s + 3] = v3;
+            P[s + 3] = r3;
+        }
+        return;
+    }
+    uint32_t a[kSmallCell];
+    for (uint32_t k = 0; k < m; ++k) a[k] = __ldg(perm_tmp + s + k);
+    for (uint32_t k = 1; k < m; ++k) {
+        const uint32_t v = a[k];
         uint32_t j = k;
-        while (j > s && perm[j - 1] > v) {
-            perm[j] = perm[j - 1];
+        while (j > 0 && a[j - 1] > v) {
+            a[j] = a[j - 1];
             --j;
         }
-        perm[j] = v;
+        a[j] = v;
     }
-    for (uint32_t k = s; k < e; ++k) P[k] = rec(perm[k]);
+    for (uint32_t k = 0; k < m; ++k) {
+        perm[s + k] = a[k];
+        P[s + k] = rec(a[k]);
+    }
 }
 
 // The big cells among the warp's 32 cells, one after another, each ordered by all 32 lanes: every

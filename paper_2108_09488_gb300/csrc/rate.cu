@@ -459,8 +459,7 @@ __global__ __launch_bounds__(kRateThreads) void k_rate(const uint4 *__restrict__
                                                        const uint32_t *__restrict__ perm,
                                                        const RateParams prm, const EpiOut out)
 {
-    pdl_wait();
-    pdl_trigger();
+    pdl_wait();   // no early trigger: see pdl_trigger
     const int i = blockIdx.x * kRateThreads + threadIdx.x;
     const bool valid = i < prm.n;
     const int ii = valid ? i : prm.n - 1;
@@ -507,8 +506,7 @@ __global__ __launch_bounds__(kRateThreads, TRIM ? 0 : 10) void k_rate_pair(const
                                                             const uint32_t *__restrict__ perm,
                                                             const RateParams prm, const EpiOut out)
 {
-    pdl_wait();
-    pdl_trigger();
+    pdl_wait();   // no early trigger: see pdl_trigger
     const int t = blockIdx.x * kRateThreads + threadIdx.x;
     const int i0 = 2 * t, i1 = 2 * t + 1;
     const bool v0 = i0 < prm.n, v1 = i1 < prm.n;
@@ -556,8 +554,7 @@ __global__ __launch_bounds__(kTileThreads, 2) void k_rate_tiled(const uint4 *__r
                                                              const uint32_t *__restrict__ perm,
                                                              const RateParams prm, const EpiOut out)
 {
-    pdl_wait();
-    pdl_trigger();
+    pdl_wait();   // no early trigger: see pdl_trigger
     extern __shared__ float4 smem[];
     __shared__ int s_total;
     __shared__ int wsum[kTileThreads / 32];

@@ -156,8 +156,7 @@ __global__ __launch_bounds__(kT) void k_rate_field(const uint4 *__restrict__ Pe,
                                                    const float4 *__restrict__ DB, const uint4 *__restrict__ Inc,
                                                    const RateParams prm, const FieldParams fp, const EpiOut out)
 {
-    pdl_wait();
-    pdl_trigger();
+    pdl_wait();   // no early trigger: see pdl_trigger
     const int i = blockIdx.x * kT + threadIdx.x;
     const bool valid = i < prm.n;
     const int ii = valid ? i : prm.n - 1;
