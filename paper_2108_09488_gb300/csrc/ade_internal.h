@@ -185,6 +185,8 @@ void pair_coeffs(int dim, double gamma, const double *D, float *Kc, float *c0);
 
 // Launchers (cells.cu, rate.cu, reduce.cu).  All return cudaGetLastError() of the launches.
 int scan_blocks(int m);
+// Kernel launches of one launch_build_cells (the scan of small grids takes two, of large three).
+int cell_build_launches(int n, int ncells);
 // count_zero: w.count[0, ncells) is known to be zero (every build leaves it zero), so the memset
 // that otherwise starts the build is skipped.
 cudaError_t launch_build_cells(int dim, const uint32_t *xq, const float *C, int n, const int *nc,

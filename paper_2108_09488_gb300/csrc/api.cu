@@ -1184,9 +1184,9 @@ int ade_step_timed(ade_ctx *c, double *phase_ms, void *stream)
 int ade_launches_per_step(const ade_ctx *c, int *launches)
 {
     if (!c || !launches) return fail(ADE_ERR_ARG, "NULL argument");
-    // count, 3 scan launches, place, order, [velocity-field gather,] predictor, corrector, fold
-    // of the corrector's partials (the memset is not a kernel)
-    *launches = c->n > 0 ? 9 + (c->field ? 1 : 0) : 4;
+    // the cell build (count, 2 or 3 scan launches, place, order), [velocity-field gather,]
+    // predictor, corrector, fold of the corrector's partials
+    *launches = ade::cell_build_launches(c->n, c->ncells) + (c->n > 0 ? 3 + (c->field ? 1 : 0) : 0);
     return ADE_OK;
 }
 
@@ -2239,8 +2239,9 @@ int ade_sweep_step_timed(ade_sweep *sw, double *phase_ms, void *stream)
 int ade_sweep_launches_per_step(const ade_sweep *sw, int *launches)
 {
     if (!sw || !launches) return fail(ADE_ERR_ARG, "NULL argument");
-    // count, 3 scan launches, place, order, gather; one predictor and one corrector per group
-    *launches = sw->n > 0 ? 7 + 2 * (int)sw->groups.size() : 4;
+    // the cell build (count, 2 or 3 scan launches, place, order), gather; one predictor and one
+    // corrector per group
+    *launches = ade::cell_build_launches(sw->n, sw->ncells) + (sw->n > 0 ? 1 + 2 * (int)sw->groups.size() : 0);
     return ADE_OK;
 }
 

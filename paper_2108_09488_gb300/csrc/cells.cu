@@ -136,6 +136,11 @@ __global__ __launch_bounds__(kThreads) void k_scan_top(uint32_t *__restrict__ bl
 }
 
 // Also clears count (each entry is read here once, by one thread), so the next build finds it zero.
+// SUMS: block_off holds the blocks' plain sums (k_scan_top did not run) and every block adds up the
+// sums of the blocks before it itself -- one launch less, for grids of up to kScanFoldBlocks blocks.
+constexpr int kScanFoldBlocks = 1024;
+
+template <bool SUMS>
 __global__ __launch_bounds__(kThreads) void k_scan_apply(uint32_t *__restrict__ count, int m,
                                                          const uint32_t *__restrict__ block_off,
                                                          uint32_t *__restrict__ start)
@@ -143,6 +148,16 @@ __global__ __launch_bounds__(kThreads) void k_scan_apply(uint32_t *__restrict__ 
     pdl_wait();
     pdl_trigger();
     __shared__ uint32_t total;
+    uint32_t off = 0u;
+    if (SUMS) {
+        uint32_t part = 0u;
+        for (int b = threadIdx.x; b < (int)blockIdx.x; b += kThreads) part += __ldg(block_off + b);
+        block_exclusive_scan(part, &total);
+        off = total;                      // read after the scan's closing barrier
+        __syncthreads();                  // total is reused below
+    } else {
+        off = __ldg(block_off + blockIdx.x);
+    }
     const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
     uint32_t v[kScanItems];
     uint32_t s = 0u;
@@ -155,7 +170,7 @@ __global__ __launch_bounds__(kThreads) void k_scan_apply(uint32_t *__restrict__ 
         }
         s += v[k];
     }
-    uint32_t run = block_exclusive_scan(s, &total) + __ldg(block_off + blockIdx.x);
+    uint32_t run = block_exclusive_scan(s, &total) + off;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         if (base + k < m) start[base + k] = run;
@@ -429,6 +444,12 @@ __global__ __launch_bounds__(kThreads) void k_order_batch(const uint32_t *__rest
 
 int scan_blocks(int m) { return (m + kScanTile - 1) / kScanTile; }
 
+int cell_build_launches(int n, int ncells)
+{
+    const int scans = scan_blocks(ncells) <= kScanFoldBlocks ? 2 : 3;
+    return scans + (n > 0 ? 3 : 0);   // k_count, k_place, k_order (or k_order_block)
+}
+
 cudaError_t launch_build_cells_batch(int dim, const uint32_t *xq, const float *C, int n, int ncells,
                                      const RateParams *descs, const uint16_t *plume_of,
                                      const Work &w, cudaStream_t s)
@@ -441,7 +462,7 @@ cudaError_t launch_build_cells_batch(int dim, const uint32_t *xq, const float *C
     const int sb = scan_blocks(ncells);
     k_scan_blocks<<<sb, kThreads, 0, s>>>(w.count, ncells, w.block_sums);
     k_scan_top<<<1, kThreads, 0, s>>>(w.block_sums, sb);
-    k_scan_apply<<<sb, kThreads, 0, s>>>(w.count, ncells, w.block_sums, w.cell_start);
+    k_scan_apply<false><<<sb, kThreads, 0, s>>>(w.count, ncells, w.block_sums, w.cell_start);
     if (nb > 0) {
         k_place<<<nb, kThreads, 0, s>>>(w.keys, w.rank, n, w.cell_start, w.perm_tmp);
         k_order_batch<<<(ncells + kThreads - 1) / kThreads, kThreads, 0, s>>>(
@@ -460,9 +481,14 @@ cudaError_t launch_build_cells(int dim, const uint32_t *xq, const float *C, int 
         e = launch_pdl(k_count, nb, kThreads, 0, s, xq, n, dim, nc[0], nc[1], nc[2], w.keys, w.rank, w.count);
     const int sb = scan_blocks(ncells);
     if (e == cudaSuccess) e = launch_pdl(k_scan_blocks, sb, kThreads, 0, s, w.count, ncells, w.block_sums);
-    if (e == cudaSuccess) e = launch_pdl(k_scan_top, 1, kThreads, 0, s, w.block_sums, sb);
-    if (e == cudaSuccess)
-        e = launch_pdl(k_scan_apply, sb, kThreads, 0, s, w.count, ncells, w.block_sums, w.cell_start);
+    if (sb <= kScanFoldBlocks) {
+        if (e == cudaSuccess)
+            e = launch_pdl(k_scan_apply<true>, sb, kThreads, 0, s, w.count, ncells, w.block_sums, w.cell_start);
+    } else {
+        if (e == cudaSuccess) e = launch_pdl(k_scan_top, 1, kThreads, 0, s, w.block_sums, sb);
+        if (e == cudaSuccess)
+            e = launch_pdl(k_scan_apply<false>, sb, kThreads, 0, s, w.count, ncells, w.block_sums, w.cell_start);
+    }
     if (nb > 0 && e == cudaSuccess) {
         e = launch_pdl(k_place, nb, kThreads, 0, s, w.keys, w.rank, n, w.cell_start, w.perm_tmp);
         if (e != cudaSuccess) return e;

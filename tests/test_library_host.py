@@ -158,7 +158,10 @@ def test_velocity_field_mode_time_step_skin_and_grid(adelib, orc, rule):
         k = info.cell_subdiv
         assert info.nc[0] == math.floor(k / (info.support + info.skin))
         assert info.variant == 0
-        assert adelib.launches_per_step(ctx) == 10
+        # count, scan (2 launches up to 1024 scan blocks of 2048 cells, else 3), place, order,
+        # field gather, predictor, corrector, statistics fold
+        scans = 2 if -(-info.ncells // 2048) <= 1024 else 3
+        assert adelib.launches_per_step(ctx) == 3 + scans + 4
         assert nbytes >= (64 + 32) * plume.n   # caller-order and sorted V, D records + 2 sorted states
     finally:
         adelib.destroy(ctx)
@@ -257,7 +260,8 @@ def test_sweep_host_validation_and_info(adelib, orc):
         assert info.dt == pytest.approx(min(dts), rel=1e-14)
         assert info.tile[0] == 2                      # 12 sets = one group of 8 + one of 4
         v = ctypes.c_int(0)
-        assert lib.ade_sweep_launches_per_step(ctx, ctypes.byref(v)) == 0 and v.value == 7 + 4
+        scans = 2 if -(-info.ncells // 2048) <= 1024 else 3
+        assert lib.ade_sweep_launches_per_step(ctx, ctypes.byref(v)) == 0 and v.value == 4 + scans + 4
     finally:
         lib.ade_sweep_destroy(ctx)
     bad = theta.copy()
