@@ -96,10 +96,12 @@ TRAFFIC_PER_LAUNCH = {("ladder-1024-n120-r10", "direct-branch-free"): 23.84e6,
 # interaction walks (ade flags) selectable with --variant; "auto" autotunes grid and walk
 VARIANT_FLAGS = {"direct-branch-free": 1, "tiled": 2, "direct-branched": 4,
                  "direct-branch-free-trimmed": 9, "direct-branched-trimmed": 12,
-                 "direct-branch-free-paired": 17, "direct-branch-free-trimmed-paired": 25}
+                 "direct-branch-free-paired": 17, "direct-branch-free-trimmed-paired": 25,
+                 "direct-branched-paired": 20, "direct-branched-trimmed-paired": 28}
 VARIANT_NAMES = {0: "direct-branch-free", 1: "tiled", 2: "direct-branched", 3: "direct-branch-free-trimmed",
                  4: "direct-branched-trimmed", 5: "direct-branch-free-paired",
-                 6: "direct-branch-free-trimmed-paired"}
+                 6: "direct-branch-free-trimmed-paired", 7: "direct-branched-paired",
+                 8: "direct-branched-trimmed-paired"}
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
 

@@ -55,12 +55,13 @@ extern "C" {
                                 the stencil cells within (1 + 2^-12) H of itself; the skipped
                                 candidates contribute exactly 0, so results are bitwise unchanged
                                 (square or cubic boxes; other boxes walk the full stencil) */
-#define ADE_FLAG_PAIRED 16u  /* with DIRECT and/or TRIMMED (or alone = DIRECT): the branch-free direct
-                                walk with two adjacent sorted particles per thread, which share one
-                                candidate stream (the union of their stencil ranges) and evaluate
-                                both terms with packed FP32x2 instructions; candidates outside a
-                                particle's own range contribute exactly 0, so results are bitwise
-                                those of the one-particle walk.  Not in velocity-field mode. */
+#define ADE_FLAG_PAIRED 16u  /* with DIRECT or BRANCHED (alone = DIRECT), optionally TRIMMED: that
+                                direct walk with two adjacent sorted particles per thread, which
+                                share one candidate stream (the union of their stencil ranges) and
+                                evaluate both terms with packed FP32x2 instructions; candidates
+                                outside a particle's own range contribute exactly 0, so results are
+                                bitwise those of the one-particle walk.  Not in velocity-field
+                                mode. */
 
 #define ADE_DT_LAMBDA_MAX 0 /* dt = coef h^2 / lambda_max(D) */
 #define ADE_DT_TRACE 1      /* Eq. 10: dt = coef h^2 / (D_xx + D_yy [+ D_zz]) */

@@ -14,7 +14,7 @@ import sys
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
-SOURCES = ["cells.cu", "rate.cu", "rate_field.cu", "reduce.cu", "api.cu", "noalloc.cu", "adjoint.cu", "peak.cu", "sweep.cu", "checkpoint.cu"]
+SOURCES = ["cells.cu", "rate.cu", "rate_pair.cu", "rate_field.cu", "reduce.cu", "api.cu", "noalloc.cu", "adjoint.cu", "peak.cu", "sweep.cu", "checkpoint.cu"]
 LIB = os.path.join(PKG, "libade_sph.so")
 BUILD_DIR = os.path.join(ROOT, "_build", "ade")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -71,7 +71,7 @@ struct RateParams {
     uint32_t back[3];// evaluation position minus cell-build position (0, or the half-step drift)
     int variant;     // 0 = direct walk (branch-free), 1 = shared-memory tiles, 2 = direct walk
                      // branching on the support test, 3 / 4 = 0 / 2 with per-particle trimmed rows,
-                     // 5 / 6 = 0 / 3 with two targets per thread (packed FP32x2)
+                     // 5 / 6 / 7 / 8 = 0 / 3 / 2 / 4 with two targets per thread (packed FP32x2)
     int k;           // halo width in cells (cells per support radius)
     int tx, ty, tz;  // target cells per tile
     int ntx, nty, ntz;  // tiles per axis
@@ -221,6 +221,10 @@ cudaError_t launch_field_records(int dim, const float *v_dev, int n, const Field
                                  cudaStream_t s);
 // Sorted records: V[i] = Vc[perm[i]] (and DA, DB).
 cudaError_t launch_field_permute(int dim, const uint32_t *perm, int n, const FieldWork &fw, cudaStream_t s);
+// Paired walks (variants 5-8; rate_pair.cu), called by launch_rate.
+cudaError_t launch_rate_pair(int dim, int kernel, int epi, bool iso, const uint4 *Pe, const uint4 *Pc,
+                             const uint32_t *cs, const uint32_t *perm, const RateParams &prm, const EpiOut &out,
+                             cudaStream_t s);
 cudaError_t launch_rate_field(int dim, int kernel, int epi, const uint4 *Pe, const uint32_t *cell_start,
                               const uint32_t *perm, const FieldWork &fw, const RateParams &prm,
                               const FieldParams &fp, const EpiOut &out, cudaStream_t s);

@@ -234,11 +234,14 @@ int validate(const ade_params *p, int n)
     if (!isfinite(p->dt) || !isfinite(p->gamma)) return fail(ADE_ERR_ARG, "dt and gamma must be finite");
     if (p->dt_rule != ADE_DT_LAMBDA_MAX && p->dt_rule != ADE_DT_TRACE) return fail(ADE_ERR_ARG, "unknown dt_rule");
     if (p->cell_subdiv < 0 || p->cell_subdiv > ade::kMaxSubdiv) return fail(ADE_ERR_ARG, "cell_subdiv must be 0..6");
+    // the paired walks: PAIRED with DIRECT or BRANCHED (not both), optionally TRIMMED
     const unsigned pf = p->flags & ~(ADE_FLAG_DIRECT | ADE_FLAG_TRIMMED);
+    const unsigned pb = p->flags & ~(ADE_FLAG_BRANCHED | ADE_FLAG_TRIMMED);
+    const bool paired_ok = pf == ADE_FLAG_PAIRED || pb == ADE_FLAG_PAIRED;
     if (p->flags != 0u && p->flags != ADE_FLAG_DIRECT && p->flags != ADE_FLAG_TILED &&
         p->flags != ADE_FLAG_BRANCHED && p->flags != ADE_FLAG_TRIMMED &&
         p->flags != (ADE_FLAG_TRIMMED | ADE_FLAG_DIRECT) && p->flags != (ADE_FLAG_TRIMMED | ADE_FLAG_BRANCHED) &&
-        pf != ADE_FLAG_PAIRED)
+        !paired_ok)
         return fail(ADE_ERR_ARG, "unknown or conflicting flags");
     if (!(p->vmax >= 0.0) || !isfinite(p->vmax)) return fail(ADE_ERR_ARG, "vmax must be finite and >= 0");
     if (p->vmax > 0.0 && p->flags != 0u && p->flags != ADE_FLAG_DIRECT)
@@ -631,7 +634,9 @@ int plume_constants(const ade_params *p, int n, const Derived &d, double *D, dou
     rp.pf = (float)(0.5 * (p->mass / p->rho) * kernel_kc(p->kernel, dm, d.H));
     rp.variant = d.tiles.variant == 1 ? 1 : ((p->flags & ADE_FLAG_BRANCHED) ? 2 : 0);
     if (rp.variant != 1 && (p->flags & ADE_FLAG_TRIMMED)) rp.variant = rp.variant == 2 ? 4 : 3;  // trimmed rows
-    if (p->flags & ADE_FLAG_PAIRED) rp.variant = (p->flags & ADE_FLAG_TRIMMED) ? 6 : 5;       // paired walk
+    if (p->flags & ADE_FLAG_PAIRED)                                                           // paired walks
+        rp.variant = (p->flags & ADE_FLAG_BRANCHED) ? ((p->flags & ADE_FLAG_TRIMMED) ? 8 : 7)
+                                                    : ((p->flags & ADE_FLAG_TRIMMED) ? 6 : 5);
     rp.k = d.tiles.k;
     rp.tx = d.tiles.tx;
     rp.ty = d.tiles.ty;
@@ -860,7 +865,7 @@ int ade_autotune(ade_ctx *c, double *best_ms_host, void *stream)
     };
     Cand top[3] = {{1e30, c->subdiv, c->rp.variant}, {1e30, 0, -1}, {1e30, 0, -1}};
     for (int k = 1; rc == ADE_OK && k <= ade::kMaxSubdiv; ++k)
-        for (int variant = 0; rc == ADE_OK && variant < 7; ++variant) {
+        for (int variant = 0; rc == ADE_OK && variant < 9; ++variant) {
             if (c->field && variant != 0) continue;  // one interaction kernel in velocity-field mode
             double ms = 1e30, t = 0.0;
             for (int rep = 0; rep < 2; ++rep)

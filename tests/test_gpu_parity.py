@@ -100,7 +100,7 @@ def test_cells_bit_exact_every_subdivision(lib, orc, k):
 # ADE_FLAG_TILED, _DIRECT, _BRANCHED, the two direct walks with _TRIMMED rows, and the _PAIRED
 # branch-free walk (full and trimmed rows)
 VARIANTS = {"tiled": 2, "direct": 1, "branched": 4, "direct-trimmed": 9, "branched-trimmed": 12,
-            "paired": 17, "paired-trimmed": 25}
+            "paired": 17, "paired-trimmed": 25, "paired-branched": 20, "paired-branched-trimmed": 28}
 
 
 @pytest.mark.parametrize("variant", sorted(VARIANTS))
@@ -114,7 +114,8 @@ def test_rate_parity(lib, orc, name, variant):
     if variant == "branched":
         assert sim.info.variant == 2
     if variant.startswith("paired"):
-        assert sim.info.variant == (6 if variant.endswith("trimmed") else 5)
+        assert sim.info.variant == {"paired": 5, "paired-trimmed": 6, "paired-branched": 7,
+                                    "paired-branched-trimmed": 8}[variant]
     r_gpu = sim.rate().cpu().numpy()
     r_orc, pairs = _oracle_rate(orc, plume, xq, C)
     assert _rel(r_gpu, r_orc) <= RATE_TOL
@@ -160,6 +161,13 @@ def test_trimmed_direct_walk_equals_full_stencil_bitwise(lib, name):
         assert pf.info.variant == 5 and pt.info.variant == 6
         assert np.array_equal(pf.rate().cpu().numpy().view(np.uint32), rf.view(np.uint32)), k
         assert np.array_equal(pt.rate().cpu().numpy().view(np.uint32), rf.view(np.uint32)), k
+        # the paired branched walks against the one-target branched walk
+        pb = _sim(lib, plume, xq, C, cell_subdiv=k, flags=lib.FLAG_PAIRED | lib.FLAG_BRANCHED)
+        pbt = _sim(lib, plume, xq, C, cell_subdiv=k, flags=lib.FLAG_PAIRED | lib.FLAG_BRANCHED | lib.FLAG_TRIMMED)
+        assert pb.info.variant == 7 and pbt.info.variant == 8
+        rb = b.rate().cpu().numpy()
+        assert np.array_equal(pb.rate().cpu().numpy().view(np.uint32), rb.view(np.uint32)), k
+        assert np.array_equal(pbt.rate().cpu().numpy().view(np.uint32), rb.view(np.uint32)), k
         # one step with trimmed rows, or paired, equals one with the full stencil
         f.step(1)
         d.step(1)
@@ -196,6 +204,10 @@ def test_paired_walk_clustered_odd_count_bitwise(lib, orc, k):
     r1 = one.rate().cpu().numpy()
     assert np.array_equal(r1.view(np.uint32), two.rate().cpu().numpy().view(np.uint32))
     assert np.array_equal(r1.view(np.uint32), two_t.rate().cpu().numpy().view(np.uint32))
+    ob = sim(lib.FLAG_BRANCHED)
+    rb = ob.rate().cpu().numpy()
+    for fl in (lib.FLAG_PAIRED | lib.FLAG_BRANCHED, lib.FLAG_PAIRED | lib.FLAG_BRANCHED | lib.FLAG_TRIMMED):
+        assert np.array_equal(rb.view(np.uint32), sim(fl).rate().cpu().numpy().view(np.uint32))
     r_orc, _ = orc.rate(xo, plume.velocity, C.astype(np.float64), 1.0 / n, 1.0, box, 0,
                         plume.support, 4.0, plume.alpha_L, plume.alpha_T, plume.D_m)
     assert _rel(r1, r_orc) <= RATE_TOL

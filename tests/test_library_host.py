@@ -167,10 +167,10 @@ def test_velocity_field_mode_time_step_skin_and_grid(adelib, orc, rule):
         adelib.destroy(ctx)
 
 
-@pytest.mark.parametrize("flags,variant", [(16, 5), (17, 5), (24, 6), (25, 6)])
+@pytest.mark.parametrize("flags,variant", [(16, 5), (17, 5), (24, 6), (25, 6), (20, 7), (28, 8)])
 def test_paired_walk_flags(adelib, flags, variant):
     """ADE_FLAG_PAIRED alone or with DIRECT selects the paired branch-free walk (5), with TRIMMED
-    its trimmed form (6)."""
+    its trimmed form (6); with BRANCHED the paired branched walk (7) and its trimmed form (8)."""
     plume = inputs.ladder_2d(256, 10)
     ctx, _ = _ctx(adelib, adelib.params_for(plume, flags=flags), plume.n)
     try:
@@ -179,9 +179,10 @@ def test_paired_walk_flags(adelib, flags, variant):
         adelib.destroy(ctx)
 
 
-@pytest.mark.parametrize("flags", [16 | 2, 16 | 4, 16 | 4 | 8, 32])
+@pytest.mark.parametrize("flags", [16 | 2, 16 | 4 | 1, 16 | 4 | 8 | 1, 32])
 def test_paired_walk_conflicting_flags(adelib, flags):
-    """PAIRED with the tiled or branched walks, and unknown bits, are rejected."""
+    """PAIRED with the tiled walk or with both DIRECT and BRANCHED, and unknown bits, are
+    rejected."""
     plume = inputs.ladder_2d(256, 10)
     with pytest.raises(adelib.AdeError) as e:
         adelib.workspace_bytes(adelib.params_for(plume, flags=flags), plume.n)
