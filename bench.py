@@ -451,31 +451,56 @@ def run_batched(args):
                 "phase_ms_per_step": {k: sum(p[i] for p in phases) / len(phases)
                                       for i, k in enumerate(("cells", "predictor", "corrector"))}}
 
-    # end to end: H2D of every plume's x and C, one graph-replayed step, D2H of C
+    # end to end: H2D of every plume's x and C, one graph-replayed step, D2H of C; as for the
+    # single plume, a second batch given the first one's autotuned configuration alternates with
+    # it so that one's copies (on their own streams) overlap the other's step
     xq_pin = b.xq.cpu().pin_memory()
     C_pin = b.C.cpu().pin_memory()
     C_out = torch.empty_like(C_pin).pin_memory()
-    for _ in range(args.warmup):
-        b.xq.copy_(xq_pin, non_blocking=True)
-        b.C.copy_(C_pin, non_blocking=True)
-        b.run(1)
-        C_out.copy_(b.C, non_blocking=True)
+    b2 = ade.Batch(plist, [s_[0] for s_ in states], [s_[1] for s_ in states], device=device)
+    b2.set_config(b.config())
+    batches = (b, b2)
+    h2d, d2h = torch.cuda.Stream(device), torch.cuda.Stream(device)
+    ev = {k: [torch.cuda.Event() for _ in batches] for k in ("in", "ran", "out")}
+    for e in ev["out"]:
+        e.record(d2h)
+
+    def e2e_step(k):
+        q, bx = k % 2, batches[k % 2]
+        h2d.wait_event(ev["out"][q])
+        with torch.cuda.stream(h2d):
+            bx.xq.copy_(xq_pin, non_blocking=True)
+            bx.C.copy_(C_pin, non_blocking=True)
+        ev["in"][q].record(h2d)
+        stream.wait_event(ev["in"][q])
+        with torch.cuda.stream(stream):
+            bx.run(1)
+        ev["ran"][q].record(stream)
+        d2h.wait_event(ev["ran"][q])
+        with torch.cuda.stream(d2h):
+            C_out.copy_(bx.C, non_blocking=True)
+        ev["out"][q].record(d2h)
+
+    for k in range(max(args.warmup, 1)):
+        e2e_step(k)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
-        b.xq.copy_(xq_pin, non_blocking=True)
-        b.C.copy_(C_pin, non_blocking=True)
-        b.run(1)
-        C_out.copy_(b.C, non_blocking=True)
+    h2d.wait_stream(stream)
+    d2h.wait_stream(stream)
+    for k in range(args.steps):
+        e2e_step(k)
+    stream.wait_stream(d2h)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_value, e2e_ms, _ = sharding.aggregate(2.0 * pairs * args.steps, e0.elapsed_time(e1), device=agg_dev)
     e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": int(xq_pin.numel() * 4 + C_pin.numel() * 4),
            "d2h_bytes_per_step": int(C_out.numel() * 4), "ms_per_step": e2e_ms / args.steps,
-           "path": "ade_batch_run (graph replay) via ctypes"}
+           "path": "ade_batch_run (graph replay) via ctypes; two batches of one configuration "
+                   "alternate, H2D and D2H on their own streams overlapping the other batch's step"}
+    b2.close()
     ms_per_step = total_ms / args.steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -688,30 +713,55 @@ def run_sweep(args):
     roofline["measured_alu"]["pair_set_roof"] = roofline["measured_alu"]["ffma_per_s"] / per_set / 1e9
     roofline["measured_alu"]["frac"] = achieved / roofline["measured_alu"]["pair_set_roof"]
 
-    # end to end: H2D of x and the P fields, one graph-replayed step, D2H of the P fields
+    # end to end: H2D of x and the P fields, one graph-replayed step, D2H of the P fields; as for
+    # the single plume, two sweeps of the same configuration alternate so that one's copies (on
+    # their own streams) overlap the other's step
     xq_pin = sw.xq.cpu().pin_memory()
     C_pin = sw.C.cpu().pin_memory()
     C_out = torch.empty_like(C_pin).pin_memory()
-    for _ in range(args.warmup):
-        sw.xq.copy_(xq_pin, non_blocking=True)
-        sw.C.copy_(C_pin, non_blocking=True)
-        sw.run(1)
-        C_out.copy_(sw.C, non_blocking=True)
+    sw2 = ade.Sweep(ade.params_for(plume), xq, np.broadcast_to(C, (P, plume.n)), theta, device=device)
+    assert sw2.info.cell_subdiv == sw.info.cell_subdiv and sw2.info.dt == sw.info.dt
+    sweeps = (sw, sw2)
+    h2d, d2h = torch.cuda.Stream(device), torch.cuda.Stream(device)
+    ev = {k: [torch.cuda.Event() for _ in sweeps] for k in ("in", "ran", "out")}
+    for e in ev["out"]:
+        e.record(d2h)
+
+    def e2e_step(k):
+        q, sx = k % 2, sweeps[k % 2]
+        h2d.wait_event(ev["out"][q])
+        with torch.cuda.stream(h2d):
+            sx.xq.copy_(xq_pin, non_blocking=True)
+            sx.C.copy_(C_pin, non_blocking=True)
+        ev["in"][q].record(h2d)
+        stream.wait_event(ev["in"][q])
+        with torch.cuda.stream(stream):
+            sx.run(1)
+        ev["ran"][q].record(stream)
+        d2h.wait_event(ev["ran"][q])
+        with torch.cuda.stream(d2h):
+            C_out.copy_(sx.C, non_blocking=True)
+        ev["out"][q].record(d2h)
+
+    for k in range(max(args.warmup, 1)):
+        e2e_step(k)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
-        sw.xq.copy_(xq_pin, non_blocking=True)
-        sw.C.copy_(C_pin, non_blocking=True)
-        sw.run(1)
-        C_out.copy_(sw.C, non_blocking=True)
+    h2d.wait_stream(stream)
+    d2h.wait_stream(stream)
+    for k in range(args.steps):
+        e2e_step(k)
+    stream.wait_stream(d2h)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_value, e2e_ms, _ = sharding.aggregate(units_per_step * args.steps, e0.elapsed_time(e1), device=agg_dev)
     e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(xq_pin.numel() * 4 + C_pin.numel() * 4),
            "d2h_bytes_per_step": int(C_out.numel() * 4), "ms_per_step": e2e_ms / args.steps,
-           "path": "ade_sweep_run (graph replay) via ctypes"}
+           "path": "ade_sweep_run (graph replay) via ctypes; two sweeps alternate, H2D and D2H on their "
+                   "own streams overlapping the other sweep's step"}
+    sw2.close()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,

@@ -307,6 +307,15 @@ int ade_batch_get_plume_info(const ade_batch *b, int plume, ade_info *info_host)
  * Leaves the particle state unchanged; waits; best_ms_host (may be NULL) gets the best time. */
 int ade_batch_autotune(ade_batch *b, double *best_ms_host, void *stream);
 
+/* The batch's configuration -- cell-subdivision policy (0 = per-plume cost model, 1..6 cells per
+ * support radius), work-item size in particles and persistent grid in blocks -- as chosen by
+ * ade_batch_autotune, and its application to another batch of the same plumes so that both run
+ * the same kernels (no counterpart in the paper).  set: subdiv_mode in [0, 6], tile_size in
+ * [32, 4096], grid_blocks in [1, 65536]; re-plans the work list and uploads it on `stream` (waits);
+ * ADE_ERR_ARG outside those ranges, the batch unchanged.  Host pointers may not be NULL. */
+int ade_batch_get_config(const ade_batch *b, int *subdiv_mode_host, int *tile_size_host, int *grid_blocks_host);
+int ade_batch_set_config(ade_batch *b, int subdiv_mode, int tile_size, int grid_blocks, void *stream);
+
 /* One batched step bracketed by CUDA events; waits; phase_ms_host[4] = {cell build, predictor,
  * corrector, 0} in milliseconds. */
 int ade_batch_step_timed(ade_batch *b, double *phase_ms_host, void *stream);

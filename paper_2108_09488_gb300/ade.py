@@ -38,6 +38,7 @@ EXPORTS = ("ade_workspace_bytes", "ade_init_particles", "ade_get_info", "ade_bui
            "ade_batch_workspace_bytes", "ade_batch_init", "ade_batch_step", "ade_batch_run",
            "ade_batch_stats", "ade_batch_count_pairs", "ade_batch_get_plume_info",
            "ade_batch_autotune", "ade_batch_launches_per_step", "ade_batch_destroy",
+           "ade_batch_get_config", "ade_batch_set_config",
            "ade_batch_step_timed", "ade_set_dispersivity", "ade_adjoint_workspace_bytes",
            "ade_adjoint", "ade_autotune", "ade_set_velocity_field", "ade_alu_peaks",
            "ade_sweep_workspace_bytes", "ade_sweep_init", "ade_sweep_get_info", "ade_sweep_rate",
@@ -119,6 +120,8 @@ def load():
         "ade_batch_count_pairs": (I, [P, ctypes.POINTER(LL), V]),
         "ade_batch_get_plume_info": (I, [P, I, ctypes.POINTER(Info)]),
         "ade_batch_autotune": (I, [P, ctypes.POINTER(ctypes.c_double), V]),
+        "ade_batch_get_config": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "ade_batch_set_config": (I, [P, I, I, I, V]),
         "ade_batch_launches_per_step": (I, [P, ctypes.POINTER(I)]),
         "ade_batch_step_timed": (I, [P, ctypes.POINTER(ctypes.c_double), V]),
         "ade_set_dispersivity": (I, [P, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
@@ -519,6 +522,17 @@ class Batch:
         ms = ctypes.c_double(0.0)
         _check(load().ade_batch_autotune(self.ctx, ctypes.byref(ms), self.stream))
         return ms.value
+
+    def config(self):
+        """(subdivision policy, work-item size, persistent grid) in use."""
+        m, t, g = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(load().ade_batch_get_config(self.ctx, ctypes.byref(m), ctypes.byref(t), ctypes.byref(g)))
+        return m.value, t.value, g.value
+
+    def set_config(self, cfg):
+        """Apply a (subdivision policy, work-item size, persistent grid) triple, e.g. another
+        batch's config() after its autotune."""
+        _check(load().ade_batch_set_config(self.ctx, int(cfg[0]), int(cfg[1]), int(cfg[2]), self.stream))
 
     def launches_per_step(self):
         v = ctypes.c_int(0)

@@ -1693,6 +1693,36 @@ int ade_batch_count_pairs(ade_batch *b, long long *pairs_host, void *stream)
     return ADE_OK;
 }
 
+int ade_batch_get_config(const ade_batch *b, int *subdiv_mode, int *tile_size, int *grid_blocks)
+{
+    if (!b || !subdiv_mode || !tile_size || !grid_blocks) return fail(ADE_ERR_ARG, "NULL argument");
+    *subdiv_mode = b->subdiv_mode;
+    *tile_size = b->tile_size;
+    *grid_blocks = b->grid;
+    return ADE_OK;
+}
+
+int ade_batch_set_config(ade_batch *b, int subdiv_mode, int tile_size, int grid_blocks, void *stream)
+{
+    if (!b) return fail(ADE_ERR_ARG, "batch is NULL");
+    if (subdiv_mode < 0 || subdiv_mode > ade::kMaxSubdiv || tile_size < kMinTile || tile_size > 4096 ||
+        grid_blocks < 1 || grid_blocks > 65536)
+        return fail(ADE_ERR_ARG, "configuration out of range");
+    const int m0 = b->subdiv_mode, t0 = b->tile_size, g0 = b->grid;
+    b->subdiv_mode = subdiv_mode;
+    b->tile_size = tile_size;
+    b->grid = grid_blocks;
+    int rc = batch_plan(b);
+    if (rc) {
+        b->subdiv_mode = m0;
+        b->tile_size = t0;
+        b->grid = g0;
+        batch_plan(b);
+        return rc;
+    }
+    return batch_upload(b, (cudaStream_t)stream);
+}
+
 int ade_batch_get_plume_info(const ade_batch *b, int plume, ade_info *info)
 {
     if (!b || !info || plume < 0 || plume >= b->P) return fail(ADE_ERR_ARG, "bad argument");

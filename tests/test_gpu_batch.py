@@ -115,3 +115,30 @@ def test_full_batch_64_plumes_sampled_identity(lib):
         s = _single(lib, plumes[i], b.plume_info(i).cell_subdiv, states[i])
         s.step(1)
         assert _same(s.state()[1], b.state(i)[1]) and _same(s.state()[0], b.state(i)[0])
+
+
+def test_batch_config_copy_gives_identical_steps(lib):
+    """ade_batch_get_config / ade_batch_set_config: a second batch of the same plumes given the
+    first one's autotuned configuration steps bit for bit like it; out-of-range configurations
+    are refused and leave the batch unchanged."""
+    plumes = inputs.batched_2d(**SMALL)
+    a, _ = _batch(lib, plumes)
+    b, _ = _batch(lib, plumes)
+    a.autotune()
+    cfg = a.config()
+    b.set_config(cfg)
+    assert b.config() == cfg
+    for i in range(len(plumes)):
+        assert b.plume_info(i).tile[0] == a.plume_info(i).tile[0]
+        assert b.plume_info(i).cell_subdiv == a.plume_info(i).cell_subdiv
+    a.run(3)
+    b.run(3)
+    for i in range(len(plumes)):
+        xa, Ca = a.state(i)
+        xb, Cb = b.state(i)
+        assert _same(xa, xb) and _same(Ca, Cb)
+    for bad in ((7, 256, 100), (0, 16, 100), (0, 256, 0)):
+        with pytest.raises(lib.AdeError) as e:
+            b.set_config(bad)
+        assert e.value.code == -1
+    assert b.config() == cfg
