@@ -158,24 +158,28 @@ int ade_dispersion_rate(ade_ctx *ctx, float *dCdt_dev, void *stream);
 int ade_count_pairs(ade_ctx *ctx, long long *pairs_host, void *stream);
 
 /* nsteps predictor-corrector steps (Eq. 8-9), each: cell build, rate at level l with the fused
- * predictor, rate at level l+1/2 with the fused corrector and FP64 reductions. */
+ * predictor, rate at level l+1/2 with the fused corrector (which writes one partial of sum C,
+ * min C and max C per warp), and the fold of those partials into the step's FP64 statistics. */
 int ade_step(ade_ctx *ctx, int nsteps, void *stream);
 
 /* As ade_step, replaying one captured CUDA graph per step (captured on the first call).  With
- * stats_host non-NULL it waits for the stream and fills in the final diagnostics; with NULL it
+ * stats_host non-NULL it waits for the stream and fills in the last step's statistics (those of
+ * the state it wrote; with nsteps = 0, those of the current state as ade_get_stats); with NULL it
  * only enqueues. */
 int ade_run(ade_ctx *ctx, int nsteps, ade_stats *stats_host, void *stream);
 
 /* One step (as ade_step) bracketed by CUDA events on `stream`; waits for it and returns the device
- * time of each phase in phase_ms_host[4] = {cell build, predictor rate, corrector rate, reduction}
- * (milliseconds).  Used for per-kernel roofline measurements. */
+ * time of each phase in phase_ms_host[4] = {cell build, predictor rate, corrector rate, fold of
+ * the statistics} (milliseconds).  Used for per-kernel roofline measurements. */
 int ade_step_timed(ade_ctx *ctx, double *phase_ms_host, void *stream);
 
-/* Kernel launches one step enqueues (cell build passes, reorder, the velocity-field gather in
- * velocity-field mode, two rate launches). */
+/* Kernel launches one step enqueues: the cell build (count, two scan launches -- three above 1024
+ * scan blocks of 2048 cells --, placement, ordering), the velocity-field gather in velocity-field
+ * mode, the two rate launches and the statistics fold. */
 int ade_launches_per_step(const ade_ctx *ctx, int *launches);
 
-/* FP64 mass, min and max of the current concentrations; waits for the stream. */
+/* FP64 mass, min and max of the current concentrations (recomputed from C, so a caller's own
+ * writes to C count); waits for the stream. */
 int ade_get_stats(ade_ctx *ctx, ade_stats *stats_host, void *stream);
 
 /* Error of the current state against the closed form of Sec. 3 (Eq. 12-13 in 2D, the same
