@@ -90,7 +90,7 @@ MUFU_LANES_PER_SM = 16
 TRAFFIC_PER_LAUNCH = {("ladder-1024-n120-r10", "direct-branch-free"): 23.84e6,
                       ("ladder-1024-n120-r10", "direct-branch-free-paired"): 23.88e6,
                       ("paper-1m-n31k-c4", "direct-branch-free-trimmed-paired"): 20.11e6,
-                      ("batched-64", None): 42.12e6,
+                      ("batched-64", None): 42.04e6,
                       ("field-1024-n120-r10", "velocity-field-direct"): 82.24e6,
                       ("sweep-512-8", None): 18.77e6}
 # interaction walks (ade flags) selectable with --variant; "auto" autotunes grid and walk

@@ -63,6 +63,7 @@ __global__ __launch_bounds__(kRedThreads) void k_reduce_final(const double *__re
 constexpr int kFoldThreads = 1024;
 constexpr int kFoldPerCta = 1024;   // partials per CTA before another CTA of the cluster is used
 static_assert(kFoldMaxCtas <= 32, "CTA 0 folds one CTA result per lane of one warp");
+static_assert(kFoldThreads == 32 * 32, "warp 0 folds one result per warp of the CTA");
 
 __device__ __forceinline__ void fold_two_sum(float &hi, float &lo, float x, float xlo)
 {
