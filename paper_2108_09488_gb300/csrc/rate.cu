@@ -12,22 +12,27 @@
 // Wendland C4 (Eq. 7, support H = h): f = (1-q)^5 (1+5q), kc = -(56/3) B / H^2.
 // The convective term of Eq. 4 is identically zero for uniform v and is not evaluated.
 //
-// Two variants share the pair arithmetic and the epilogue:
-//   * direct: one thread per cell-sorted particle; candidates are read from the sorted copy in
-//     global memory (L1-cached 16-byte words {x, y, z, C}); separations are int32 differences of
-//     fixed-point words converted to FP32 for every pair; each stencil row (2w+1 cells with
-//     consecutive keys) is one contiguous index range, two at a periodic seam.
-//   * tiled: one CTA per block of TX x TY (x TZ) cells.  The CTA stages every particle of the
-//     block and its k-cell halo into shared memory once, as int32 fixed-point offsets from the
-//     block centre (the minimum image from the centre), plus a local cell start table.  Each
-//     thread then walks its targets' stencil rows over shared memory; the pair separation is the
-//     exact int32 difference converted to FP32, as in the direct walk, so both variants round
-//     relative to the separation itself rather than to the block size.  The pair term is
+// The walks share the pair arithmetic and the epilogue (rate_walk.cuh):
+//   * direct (variants 0, 2, 3, 4; this file): one thread per cell-sorted particle; candidates are
+//     read from the sorted copy in global memory (L1-cached 16-byte words {x, y, z, C});
+//     separations are int32 differences of fixed-point words converted to FP32 for every pair;
+//     each stencil row (2w+1 cells with consecutive keys) is one contiguous index range, two at a
+//     periodic seam.  Branch-free (0, 3) or branching on the support test (2, 4), over the full
+//     stencil (0, 2) or the cells within reach of the particle (trimmed rows: 3, 4).
+//   * paired (variants 5-8; rate_pair.cu): the direct walks with two adjacent sorted particles per
+//     thread sharing one candidate stream, the FP32 arithmetic packed in FP32x2 instructions.
+//   * tiled (variant 1; this file): one CTA per block of TX x TY (x TZ) cells.  The CTA stages
+//     every particle of the block and its k-cell halo into shared memory once, as int32 fixed-point
+//     offsets from the block centre (the minimum image from the centre), plus a local cell start
+//     table.  Each thread then walks its targets' stencil rows over shared memory; the pair
+//     separation is the exact int32 difference converted to FP32, as in the direct walk, so both
+//     round relative to the separation itself rather than to the block size.  The pair term is
 //     evaluated without a branch: outside the support (1 - q) is clamped to 0, so the term
 //     vanishes.  A block whose halo does not fit the staging buffer falls back to the direct walk.
-// Both variants sum each stencil row's terms in FP32 and add the row sums with Neumaier's
-// compensated summation, visiting rows and, inside a row, particles in sorted order, so results
-// are deterministic and independent of the tiling.
+//   * batched (this file): the direct walk over a persistent queue of (plume, range) work items.
+// All walks sum each stencil row's terms in FP32 and add the row sums with Neumaier's compensated
+// summation, visiting rows and, inside a row, particles in sorted order, so results are
+// deterministic and the same bits whichever walk computes them.
 #include "ade_internal.h"
 
 namespace ade {
