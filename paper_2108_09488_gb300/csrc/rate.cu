@@ -32,7 +32,9 @@
 //   * batched (this file): the direct walk over a persistent queue of (plume, range) work items.
 // All walks sum each stencil row's terms in FP32 and add the row sums with Neumaier's compensated
 // summation, visiting rows and, inside a row, particles in sorted order, so results are
-// deterministic and the same bits whichever walk computes them.
+// deterministic; the branch-free walks (full, trimmed, paired, tiled) give the same bits, and so
+// do the branched ones among themselves (they can differ from the branch-free walks only by a
+// term whose separation rounds to the support radius).
 #include "ade_internal.h"
 
 namespace ade {
