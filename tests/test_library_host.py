@@ -136,6 +136,16 @@ def test_batch_workspace_and_validation(adelib):
     assert e.value.code == -1
 
 
+def test_batch_config_null_arguments(adelib):
+    """ade_batch_get_config / ade_batch_set_config refuse a NULL batch or NULL outputs before any
+    device work."""
+    import ctypes
+    lib = adelib.load()
+    m, t, g = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    assert lib.ade_batch_get_config(None, ctypes.byref(m), ctypes.byref(t), ctypes.byref(g)) == -1
+    assert lib.ade_batch_set_config(None, 0, 256, 1216, None) == -1
+
+
 def _field_plume():
     return inputs.Plume(dim=2, side=96, h_over_dx=1.9, jitter=0.3, seed=11)
 
