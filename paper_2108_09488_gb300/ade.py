@@ -22,6 +22,9 @@ ERRORS = {-1: "ADE_ERR_ARG", -2: "ADE_ERR_CUDA", -3: "ADE_ERR_NUMERIC", -4: "ADE
           -5: "ADE_ERR_CAPACITY", -6: "ADE_ERR_STATE"}
 WENDLAND_C2 = 0
 WENDLAND_C4 = 1
+# interaction walks (ADE_FLAG_* of ade_sph.h); info.variant reports the one in use:
+# 0 branch-free direct, 1 tiled, 2 branched direct, 3 / 4 = 0 / 2 over trimmed rows,
+# 5 / 6 / 7 / 8 = 0 / 3 / 2 / 4 with two particles per thread (FLAG_PAIRED, packed FP32x2)
 FLAG_DIRECT = 1
 FLAG_TILED = 2
 FLAG_BRANCHED = 4
@@ -366,7 +369,8 @@ class Simulation:
         return closed_form_error(self.ctx, x0, w, C0, nimg, self.stream)
 
     def autotune(self):
-        """Pick the cell subdivision and interaction variant by timing (ade_autotune)."""
+        """Pick the cell subdivision and interaction walk (variants 0-8) by timing a cell build
+        and two evaluations per configuration (ade_autotune); returns that time in ms."""
         ms = ctypes.c_double(0.0)
         _check(load().ade_autotune(self.ctx, ctypes.byref(ms), self.stream))
         self.info = get_info(self.ctx)
