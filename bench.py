@@ -5,9 +5,11 @@ A *step* is one predictor-corrector step (Eq. 8-9) of the whole hot path on one 
 hash, radix sort, reorder and cell table, the rate evaluation at level l with the fused predictor,
 the rate evaluation at level l+1/2 with the fused corrector and the FP64 reductions.  An
 *interaction* is one ordered in-support pair (b != a, |x_ab| < H) evaluated once; a step evaluates
-2 x pairs.  Inputs are synthetic and seeded (inputs.py): the default workload is the top rung of
-the 2D convergence ladder, a 1024^2 lattice with 120 neighbours, alpha_L/alpha_T = 10, 45-degree
-flow.  The L2 cache is flushed (256 MiB write) before every timed step.
+2 x pairs.  Inputs are synthetic and seeded (inputs.py): the default workload is the largest
+single-GPU configuration, the 3D plume on a 128^3 lattice in the unit cube (2,097,152 particles,
+h = 2 dx, about 250 neighbours, flow along the diagonal); --workload selects the others (the 2D
+convergence ladder, the batched plumes, the sweep, the adjoint, paper scale).  The L2 cache is
+flushed (256 MiB write) before every timed step.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
 Under torchrun (N > 1) every rank runs an independent replica of the workload (the single-plume
@@ -66,12 +68,13 @@ ADJ_STEPS, ADJ_CKPT = 400, 40
 def adjoint_plume():
     return inputs.Plume(dim=2, side=512, h_over_dx=1.3, alpha_L=ADJ_THETA[0], alpha_T=ADJ_THETA[1],
                         D_m=ADJ_THETA[2], name="2d-512^2-h1.3dx-adjoint-400steps")
-DEFAULT_WORKLOAD = "ladder-1024-n120-r10"
+DEFAULT_WORKLOAD = "cube-128-h2"
 METRIC = "particle-pair interactions/s"
 UNIT = "interactions/s"
 
 # Minimum FP32-pipe instructions per in-support ordered pair of the uniform-D Wendland C2 term
-# (2D: 16, 3D: 22); the derivation is in the design doc.  The ALU roof is
+# (2D: 16, 3D: 22: separation, r^2, r, 1 - q, the kernel shape, the quadratic form of Eq. 5 over
+# r^2, the weight, C_a - C_b and the accumulation).  The ALU roof is
 # SMs x 128 FP32 lanes x clock / I_MIN pairs per second.
 I_MIN = {2: 16, 3: 22}
 # Velocity-field pair term (per-particle D, harmonic means, convective term): minimum FP32-pipe

@@ -372,9 +372,14 @@ void ade_sweep_destroy(ade_sweep *sw);
  *   positions and C_dev [n] (inputs); nc_host [dim] cells per axis, product <= ADE_NOALLOC_MAX_CELLS.
  *   Outputs: perm_dev [n] caller index at each sorted position, cell_start_dev [ncells + 1],
  *   sorted_dev [n] 16-byte records {x, y, z (0 in 2D), C bits} in sorted order.
+ *   Alignment: sorted_dev 16 bytes; xq_dev, C_dev, perm_dev and cell_start_dev 4 bytes.  A
+ *   misaligned pointer returns ADE_ERR_ARG before any GPU work.
  * Larger sizes return ADE_ERR_CAPACITY without touching the GPU.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls share the array and it keeps the last call's
+ * call before any stream capture.  The address is cached per device together with the driver's ID
+ * of the context it was taken in; a call made in another context (after cudaDeviceReset, or after
+ * another library replaced the primary context) looks it up again, so make such a call outside
+ * stream capture too.  All calls share the array and it keeps the last call's
  * contents (the per-cell counters are cleared by every call): calls that overlap on the GPU race,
  * so order them on one stream.  Work is enqueued on `stream`; the call does not wait. */
 #define ADE_NOALLOC_MAX_PARTICLES 1048576

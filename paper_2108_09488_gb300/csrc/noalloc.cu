@@ -13,6 +13,7 @@
 // counters are cleared at the start of every call.  Two calls whose work overlaps on the GPU
 // (different streams, or different host threads, on the same device) race on the array: the
 // caller must order them.
+#include <cuda.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -38,12 +39,49 @@ constexpr size_t kScratchWords = kOffBlockSums + round_words(kMaxScanBlocks);
 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kScratchWords];
 
-// Device address of g_noalloc_scratch, looked up once per device with that device current.
+// Device address of g_noalloc_scratch, looked up once per device with that device current.  A
+// context reset (cudaDeviceReset, or another library destroying the primary context) reloads the
+// module and may move the array, so each entry remembers the context it was taken in, by the
+// driver's context ID (unique for the life of the process), and the address is looked up again
+// when the current context is a different one.
 constexpr int kMaxDevices = 64;
-uint32_t *g_scratch_addr[kMaxDevices] = {nullptr};
+struct ScratchEntry {
+    unsigned long long ctx_id;
+    uint32_t *addr;
+};
+ScratchEntry g_scratch[kMaxDevices] = {};
 std::mutex g_scratch_mutex;
 
 int noalloc_fail(int code, const char *msg) { return ade::report_error(code, msg); }
+
+// The driver's ID of the calling thread's current context (0 if it cannot be read).  The driver
+// entry points are fetched through the runtime, so the library does not link libcuda.
+unsigned long long current_context_id()
+{
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void *f0 = nullptr, *f1 = nullptr;
+        cudaDriverEntryPointQueryResult q0, q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q0 == cudaDriverEntryPointSuccess && q1 == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<GetCurrent>(f0);
+            get_id = reinterpret_cast<GetId>(f1);
+        }
+        looked_up = true;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, &id) == CUDA_SUCCESS)
+        return id;
+    return 0;
+}
+
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 }  // namespace
 
@@ -67,6 +105,11 @@ extern "C" int ade_build_cells_noalloc(int dim, int n, const uint32_t *xq_dev, c
         return noalloc_fail(ADE_ERR_CAPACITY, "cell count exceeds ADE_NOALLOC_MAX_CELLS (1048576)");
     if (!cell_start_dev || (n > 0 && (!xq_dev || !C_dev || !perm_dev || !sorted_dev)))
         return noalloc_fail(ADE_ERR_ARG, "NULL buffer");
+    // the kernels store 16-byte records and 4-byte words through these pointers
+    if (!aligned(sorted_dev, 16))
+        return noalloc_fail(ADE_ERR_ARG, "sorted_dev must be 16-byte aligned");
+    if (!aligned(perm_dev, 4) || !aligned(cell_start_dev, 4) || !aligned(xq_dev, 4) || !aligned(C_dev, 4))
+        return noalloc_fail(ADE_ERR_ARG, "xq_dev, C_dev, perm_dev and cell_start_dev must be 4-byte aligned");
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
@@ -74,13 +117,17 @@ extern "C" int ade_build_cells_noalloc(int dim, int n, const uint32_t *xq_dev, c
     uint32_t *scratch;
     {
         std::lock_guard<std::mutex> lock(g_scratch_mutex);
-        if (!g_scratch_addr[dev]) {
+        ScratchEntry &ent = g_scratch[dev];
+        unsigned long long id = current_context_id();
+        if (!ent.addr || id == 0 || id != ent.ctx_id) {
+            // set-up: the runtime binds the device's context to this thread if none is current
             void *p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p) return noalloc_fail(ADE_ERR_CUDA, "cudaGetSymbolAddress failed");
-            g_scratch_addr[dev] = static_cast<uint32_t *>(p);
+            ent.addr = static_cast<uint32_t *>(p);
+            ent.ctx_id = id ? id : current_context_id();
         }
-        scratch = g_scratch_addr[dev];
+        scratch = ent.addr;
     }
 
     ade::Work w;

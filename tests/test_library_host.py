@@ -348,3 +348,16 @@ def test_checkpoint_format_and_validation(adelib):
         assert e.value.code == -1 and "parameters" in str(e.value)
     finally:
         adelib.destroy(other)
+
+
+@pytest.mark.parametrize("which", ["sorted", "perm", "cell_start", "xq", "C"])
+def test_noalloc_rejects_misaligned_buffers(adelib, which):
+    """ade_build_cells_noalloc refuses a misaligned buffer before any GPU work: the sorted records
+    are stored as 16-byte words, the other buffers as 4-byte words."""
+    ptrs = {"xq": FAKE, "C": FAKE + (1 << 30), "perm": FAKE + (2 << 30),
+            "cell_start": FAKE + (3 << 30), "sorted": FAKE + (4 << 30)}
+    ptrs[which] += 8 if which == "sorted" else 2
+    with pytest.raises(adelib.AdeError) as e:
+        adelib.build_cells_noalloc(2, 100, ptrs["xq"], ptrs["C"], [8, 8], ptrs["perm"],
+                                   ptrs["cell_start"], ptrs["sorted"])
+    assert e.value.code == -1 and "aligned" in str(e.value)

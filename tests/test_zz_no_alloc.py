@@ -2,9 +2,11 @@
 
 Callers that cannot allocate device memory (or hand the library a workspace) use this entry
 point; its scratch lives in a static device array shared by every call.  These tests call it
-through the C ABI twice in a row on different problems, so the second call runs on scratch the
-first call left behind, and compare each result with ade_build_cells bit for bit (the outputs are
-integers and bit patterns).  The file is collected last on purpose.
+through the C ABI several times in a row on different problems, so every call after the first
+runs on scratch an earlier call left behind (with fewer cells, then more cells, than the call
+before), and compare each result bit for bit (the outputs are integers and bit patterns) with
+ade_build_cells or, where no context fits the grid, with the oracle's cell list.  The file is
+collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -50,6 +52,49 @@ def test_noalloc_matches_workspace_build_two_calls(adelib, torch_cuda):
             assert np.array_equal(srt[:, d], xq[d][perm_ref])
         assert np.array_equal(srt[:, 3], C.view(np.uint32)[perm_ref])
         sim.close()
+
+
+def _noalloc_raw(lib, torch, dim, xq, C, nc):
+    n = xq.shape[1]
+    ncells = int(np.prod(nc[:dim]))
+    xq_d = torch.from_numpy(np.ascontiguousarray(xq).view(np.int32)).cuda()
+    C_d = torch.from_numpy(np.ascontiguousarray(C)).cuda()
+    perm = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    cs = torch.full((ncells + 1,), -1, dtype=torch.int32, device="cuda")
+    srt = torch.zeros((n, 4), dtype=torch.int32, device="cuda")
+    lib.build_cells_noalloc(dim, n, xq_d.data_ptr(), C_d.data_ptr(), list(nc), perm.data_ptr(),
+                            cs.data_ptr(), srt.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return (perm.cpu().numpy().view(np.uint32), cs.cpu().numpy().view(np.uint32),
+            srt.cpu().numpy().view(np.uint32))
+
+
+def _check_against_oracle(orc, dim, xq, C, nc, perm, cs, srt):
+    key = orc.cell_keys(xq, nc)
+    perm_ref, cs_ref = orc.sort_cells(key, int(np.prod(nc[:dim])))
+    assert np.array_equal(perm, perm_ref)
+    assert np.array_equal(cs, cs_ref)
+    for d in range(dim):
+        assert np.array_equal(srt[:, d], xq[d][perm_ref])
+    assert np.array_equal(srt[:, 3], C.view(np.uint32)[perm_ref])
+
+
+def test_noalloc_capacity_limits_then_coarse_grid(adelib, orc, torch_cuda):
+    """Two more calls in a row on the shared scratch: one at exactly ADE_NOALLOC_MAX_PARTICLES
+    particles and ADE_NOALLOC_MAX_CELLS cells (more cells than any call before it, so its scratch
+    offsets reach the end of the array), then one with about 64 particles per cell, which takes
+    the one-block-per-cell ordering path; both bit for bit against the oracle's cell list."""
+    torch = torch_cuda
+    n = adelib.NOALLOC_MAX_PARTICLES
+    rng = np.random.default_rng(11)
+    xq = rng.integers(0, 2 ** 32, size=(2, n), dtype=np.uint64).astype(np.uint32)
+    C = rng.random(n, dtype=np.float32)
+    nc = [1024, adelib.NOALLOC_MAX_CELLS // 1024]
+    _check_against_oracle(orc, 2, xq, C, nc, *_noalloc_raw(adelib, torch, 2, xq, C, nc))
+    plume = inputs.Plume(dim=2, side=512, h_over_dx=1.3, jitter=0.3, seed=3)
+    xq2, C2 = plume.initial_state()
+    nc2 = [64, 64]                      # 262144 particles in 4096 cells
+    _check_against_oracle(orc, 2, xq2, C2, nc2, *_noalloc_raw(adelib, torch, 2, xq2, C2, nc2))
 
 
 def test_noalloc_rejects_oversize(adelib, torch_cuda):
