@@ -62,9 +62,13 @@ struct RateParams {
     float H2;        // support radius squared
     float invH;      // 1 / support radius
     float sy, sz;    // L_y / L_x, L_z / L_x (1 for a cubic box)
-    float Kc[6];     // Gamma (K - K_last I) with K = 2 D (uniform D): xx, yy, zz, 2xy, 2xz, 2yz,
-                     // K_last = K_yy in 2D and K_zz in 3D (so Kc[1] = 0 in 2D, Kc[2] = 0 in 3D)
-    float c0;        // Gamma K_last - tr K
+    // Pair factor of Eq. 5 for the uniform tensor of Eq. 3 (K = 2D): Dcal = a (vhat . e)^2 + b with
+    // e = x_ab / r, a = 2 Gamma (alpha_L - alpha_T)|v|, b = 2 (Gamma - dim) d_T - 2 (alpha_L - alpha_T)|v|,
+    // d_T = alpha_T |v| + D_m.  The walks evaluate t = (uw . x_ab) / r with uw = sqrt(|a|) vhat and
+    // Dcal' = t^2 + ub, ub = sign(a) b, so Dcal = sign(a) Dcal'; the sign is folded into upf.
+    float uw[3];
+    float ub;
+    float upf;       // sign(a) * pf
     float pf;        // 1/2 (m / rho) * kernel prefactor of W'(r)/r
     float dt;        // step length used by the epilogue
     uint32_t inc[3]; // fixed-point position increment used by the epilogue
@@ -80,6 +84,8 @@ struct RateParams {
     double H2d;      // FP64 support radius squared (pair counting decides support in FP64)
     int goff;        // batched plumes: first particle (caller and sorted order) of this plume
     int coff;        // batched plumes: first cell of this plume in the global cell table
+    const uint4 *pencil;  // trimmed walks: per pencil (cy, cz) the transverse bounding box
+                          // {min y, max y, min z, max z} of its particles at the cell build
 };
 
 // Velocity-field mode: per-particle velocities (Eq. 1) and tensors (Eq. 3).
@@ -161,6 +167,7 @@ struct Work {
     uint32_t *cell_start;  // [ncells + 1]
     uint4 *P0;             // [n] sorted {x, y, z, C} at level l
     uint4 *P1;             // [n] sorted state at level l + 1/2
+    uint4 *pencil = nullptr;  // [ncy * ncz] transverse bounding boxes of the pencils (NULL: not built)
     double *partials;      // per-block reduction partials (state statistics)
     float4 *wpart;         // per-warp partials of the corrector (EpiOut::wpart)
     double *stats;         // {sum C, min C, max C, -, closed-form slots}
@@ -182,6 +189,10 @@ int report_error(int code, const char *msg);
 
 // Pair-factor constants Kc[6], c0 of a uniform dispersion tensor D (dim x dim, Eq. 5, K = 2D).
 void pair_coeffs(int dim, double gamma, const double *D, float *Kc, float *c0);
+// The interaction walks' form of the same factor for the tensor of Eq. 3 (RateParams uw, ub, upf;
+// pf must be set first).
+void rate_pair_consts(int dim, double gamma, const double *v, double alpha_L, double alpha_T, double D_m,
+                      RateParams *rp);
 
 // Launchers (cells.cu, rate.cu, reduce.cu).  All return cudaGetLastError() of the launches.
 int scan_blocks(int m);

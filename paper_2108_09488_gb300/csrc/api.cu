@@ -305,12 +305,14 @@ void choose_tiles(int dim, int n, const Grid &g, bool iso, unsigned flags, ade::
 
 struct Layout {
     size_t keys, rank, count, block_sums, perm_tmp, perm, cell_start, P0, P1, partials, wpart, stats,
-        cf_partials, status, pairs, fVc, fDAc, fDBc, fIncC, fV, fDA, fDB, fInc, fbits, Q, Qh, total;
+        cf_partials, status, pairs, pencil, fVc, fDAc, fDBc, fIncC, fV, fDA, fDB, fInc, fbits, Q, Qh, total;
 };
 
 // field_dim: 0 for a uniform velocity, else dim (velocity-field buffers are added at the end).
-// nw_partials: per-warp corrector partials of the widest rate launch.
-Layout layout(int n, int ncells, int nb_partials, int nw_partials, int field_dim = 0, bool catt = false)
+// nw_partials: per-warp corrector partials of the widest rate launch.  npencils: pencil boxes of
+// the trimmed walks (0: none).
+Layout layout(int n, int ncells, int nb_partials, int nw_partials, int field_dim = 0, bool catt = false,
+              int npencils = 0)
 {
     Layout L;
     size_t off = 0;
@@ -334,6 +336,7 @@ Layout layout(int n, int ncells, int nb_partials, int nw_partials, int field_dim
     L.cf_partials = take((size_t)3 * (nb_partials > 0 ? nb_partials : 1) * 8);
     L.status = take(64);
     L.pairs = take(64);
+    L.pencil = npencils > 0 ? take((size_t)npencils * 16) : 0;
     L.fVc = L.fDAc = L.fDBc = L.fIncC = L.fV = L.fDA = L.fDB = L.fInc = L.fbits = 0;
     if (field_dim) {
         const size_t rec = (size_t)n * 16, rec3 = field_dim == 3 ? (size_t)n * 16 : 16;
@@ -366,6 +369,7 @@ struct Derived {
     int nb_partials;
     int nw_partials;
     int ncells_cap;
+    int pencils_cap;     // pencils (ncy * ncz) of the largest grid the context may use
     ade::RateParams tiles;
     Layout L;
 };
@@ -400,12 +404,14 @@ int derive(const ade_params *p, int n, Derived *d)
     if (nbt > d->nb_partials) d->nb_partials = nbt;
     d->nw_partials = std::max(nbr * (ade::kRateThreads / 32), ade::rate_launch_warps(p->dim, d->tiles, iso));
     int ncells_cap = d->g.ncells;
+    int pencils_cap = d->g.ncells / d->g.nc[0];
     if (p->cell_subdiv == 0 && p->flags == 0u) {
         // automatic grid: size the workspace for every configuration the autotuner may pick
         for (int k = 1; k <= ade::kMaxSubdiv; ++k) {
             Grid g;
             if (!make_grid(*p, d->Hgrid, k, &g)) continue;
             ncells_cap = std::max(ncells_cap, g.ncells);
+            pencils_cap = std::max(pencils_cap, g.ncells / g.nc[0]);
             ade::RateParams t;
             memset(&t, 0, sizeof(t));
             t.n = n;
@@ -415,7 +421,10 @@ int derive(const ade_params *p, int n, Derived *d)
         }
     }
     d->ncells_cap = ncells_cap;
-    d->L = layout(n, ncells_cap, d->nb_partials, d->nw_partials, p->vmax > 0.0 ? p->dim : 0, p->tau > 0.0);
+    // pencil boxes serve the trimmed walks of the uniform-velocity kernels
+    d->pencils_cap = p->vmax > 0.0 ? 0 : pencils_cap;
+    d->L = layout(n, ncells_cap, d->nb_partials, d->nw_partials, p->vmax > 0.0 ? p->dim : 0, p->tau > 0.0,
+                  d->pencils_cap);
     return ADE_OK;
 }
 
@@ -630,8 +639,8 @@ int plume_constants(const ade_params *p, int n, const Derived &d, double *D, dou
     *iso = p->box[1] == p->box[0] && (p->dim == 2 || p->box[2] == p->box[0]);
     const double gamma = p->gamma > 0.0 ? p->gamma : p->dim + 2.0;
     const int dm = p->dim;
-    ade::pair_coeffs(dm, gamma, D, rp.Kc, &rp.c0);
     rp.pf = (float)(0.5 * (p->mass / p->rho) * kernel_kc(p->kernel, dm, d.H));
+    ade::rate_pair_consts(dm, gamma, p->v, p->alpha_L, p->alpha_T, p->D_m, &rp);
     rp.variant = d.tiles.variant == 1 ? 1 : ((p->flags & ADE_FLAG_BRANCHED) ? 2 : 0);
     if (rp.variant != 1 && (p->flags & ADE_FLAG_TRIMMED)) rp.variant = rp.variant == 2 ? 4 : 3;  // trimmed rows
     if (p->flags & ADE_FLAG_PAIRED)                                                           // paired walks
@@ -671,6 +680,29 @@ void ade::pair_coeffs(int dm, double gamma, const double *D, float *Kc, float *c
     Kc[4] = dm == 3 ? (float)(2.0 * gamma * K(0, 2)) : 0.0f;
     Kc[5] = dm == 3 ? (float)(2.0 * gamma * K(1, 2)) : 0.0f;
     *c0 = (float)(gamma * Klast - trK);
+}
+
+// Eq. 3 gives D = d_T I + (d_L - d_T) vhat vhat^T with d_T = alpha_T |v| + D_m, d_L = alpha_L |v| + D_m;
+// with K = 2D, Eq. 5's Gamma e^T K e - tr K = a (vhat . e)^2 + b, a = 2 Gamma (d_L - d_T),
+// b = 2 (Gamma - dim) d_T - 2 (d_L - d_T).  The walks use uw = sqrt|a| vhat, ub = sign(a) b and
+// upf = sign(a) pf (v = 0: vhat is the x axis and a = 0).
+void ade::rate_pair_consts(int dm, double gamma, const double *v, double alpha_L, double alpha_T, double D_m,
+                           RateParams *rp)
+{
+    double sp = 0.0;
+    for (int i = 0; i < dm; ++i) sp += v[i] * v[i];
+    sp = sqrt(sp);
+    const double dT = alpha_T * sp + D_m, dLT = (alpha_L - alpha_T) * sp;
+    const double a = 2.0 * gamma * dLT;
+    const double b = 2.0 * (gamma - dm) * dT - 2.0 * dLT;
+    const double sa = a < 0.0 ? -1.0 : 1.0;
+    const double ra = sqrt(fabs(a));
+    for (int i = 0; i < 3; ++i) {
+        const double vh = sp > 0.0 ? (i < dm ? v[i] / sp : 0.0) : (i == 0 ? 1.0 : 0.0);
+        rp->uw[i] = (float)(ra * vh);
+    }
+    rp->ub = (float)(sa * b);
+    rp->upf = (float)(sa * (double)rp->pf);
 }
 
 int ade::report_error(int code, const char *msg) { return fail(code, "%s", msg); }
@@ -735,12 +767,14 @@ int ade_init_particles(ade_ctx **out, const ade_params *p, int n, uint32_t *xq_d
     c->w.cf_partials = at<double>(workspace_dev, d.L.cf_partials);
     c->w.status = at<int>(workspace_dev, d.L.status);
     c->w.pairs = at<unsigned long long>(workspace_dev, d.L.pairs);
+    c->w.pencil = d.pencils_cap > 0 ? at<uint4>(workspace_dev, d.L.pencil) : nullptr;
 
     rc = plume_constants(p, n, d, c->D, &c->dt, c->inc, c->inc_half, &c->rp, &c->iso);
     if (rc) {
         delete c;
         return rc;
     }
+    c->rp.pencil = c->w.pencil;
     c->Hgrid = d.Hgrid;
     c->skin = d.skin;
     c->field = p->vmax > 0.0;
@@ -965,7 +999,7 @@ int ade_set_dispersivity(ade_ctx *c, double alpha_L, double alpha_T, double D_m)
     c->p.D_m = D_m;
     dispersion_tensor(c->dim, c->p.v, alpha_L, alpha_T, D_m, c->D);
     const double gamma = c->p.gamma > 0.0 ? c->p.gamma : c->dim + 2.0;
-    ade::pair_coeffs(c->dim, gamma, c->D, c->rp.Kc, &c->rp.c0);
+    ade::rate_pair_consts(c->dim, gamma, c->p.v, alpha_L, alpha_T, D_m, &c->rp);
     if (c->field) {
         c->fp.aL = alpha_L;
         c->fp.aT = alpha_T;

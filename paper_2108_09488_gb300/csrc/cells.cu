@@ -17,6 +17,10 @@
 //             the whole warp instead, each element placed at its rank among the cell's indices;
 //             grids averaging 16 or more particles per cell use k_order_block (one block per cell,
 //             the same ranking spread over 256 threads)
+//             and, for the trimmed interaction walks, reduces the bounding box of every pencil
+//             (the cells of one (cy, cz) row along x) over the transverse coordinates of its
+//             particles: a warp reduces its cells by pencil and the first lane of each pencil
+//             segment merges the result with atomic min / max (k_count resets the boxes)
 // The result is the stable order (key, caller index) regardless of the order the atomics took,
 // so the permutation and cell table are identical on every run and bit-exact against a stable
 // counting sort.
@@ -44,11 +48,14 @@ __global__ __launch_bounds__(kThreads) void k_count(const uint32_t *__restrict__
                                                     int ncx, int ncy, int ncz,
                                                     uint32_t *__restrict__ keys,
                                                     uint32_t *__restrict__ rank,
-                                                    uint32_t *__restrict__ count)
+                                                    uint32_t *__restrict__ count,
+                                                    uint4 *__restrict__ pencil, int npencils)
 {
     pdl_wait();
     pdl_trigger();
     const int i = blockIdx.x * kThreads + threadIdx.x;
+    if (pencil)   // empty boxes {min y, max y, min z, max z}: k_order merges into them
+        for (int q = i; q < npencils; q += gridDim.x * kThreads) pencil[q] = make_uint4(0xffffffffu, 0u, 0xffffffffu, 0u);
     if (i >= n) return;
     const uint32_t key = cell_key(xq, n, i, dim, ncx, ncy, ncz);
     keys[i] = key;
@@ -207,9 +214,67 @@ __device__ __forceinline__ void cswap(uint32_t &a, uint32_t &b)
     b = hi;
 }
 
+// Transverse bounding box of one cell's (or a set of cells') particles in fixed-point units:
+// {min y, max y, min z, max z} (z stays empty in 2D).  The cell interval along each axis does not
+// wrap, so plain unsigned min / max are well defined.
+struct Box {
+    uint32_t ylo = 0xffffffffu, yhi = 0u, zlo = 0xffffffffu, zhi = 0u;
+    __device__ __forceinline__ void add(const uint4 &r)
+    {
+        ylo = min(ylo, r.y);
+        yhi = max(yhi, r.y);
+        zlo = min(zlo, r.z);
+        zhi = max(zhi, r.z);
+    }
+    __device__ __forceinline__ void merge(const Box &o)
+    {
+        ylo = min(ylo, o.ylo);
+        yhi = max(yhi, o.yhi);
+        zlo = min(zlo, o.zlo);
+        zhi = max(zhi, o.zhi);
+    }
+};
+
+__device__ __forceinline__ Box shfl_down_box(const Box &b, int o)
+{
+    Box r;
+    r.ylo = __shfl_down_sync(0xffffffffu, b.ylo, o);
+    r.yhi = __shfl_down_sync(0xffffffffu, b.yhi, o);
+    r.zlo = __shfl_down_sync(0xffffffffu, b.zlo, o);
+    r.zhi = __shfl_down_sync(0xffffffffu, b.zhi, o);
+    return r;
+}
+
+// Merges the warp's per-cell boxes into their pencils.  Lane l holds cell c (pencil c / ncx, or
+// none when c >= ncells); consecutive lanes hold consecutive cells, so the lanes of one pencil form
+// one contiguous segment.  A segmented shuffle reduction leaves each segment's box in its first
+// lane, which merges it with one atomic min / max per word.  Every lane of the warp must call it.
+__device__ __forceinline__ void merge_pencils(int c, int ncells, int ncx, Box b, uint4 *__restrict__ pencil)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned p = c < ncells ? (unsigned)(c / ncx) : 0xffffffffu;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned p2 = __shfl_down_sync(0xffffffffu, p, o);
+        const Box b2 = shfl_down_box(b, o);
+        if (lane + o < 32 && p2 == p) b.merge(b2);
+    }
+    const unsigned pprev = __shfl_up_sync(0xffffffffu, p, 1);
+    if (p != 0xffffffffu && (lane == 0 || pprev != p) && b.ylo <= b.yhi) {
+        unsigned *w = reinterpret_cast<unsigned *>(pencil + p);
+        atomicMin(w + 0, b.ylo);
+        atomicMax(w + 1, b.yhi);
+        if (b.zlo <= b.zhi) {
+            atomicMin(w + 2, b.zlo);
+            atomicMax(w + 3, b.zhi);
+        }
+    }
+}
+
 template <class Rec>
 __device__ __forceinline__ void order_small_cell(uint32_t s, uint32_t e, const uint32_t *__restrict__ perm_tmp,
-                                                 uint32_t *__restrict__ perm, uint4 *__restrict__ P, Rec rec)
+                                                 uint32_t *__restrict__ perm, uint4 *__restrict__ P, Rec rec,
+                                                 Box *box = nullptr)
 {
     const uint32_t m = e - s;
     if (m <= 4) {
@@ -227,6 +292,12 @@ __device__ __forceinline__ void order_small_cell(uint32_t s, uint32_t e, const u
         if (m > 1) r1 = rec(v1);
         if (m > 2) r2 = rec(v2);
         if (m > 3) r3 = rec(v3);
+        if (box) {
+            box->add(r0);
+            box->add(r1);
+            box->add(r2);
+            box->add(r3);
+        }
         perm[s] = v0;
         P[s] = r0;
         if (m > 1) {
@@ -256,7 +327,9 @@ __device__ __forceinline__ void order_small_cell(uint32_t s, uint32_t e, const u
     }
     for (uint32_t k = 0; k < m; ++k) {
         perm[s + k] = a[k];
-        P[s + k] = rec(a[k]);
+        const uint4 r = rec(a[k]);
+        if (box) box->add(r);
+        P[s + k] = r;
     }
 }
 
@@ -268,7 +341,8 @@ __device__ __forceinline__ void order_small_cell(uint32_t s, uint32_t e, const u
 template <class Rec>
 __device__ __forceinline__ void order_big_cells(bool big, uint32_t s, uint32_t e,
                                                 const uint32_t *__restrict__ perm_tmp,
-                                                uint32_t *__restrict__ perm, uint4 *__restrict__ P, Rec rec)
+                                                uint32_t *__restrict__ perm, uint4 *__restrict__ P, Rec rec,
+                                                Box *box = nullptr)
 {
     const int lane = threadIdx.x & 31;
     unsigned todo = __ballot_sync(0xffffffffu, big);
@@ -276,6 +350,7 @@ __device__ __forceinline__ void order_big_cells(bool big, uint32_t s, uint32_t e
         const int l = __ffs(todo) - 1;
         todo &= todo - 1u;
         const uint32_t bs = __shfl_sync(0xffffffffu, s, l), be = __shfl_sync(0xffffffffu, e, l);
+        Box cb;   // this big cell's box, gathered over the lanes and handed to lane l
         for (uint32_t k0 = bs; k0 < be; k0 += 32) {
             const uint32_t k = k0 + (uint32_t)lane;
             const bool has = k < be;
@@ -288,8 +363,17 @@ __device__ __forceinline__ void order_big_cells(bool big, uint32_t s, uint32_t e
             }
             if (has && bs + rank < be) {
                 perm[bs + rank] = v;
-                P[bs + rank] = rec(v);
+                const uint4 r = rec(v);
+                cb.add(r);
+                P[bs + rank] = r;
             }
+        }
+        if (box) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cb.merge(shfl_down_box(cb, o));
+            const Box c0{__shfl_sync(0xffffffffu, cb.ylo, 0), __shfl_sync(0xffffffffu, cb.yhi, 0),
+                         __shfl_sync(0xffffffffu, cb.zlo, 0), __shfl_sync(0xffffffffu, cb.zhi, 0)};
+            if (lane == l) box->merge(c0);
         }
     }
 }
@@ -315,7 +399,8 @@ __global__ __launch_bounds__(kThreads) void k_order(const uint32_t *__restrict__
                                                     const uint32_t *__restrict__ xq,
                                                     const float *__restrict__ C, int n, int dim,
                                                     uint32_t *__restrict__ perm,
-                                                    uint4 *__restrict__ P)
+                                                    uint4 *__restrict__ P, int ncx,
+                                                    uint4 *__restrict__ pencil)
 {
     pdl_wait();
     pdl_trigger();
@@ -327,8 +412,11 @@ __global__ __launch_bounds__(kThreads) void k_order(const uint32_t *__restrict__
     }
     const bool valid = e > s && e <= (uint32_t)n;
     const PlainRec rec{xq, C, n, dim};
-    if (valid && e - s <= kSmallCell) order_small_cell(s, e, perm_tmp, perm, P, rec);
-    order_big_cells(valid && e - s > kSmallCell, s, e, perm_tmp, perm, P, rec);
+    Box box;
+    Box *bp = pencil ? &box : nullptr;
+    if (valid && e - s <= kSmallCell) order_small_cell(s, e, perm_tmp, perm, P, rec, bp);
+    order_big_cells(valid && e - s > kSmallCell, s, e, perm_tmp, perm, P, rec, bp);
+    if (pencil) merge_pencils(c, ncells, ncx, box, pencil);
 }
 
 // One block per cell, for grids whose cells hold many particles on average (wide kernels, coarse
@@ -341,16 +429,19 @@ __global__ __launch_bounds__(kThreads) void k_order_block(const uint32_t *__rest
                                                           const uint32_t *__restrict__ perm_tmp,
                                                           const uint32_t *__restrict__ xq,
                                                           const float *__restrict__ C, int n, int dim,
-                                                          uint32_t *__restrict__ perm, uint4 *__restrict__ P)
+                                                          uint32_t *__restrict__ perm, uint4 *__restrict__ P,
+                                                          int ncx, uint4 *__restrict__ pencil)
 {
     pdl_wait();
     pdl_trigger();
     __shared__ uint32_t chunk[kRankChunk];
+    __shared__ Box wbox[kThreads / 32];
     const int c = blockIdx.x;
     if (c >= ncells) return;
     const uint32_t s = __ldg(start + c), e = __ldg(start + c + 1);
     if (e <= s || e > (uint32_t)n) return;                       // uniform over the block
     const PlainRec rec{xq, C, n, dim};
+    Box box;
     for (uint32_t k0 = s; k0 < e; k0 += kThreads * kRankItems) {
         uint32_t v[kRankItems], rank[kRankItems];
 #pragma unroll
@@ -375,7 +466,28 @@ __global__ __launch_bounds__(kThreads) void k_order_block(const uint32_t *__rest
             const uint32_t k = k0 + threadIdx.x + r * kThreads;
             if (k < e && s + rank[r] < e) {
                 perm[s + rank[r]] = v[r];
-                P[s + rank[r]] = rec(v[r]);
+                const uint4 q = rec(v[r]);
+                box.add(q);
+                P[s + rank[r]] = q;
+            }
+        }
+    }
+    if (pencil) {   // block reduction of the cell's box, one merge into its pencil
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) box.merge(shfl_down_box(box, o));
+        if ((threadIdx.x & 31) == 0) wbox[threadIdx.x >> 5] = box;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            Box b = wbox[0];
+            for (int w = 1; w < kThreads / 32; ++w) b.merge(wbox[w]);
+            unsigned *pw = reinterpret_cast<unsigned *>(pencil + c / ncx);
+            if (b.ylo <= b.yhi) {
+                atomicMin(pw + 0, b.ylo);
+                atomicMax(pw + 1, b.yhi);
+            }
+            if (b.zlo <= b.zhi) {
+                atomicMin(pw + 2, b.zlo);
+                atomicMax(pw + 3, b.zhi);
             }
         }
     }
@@ -478,7 +590,8 @@ cudaError_t launch_build_cells(int dim, const uint32_t *xq, const float *C, int 
     if (e != cudaSuccess) return e;
     const int nb = (n + kThreads - 1) / kThreads;
     if (nb > 0 && e == cudaSuccess)
-        e = launch_pdl(k_count, nb, kThreads, 0, s, xq, n, dim, nc[0], nc[1], nc[2], w.keys, w.rank, w.count);
+        e = launch_pdl(k_count, nb, kThreads, 0, s, xq, n, dim, nc[0], nc[1], nc[2], w.keys, w.rank, w.count,
+                       w.pencil, ncells / nc[0]);
     const int sb = scan_blocks(ncells);
     if (e == cudaSuccess) e = launch_pdl(k_scan_blocks, sb, kThreads, 0, s, w.count, ncells, w.block_sums);
     if (sb <= kScanFoldBlocks) {
@@ -494,10 +607,10 @@ cudaError_t launch_build_cells(int dim, const uint32_t *xq, const float *C, int 
         if (e != cudaSuccess) return e;
         if ((long long)n >= 16ll * ncells)   // many particles per cell: one block per cell
             e = launch_pdl(k_order_block, ncells, kThreads, 0, s, w.cell_start, ncells, w.perm_tmp, xq, C, n,
-                           dim, w.perm, w.P0);
+                           dim, w.perm, w.P0, nc[0], w.pencil);
         else
             e = launch_pdl(k_order, (ncells + kThreads - 1) / kThreads, kThreads, 0, s, w.cell_start, ncells,
-                           w.perm_tmp, xq, C, n, dim, w.perm, w.P0);
+                           w.perm_tmp, xq, C, n, dim, w.perm, w.P0, nc[0], w.pencil);
     }
     return e;
 }

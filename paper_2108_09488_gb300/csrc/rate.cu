@@ -3,9 +3,10 @@
 //
 // For a uniform velocity field (Sec. 3) every particle carries the same tensor D (Eq. 3), so the
 // per-component harmonic mean of Eq. 5 is 4 D D / (D + D) = 2 D and the pair factor reduces to
-//     Dcal_ab = Gamma x_ab^T K x_ab / r^2 - tr K,   K = 2 D,
-// evaluated as x^T (Gamma K - Gamma K_last I) x / r^2 + (Gamma K_last - tr K), K_last = K_yy in
-// 2D and K_zz in 3D, which drops one diagonal term from the per-pair work.
+//     Dcal_ab = Gamma e^T K e - tr K = a (vhat . e)^2 + b,   K = 2 D, e = x_ab / r,
+// a = 2 Gamma (alpha_L - alpha_T)|v|, b = 2 (Gamma - dim)(alpha_T |v| + D_m) - 2 (alpha_L - alpha_T)|v|
+// (D = d_T I + (d_L - d_T) vhat vhat^T): one dot product, one product with 1/r and one fused
+// multiply-add per pair, t = (sqrt|a| vhat . x_ab) / r, Dcal = sign(a) (t^2 + sign(a) b).
 // With grad_a W = W'(r) x_ab / r, the dispersive term of Eq. 4 for one ordered pair is
 //     1/2 (m_b / rhobar) Dcal_ab (C_a - C_b) W'(r) / r,
 // and W'(r)/r = kc f(q): Wendland C2 (support H = 2h): f = (1-q)^3, kc = -20 B / H^2;
@@ -246,16 +247,16 @@ __global__ __launch_bounds__(kTileThreads, 2) void k_rate_tiled(const uint4 *__r
                     const float dz = DIM == 3 ? (float)(a.z - q.z) : 0.f;
                     float r2 = fmaf(dx, dx, dy * dy);
                     if (DIM == 3) r2 = fmaf(dz, dz, r2);
-                    const float rinv = rsqrtf(fmaxf(r2, 1.0f));
+                    const float rinv = rsqrt_ftz(fmaxf(r2, 1.0f));
                     const float omq = fmaxf(fmaf(-r2 * rinv, kc.invH, 1.f), 0.f);
-                    const float s = dcal<DIM>(dx, dy, dz, rinv * rinv, kc);
+                    const float s = dcal<DIM>(dx, dy, dz, rinv, kc);
                     const float w = r2 > 0.f ? shape<KERNEL>(omq) * s : 0.f;
                     rs = fmaf(w, Ca - __int_as_float(q.w), rs);
                     if (COUNT) cnt += in_support_fp64<DIM>(a.x - q.x, a.y - q.y, a.z - q.z, prm);
                 }
                 neumaier_add(sum, comp, rs);
             }
-            rate = prm.pf * (sum + comp);
+            rate = prm.upf * (sum + comp);
         } else {
             rate = rate_direct<DIM, KERNEL, true, COUNT>(Pe, cs, pe, cx, cy, cz, prm, cnt);
         }

@@ -4,6 +4,15 @@
 // C).  Included inside an unnamed namespace of ade.
 #pragma once
 
+// 1/sqrt(x) from the special-function unit with subnormal inputs flushed to zero.  The walks take
+// it of r^2 in fixed-point units, which is 0 (the particle itself) or at least 1, never subnormal.
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ void neumaier_add(float &sum, float &comp, float x)
 {
     float t = sum + x;

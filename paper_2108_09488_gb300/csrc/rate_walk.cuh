@@ -22,29 +22,41 @@ __device__ __forceinline__ unsigned in_support_fp64(int ix, int iy, int iz, cons
 // Per-pair constants, copied into registers once per particle (the parameter block may live in
 // shared or constant memory).
 struct PairConst {
-    float H2, invH, sy, sz, c0;
-    float K0, K1, K3, K4, K5;
+    float H2, invH, sy, sz;
+    float w0, w1, w2, b;
     template <class P>
     __device__ __forceinline__ explicit PairConst(const P &prm)
-        : H2(prm.H2), invH(prm.invH), sy(prm.sy), sz(prm.sz), c0(prm.c0), K0(prm.Kc[0]),
-          K1(prm.Kc[1]), K3(prm.Kc[3]), K4(prm.Kc[4]), K5(prm.Kc[5])
+        : H2(prm.H2), invH(prm.invH), sy(prm.sy), sz(prm.sz), w0(prm.uw[0]), w1(prm.uw[1]), w2(prm.uw[2]),
+          b(prm.ub)
     {
     }
 };
 
-// Dcal factor of the pair (without the kernel shape): x^T Kc x / r^2 + c0.
+// Pair factor of Eq. 5 up to the sign folded into upf: with uniform D (Eq. 3) the harmonic mean is
+// K = 2D and Gamma e^T K e - tr K = a (vhat . e)^2 + b; here t = (sqrt|a| vhat . x) / r and the
+// factor is t^2 + sign(a) b.  rinv = 1 / r.
 template <int DIM>
-__device__ __forceinline__ float dcal(float dx, float dy, float dz, float rinv2, const PairConst &k)
+__device__ __forceinline__ float dcal(float dx, float dy, float dz, float rinv, const PairConst &k)
 {
-    float Q;
-    if (DIM == 2) {
-        Q = dx * fmaf(k.K0, dx, k.K3 * dy);
-    } else {
-        float qx = fmaf(k.K0, dx, fmaf(k.K3, dy, k.K4 * dz));
-        float qy = fmaf(k.K1, dy, k.K5 * dz);
-        Q = fmaf(dx, qx, dy * qy);
+    float u = fmaf(k.w0, dx, k.w1 * dy);
+    if (DIM == 3) u = fmaf(k.w2, dz, u);
+    const float t = u * rinv;
+    return fmaf(t, t, k.b);
+}
+
+// Lower bound, in fixed-point units of the x axis, of the transverse distance from a target at
+// build-relative coordinates (ya, za) to any particle of a pencil with box bb = {min y, max y,
+// min z, max z} (also build-relative); squared.  Differences are taken as int32 (minimum image).
+template <int DIM>
+__device__ __forceinline__ float pencil_gap2(const uint4 &bb, uint32_t ya, uint32_t za, float sy, float sz)
+{
+    const float ey = (float)max(max((int)(bb.x - ya), (int)(ya - bb.y)), 0) * sy;
+    float e2 = ey * ey;
+    if (DIM == 3) {
+        const float ez = (float)max(max((int)(bb.z - za), (int)(za - bb.w)), 0) * sz;
+        e2 = fmaf(ez, ez, e2);
     }
-    return fmaf(Q, rinv2, k.c0);
+    return e2;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -81,15 +93,15 @@ __device__ __forceinline__ void pair_range_direct(const uint4 *__restrict__ P, i
         float r2 = fmaf(dx, dx, dy * dy);
         if (DIM == 3) r2 = fmaf(dz, dz, r2);
         if (BF) {
-            const float rinv = rsqrtf(r2);
+            const float rinv = rsqrt_ftz(r2);
             const float omq = fmaxf(fmaf(-(r2 * rinv), k.invH, 1.f), 0.f);
-            const float sr = dcal<DIM>(dx, dy, dz, rinv * rinv, k);
+            const float sr = dcal<DIM>(dx, dy, dz, rinv, k);
             const float s = ZS ? fmaxf(sr, -3.402823466e38f) : sr;
             rs = fmaf(shape<KERNEL>(omq) * s, Ca - __uint_as_float(pb.w), rs);
         } else if (r2 < k.H2 && r2 > 0.f) {
-            const float rinv = rsqrtf(r2);
+            const float rinv = rsqrt_ftz(r2);
             const float omq = fmaf(-(r2 * rinv), k.invH, 1.f);
-            const float s = dcal<DIM>(dx, dy, dz, rinv * rinv, k);
+            const float s = dcal<DIM>(dx, dy, dz, rinv, k);
             rs = fmaf(shape<KERNEL>(omq) * s, Ca - __uint_as_float(pb.w), rs);
         }
     }
@@ -108,39 +120,21 @@ __device__ float rate_direct(const uint4 *__restrict__ Pe, const uint32_t *__res
     float acc = 0.f, comp = 0.f;
     // Per-particle trimming of the stencil (TRIM).  The stencil row (dy, dz, w) holds every
     // neighbour of any point of the cell; for this particle only the cells within H of its own
-    // position are
-    // needed.  Its fractional position in its build cell is the low word of x nc (umulhi gives the
-    // cell, the low 32 bits the offset within it exactly), so the row's distance e (in x-axis
-    // units) and the x cell range [floor(f_x - xe), floor(f_x + xe)], xe = sqrt(H^2 - e^2) / width,
-    // follow in FP32.  The radius is widened by 2^-12 H (far above the FP32 rounding of these
-    // bounds), so a skipped candidate lies beyond H by more than the evaluation's rounding and its
-    // term is exactly 0: the sums are bitwise those of the full stencil.
+    // position are needed.  The row's pencil box (the transverse extent of the particles in that
+    // y-z row of cells at the cell build) bounds the transverse distance e from below, so rows with
+    // e >= H are skipped, and the x cell range shrinks to [floor(f_x - xe), floor(f_x + xe)],
+    // xe = sqrt(H^2 - e^2) / width, f_x the particle's fractional cell coordinate (the low word of
+    // x nc: umulhi gives the cell, the low 32 bits the offset within it exactly).  The radius is
+    // widened by 2^-12 H (far above the FP32 rounding of these bounds), so a skipped candidate lies
+    // beyond H by more than the evaluation's rounding and its term is exactly 0: the sums are
+    // bitwise those of the full stencil.
     const float two32 = 4294967296.f;
     const float fx = (float)((pa.x - prm.back[0]) * (uint32_t)ncx) * (1.f / two32);
-    const float fy = (float)((pa.y - prm.back[1]) * (uint32_t)ncy) * (1.f / two32);
-    const float fz = DIM == 3 ? (float)((pa.z - prm.back[2]) * (uint32_t)ncz) * (1.f / two32) : 0.f;
+    const uint32_t ya = pa.y - prm.back[1], za = pa.z - prm.back[2];
     const float inv_wx = (float)ncx * (1.f / two32);              // cells per x unit
-    const float chy = two32 / (float)ncy * kc.sy, chz = DIM == 3 ? two32 / (float)ncz * kc.sz : 0.f;
     const float Hm2 = kc.H2 * (1.f + 1.f / 2048.f);                // (H (1 + 2^-12))^2, rounded up
     for (int ri = 0; ri < nrows; ++ri) {
         const StencilRow row = prm.rows[ri];
-        float e2 = 0.f;
-        if (TRIM) {
-            const float ey = fmaxf(fmaxf((float)row.dy - fy, fy - (float)(row.dy + 1)), 0.f) * chy;
-            e2 = ey * ey;
-            if (DIM == 3) {
-                const float ez = fmaxf(fmaxf((float)row.dz - fz, fz - (float)(row.dz + 1)), 0.f) * chz;
-                e2 = fmaf(ez, ez, e2);
-            }
-        }
-        int dlo = -(int)row.w, dhi = row.w;
-        if (TRIM) {
-            if (!(e2 < Hm2)) continue;                              // the whole row is out of reach
-            const float t = Hm2 - e2;
-            const float xe = t * rsqrtf(t) * inv_wx + 1.f / 4096.f;  // half-extent in cells
-            dlo = max(__float2int_rd(fx - xe), dlo);
-            dhi = min(__float2int_rd(fx + xe), dhi);
-        }
         int yy = cy + row.dy;
         yy += (yy < 0) ? ncy : 0;
         yy -= (yy >= ncy) ? ncy : 0;
@@ -149,6 +143,17 @@ __device__ float rate_direct(const uint4 *__restrict__ Pe, const uint32_t *__res
             zz = cz + row.dz;
             zz += (zz < 0) ? ncz : 0;
             zz -= (zz >= ncz) ? ncz : 0;
+        }
+        int dlo = -(int)row.w, dhi = row.w;
+        if (TRIM) {
+            const uint4 bb = __ldg(prm.pencil + (zz * ncy + yy));
+            if (bb.x > bb.y) continue;                              // empty pencil
+            const float e2 = pencil_gap2<DIM>(bb, ya, za, kc.sy, kc.sz);
+            if (!(e2 < Hm2)) continue;                              // the whole row is out of reach
+            const float t = Hm2 - e2;
+            const float xe = t * rsqrt_ftz(t) * inv_wx + 1.f / 4096.f;  // half-extent in cells
+            dlo = max(__float2int_rd(fx - xe), dlo);
+            dhi = min(__float2int_rd(fx + xe), dhi);
         }
         const int base = (zz * ncy + yy) * ncx;
         const int lo = cx + dlo, hi = cx + dhi + 1;
@@ -177,7 +182,7 @@ __device__ float rate_direct(const uint4 *__restrict__ Pe, const uint32_t *__res
         }
         neumaier_add(acc, comp, rs);
     }
-    return prm.pf * (acc + comp);
+    return prm.upf * (acc + comp);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -204,15 +209,23 @@ __device__ __forceinline__ float2 shape2(float2 omq)
 
 // Packed per-pair constants (both halves equal).
 struct PairConst2 {
-    float2 K0, K1, K3, K4, K5, c0, ninvH, sy, sz;
+    float2 w0, w1, w2, b, ninvH, sy, sz;
     float H2;
     __device__ __forceinline__ explicit PairConst2(const PairConst &k)
-        : K0(f2(k.K0, k.K0)), K1(f2(k.K1, k.K1)), K3(f2(k.K3, k.K3)), K4(f2(k.K4, k.K4)),
-          K5(f2(k.K5, k.K5)), c0(f2(k.c0, k.c0)), ninvH(f2(-k.invH, -k.invH)), sy(f2(k.sy, k.sy)),
-          sz(f2(k.sz, k.sz)), H2(k.H2)
+        : w0(f2(k.w0, k.w0)), w1(f2(k.w1, k.w1)), w2(f2(k.w2, k.w2)), b(f2(k.b, k.b)),
+          ninvH(f2(-k.invH, -k.invH)), sy(f2(k.sy, k.sy)), sz(f2(k.sz, k.sz)), H2(k.H2)
     {
     }
 };
+
+template <int DIM>
+__device__ __forceinline__ float2 dcal2(float2 dx, float2 dy, float2 dz, float2 rinv, const PairConst2 &k)
+{
+    float2 u = __ffma2_rn(k.w0, dx, __fmul2_rn(k.w1, dy));
+    if (DIM == 3) u = __ffma2_rn(k.w2, dz, u);
+    const float2 t = __fmul2_rn(u, rinv);
+    return __ffma2_rn(t, t, k.b);
+}
 
 // BF = false: the branched form -- the term is evaluated when either target is in support
 // (0 < r^2 < H^2), each half with the operations of pair_range_direct<BF = false>, and a half
@@ -238,34 +251,18 @@ __device__ __forceinline__ void pair_range_direct2(const uint4 *__restrict__ P, 
         if (!BF) {
             const bool in0 = r2.x < k.H2 && r2.x > 0.f, in1 = r2.y < k.H2 && r2.y > 0.f;
             if (in0 || in1) {
-                const float2 rinv = f2(rsqrtf(r2.x), rsqrtf(r2.y));
+                const float2 rinv = f2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
                 const float2 omq = __ffma2_rn(__fmul2_rn(r2, rinv), k.ninvH, f2(1.f, 1.f));
-                float2 Q;
-                if (DIM == 2) {
-                    Q = __fmul2_rn(dx, __ffma2_rn(k.K0, dx, __fmul2_rn(k.K3, dy)));
-                } else {
-                    const float2 qx = __ffma2_rn(k.K0, dx, __ffma2_rn(k.K3, dy, __fmul2_rn(k.K4, dz)));
-                    const float2 qy = __ffma2_rn(k.K1, dy, __fmul2_rn(k.K5, dz));
-                    Q = __ffma2_rn(dx, qx, __fmul2_rn(dy, qy));
-                }
-                const float2 w = __fmul2_rn(shape2<KERNEL>(omq), __ffma2_rn(Q, __fmul2_rn(rinv, rinv), k.c0));
+                const float2 w = __fmul2_rn(shape2<KERNEL>(omq), dcal2<DIM>(dx, dy, dz, rinv, k));
                 const float nCb = -__uint_as_float(pb.w);
                 rs = __ffma2_rn(f2(in0 ? w.x : 0.f, in1 ? w.y : 0.f), __fadd2_rn(Ca, f2(nCb, nCb)), rs);
             }
             continue;
         }
-        const float2 rinv = f2(rsqrtf(r2.x), rsqrtf(r2.y));
+        const float2 rinv = f2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
         const float2 om = __ffma2_rn(__fmul2_rn(r2, rinv), k.ninvH, f2(1.f, 1.f));
         const float2 omq = f2(fmaxf(om.x, 0.f), fmaxf(om.y, 0.f));
-        float2 Q;
-        if (DIM == 2) {
-            Q = __fmul2_rn(dx, __ffma2_rn(k.K0, dx, __fmul2_rn(k.K3, dy)));
-        } else {
-            const float2 qx = __ffma2_rn(k.K0, dx, __ffma2_rn(k.K3, dy, __fmul2_rn(k.K4, dz)));
-            const float2 qy = __ffma2_rn(k.K1, dy, __fmul2_rn(k.K5, dz));
-            Q = __ffma2_rn(dx, qx, __fmul2_rn(dy, qy));
-        }
-        const float2 sr = __ffma2_rn(Q, __fmul2_rn(rinv, rinv), k.c0);
+        const float2 sr = dcal2<DIM>(dx, dy, dz, rinv, k);
         const float2 sc = ZS ? f2(fmaxf(sr.x, -3.402823466e38f), fmaxf(sr.y, -3.402823466e38f)) : sr;
         const float nCb = -__uint_as_float(pb.w);
         rs = __ffma2_rn(__fmul2_rn(shape2<KERNEL>(omq), sc), __fadd2_rn(Ca, f2(nCb, nCb)), rs);
@@ -287,34 +284,34 @@ __device__ void rate_direct_pair(const uint4 *__restrict__ Pe, const uint32_t *_
     const float two32 = 4294967296.f;
     const float fx0 = (float)((pa0.x - prm.back[0]) * (uint32_t)ncx) * (1.f / two32);
     const float fx1 = (float)((pa1.x - prm.back[0]) * (uint32_t)ncx) * (1.f / two32);
-    const float fy0 = (float)((pa0.y - prm.back[1]) * (uint32_t)ncy) * (1.f / two32);
-    const float fy1 = (float)((pa1.y - prm.back[1]) * (uint32_t)ncy) * (1.f / two32);
-    const float fz0 = DIM == 3 ? (float)((pa0.z - prm.back[2]) * (uint32_t)ncz) * (1.f / two32) : 0.f;
-    const float fz1 = DIM == 3 ? (float)((pa1.z - prm.back[2]) * (uint32_t)ncz) * (1.f / two32) : 0.f;
+    const uint32_t ya0 = pa0.y - prm.back[1], za0 = pa0.z - prm.back[2];
+    const uint32_t ya1 = pa1.y - prm.back[1], za1 = pa1.z - prm.back[2];
     const float inv_wx = (float)ncx * (1.f / two32);
-    const float chy = two32 / (float)ncy * kc.sy, chz = DIM == 3 ? two32 / (float)ncz * kc.sz : 0.f;
     const float Hm2 = kc.H2 * (1.f + 1.f / 2048.f);
     for (int ri = 0; ri < nrows; ++ri) {
         const StencilRow row = prm.rows[ri];
+        int yy = cy + row.dy;
+        yy += (yy < 0) ? ncy : 0;
+        yy -= (yy >= ncy) ? ncy : 0;
+        int zz = 0;
+        if (DIM == 3) {
+            zz = cz + row.dz;
+            zz += (zz < 0) ? ncz : 0;
+            zz -= (zz >= ncz) ? ncz : 0;
+        }
         int lo0 = cx0 - (int)row.w, hi0 = cx0 + row.w, lo1 = cx1 - (int)row.w, hi1 = cx1 + row.w;
         bool in0 = true, in1 = true;       // the target reaches the row (rate_direct does not skip it)
         bool ne0 = true, ne1 = true;       // ... and its cell range is not empty
         if (TRIM) {
-            float e0 = fmaxf(fmaxf((float)row.dy - fy0, fy0 - (float)(row.dy + 1)), 0.f) * chy;
-            float e1 = fmaxf(fmaxf((float)row.dy - fy1, fy1 - (float)(row.dy + 1)), 0.f) * chy;
-            e0 *= e0;
-            e1 *= e1;
-            if (DIM == 3) {
-                const float z0 = fmaxf(fmaxf((float)row.dz - fz0, fz0 - (float)(row.dz + 1)), 0.f) * chz;
-                const float z1 = fmaxf(fmaxf((float)row.dz - fz1, fz1 - (float)(row.dz + 1)), 0.f) * chz;
-                e0 = fmaf(z0, z0, e0);
-                e1 = fmaf(z1, z1, e1);
-            }
+            const uint4 bb = __ldg(prm.pencil + (zz * ncy + yy));
+            if (bb.x > bb.y) continue;      // empty pencil: rate_direct skips the row for both
+            const float e0 = pencil_gap2<DIM>(bb, ya0, za0, kc.sy, kc.sz);
+            const float e1 = pencil_gap2<DIM>(bb, ya1, za1, kc.sy, kc.sz);
             in0 = e0 < Hm2;
             in1 = e1 < Hm2;
             const float t0 = in0 ? Hm2 - e0 : 1.f, t1 = in1 ? Hm2 - e1 : 1.f;
-            const float xe0 = t0 * rsqrtf(t0) * inv_wx + 1.f / 4096.f;
-            const float xe1 = t1 * rsqrtf(t1) * inv_wx + 1.f / 4096.f;
+            const float xe0 = t0 * rsqrt_ftz(t0) * inv_wx + 1.f / 4096.f;
+            const float xe1 = t1 * rsqrt_ftz(t1) * inv_wx + 1.f / 4096.f;
             lo0 = cx0 + max(__float2int_rd(fx0 - xe0), -(int)row.w);
             hi0 = cx0 + min(__float2int_rd(fx0 + xe0), (int)row.w);
             lo1 = cx1 + max(__float2int_rd(fx1 - xe1), -(int)row.w);
@@ -337,15 +334,6 @@ __device__ void rate_direct_pair(const uint4 *__restrict__ Pe, const uint32_t *_
             if (in0) neumaier_add(acc0, comp0, 0.f);
             if (in1) neumaier_add(acc1, comp1, 0.f);
             continue;
-        }
-        int yy = cy + row.dy;
-        yy += (yy < 0) ? ncy : 0;
-        yy -= (yy >= ncy) ? ncy : 0;
-        int zz = 0;
-        if (DIM == 3) {
-            zz = cz + row.dz;
-            zz += (zz < 0) ? ncz : 0;
-            zz -= (zz >= ncz) ? ncz : 0;
         }
         const int base = (zz * ncy + yy) * ncx;
         int s0, e0, s1 = 0, e1 = 0;
@@ -375,8 +363,8 @@ __device__ void rate_direct_pair(const uint4 *__restrict__ Pe, const uint32_t *_
         if (in0) neumaier_add(acc0, comp0, rs.x);
         if (in1) neumaier_add(acc1, comp1, rs.y);
     }
-    r0 = prm.pf * (acc0 + comp0);
-    r1 = prm.pf * (acc1 + comp1);
+    r0 = prm.upf * (acc0 + comp0);
+    r1 = prm.upf * (acc1 + comp1);
 }
 
 // ---------------------------------------------------------------------------------------------
