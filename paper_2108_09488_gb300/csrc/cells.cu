@@ -18,9 +18,11 @@
 //             grids averaging 16 or more particles per cell use k_order_block (one block per cell,
 //             the same ranking spread over 256 threads)
 //             and, for the trimmed interaction walks, reduces the bounding box of every pencil
-//             (the cells of one (cy, cz) row along x) over the transverse coordinates of its
-//             particles: a warp reduces its cells by pencil and the first lane of each pencil
-//             segment merges the result with atomic min / max (k_count resets the boxes)
+//             (the cells of one (cy, cz) row along x) over the transverse positions of its
+//             particles, as fractions of a cell (FP32, so a walk bounds its distance to the row
+//             with FP32 arithmetic and no periodic wrap): a warp reduces its cells by pencil and
+//             the first lane of each pencil segment merges the result with atomic min / max on the
+//             bit patterns (non-negative floats order like their bits); k_count resets the boxes
 // The result is the stable order (key, caller index) regardless of the order the atomics took,
 // so the permutation and cell table are identical on every run and bit-exact against a stable
 // counting sort.
@@ -43,6 +45,7 @@ __device__ __forceinline__ uint32_t cell_key(const uint32_t *__restrict__ xq, in
 }
 
 constexpr int kThreads = 256;
+constexpr uint32_t kInfBits = 0x7f800000u;   // +inf: the lower bound of an empty pencil box
 
 __global__ __launch_bounds__(kThreads) void k_count(const uint32_t *__restrict__ xq, int n, int dim,
                                                     int ncx, int ncy, int ncz,
@@ -54,8 +57,8 @@ __global__ __launch_bounds__(kThreads) void k_count(const uint32_t *__restrict__
     pdl_wait();
     pdl_trigger();
     const int i = blockIdx.x * kThreads + threadIdx.x;
-    if (pencil)   // empty boxes {min y, max y, min z, max z}: k_order merges into them
-        for (int q = i; q < npencils; q += gridDim.x * kThreads) pencil[q] = make_uint4(0xffffffffu, 0u, 0xffffffffu, 0u);
+    if (pencil)   // empty boxes {min y, max y, min z, max z} = {+inf, 0, +inf, 0}: k_order merges into them
+        for (int q = i; q < npencils; q += gridDim.x * kThreads) pencil[q] = make_uint4(kInfBits, 0u, kInfBits, 0u);
     if (i >= n) return;
     const uint32_t key = cell_key(xq, n, i, dim, ncx, ncy, ncz);
     keys[i] = key;
@@ -214,17 +217,23 @@ __device__ __forceinline__ void cswap(uint32_t &a, uint32_t &b)
     b = hi;
 }
 
-// Transverse bounding box of one cell's (or a set of cells') particles in fixed-point units:
-// {min y, max y, min z, max z} (z stays empty in 2D).  The cell interval along each axis does not
-// wrap, so plain unsigned min / max are well defined.
+// Position of fixed-point coordinate q inside its cell as a fraction of the cell (FP32 bit
+// pattern): the low word of q nc is the offset within the cell in units of 2^-32 cells.
+__device__ __forceinline__ uint32_t cell_frac_bits(uint32_t q, uint32_t nc)
+{
+    return __float_as_uint((float)(q * nc) * 2.3283064365386963e-10f);
+}
+
+// Transverse bounding box of one cell's (or a set of cells') particles as cell fractions, FP32
+// bit patterns: {min y, max y, min z, max z}; z stays {0, 0} in 2D.
 struct Box {
-    uint32_t ylo = 0xffffffffu, yhi = 0u, zlo = 0xffffffffu, zhi = 0u;
-    __device__ __forceinline__ void add(const uint4 &r)
+    uint32_t ylo = kInfBits, yhi = 0u, zlo = kInfBits, zhi = 0u;
+    __device__ __forceinline__ void add(uint32_t fy, uint32_t fz)
     {
-        ylo = min(ylo, r.y);
-        yhi = max(yhi, r.y);
-        zlo = min(zlo, r.z);
-        zhi = max(zhi, r.z);
+        ylo = min(ylo, fy);
+        yhi = max(yhi, fy);
+        zlo = min(zlo, fz);
+        zhi = max(zhi, fz);
     }
     __device__ __forceinline__ void merge(const Box &o)
     {
@@ -232,6 +241,16 @@ struct Box {
         yhi = max(yhi, o.yhi);
         zlo = min(zlo, o.zlo);
         zhi = max(zhi, o.zhi);
+    }
+};
+
+// Accumulates records into a box (the cell counts along y and z give the fractions).
+struct BoxAcc {
+    Box *box;
+    uint32_t ncy, ncz;
+    __device__ __forceinline__ void operator()(const uint4 &r) const
+    {
+        if (box) box->add(cell_frac_bits(r.y, ncy), cell_frac_bits(r.z, ncz));
     }
 };
 
@@ -274,7 +293,7 @@ __device__ __forceinline__ void merge_pencils(int c, int ncells, int ncx, Box b,
 template <class Rec>
 __device__ __forceinline__ void order_small_cell(uint32_t s, uint32_t e, const uint32_t *__restrict__ perm_tmp,
                                                  uint32_t *__restrict__ perm, uint4 *__restrict__ P, Rec rec,
-                                                 Box *box = nullptr)
+                                                 BoxAcc acc = BoxAcc{nullptr, 0u, 0u})
 {
     const uint32_t m = e - s;
     if (m <= 4) {
@@ -292,11 +311,11 @@ __device__ __forceinline__ void order_small_cell(uint32_t s, uint32_t e, const u
         if (m > 1) r1 = rec(v1);
         if (m > 2) r2 = rec(v2);
         if (m > 3) r3 = rec(v3);
-        if (box) {
-            box->add(r0);
-            box->add(r1);
-            box->add(r2);
-            box->add(r3);
+        if (acc.box) {
+            acc(r0);
+            acc(r1);
+            acc(r2);
+            acc(r3);
         }
         perm[s] = v0;
         P[s] = r0;
@@ -328,7 +347,7 @@ __device__ __forceinline__ void order_small_cell(uint32_t s, uint32_t e, const u
     for (uint32_t k = 0; k < m; ++k) {
         perm[s + k] = a[k];
         const uint4 r = rec(a[k]);
-        if (box) box->add(r);
+        acc(r);
         P[s + k] = r;
     }
 }
@@ -342,7 +361,7 @@ template <class Rec>
 __device__ __forceinline__ void order_big_cells(bool big, uint32_t s, uint32_t e,
                                                 const uint32_t *__restrict__ perm_tmp,
                                                 uint32_t *__restrict__ perm, uint4 *__restrict__ P, Rec rec,
-                                                Box *box = nullptr)
+                                                BoxAcc acc = BoxAcc{nullptr, 0u, 0u})
 {
     const int lane = threadIdx.x & 31;
     unsigned todo = __ballot_sync(0xffffffffu, big);
@@ -364,16 +383,16 @@ __device__ __forceinline__ void order_big_cells(bool big, uint32_t s, uint32_t e
             if (has && bs + rank < be) {
                 perm[bs + rank] = v;
                 const uint4 r = rec(v);
-                cb.add(r);
+                if (acc.box) cb.add(cell_frac_bits(r.y, acc.ncy), cell_frac_bits(r.z, acc.ncz));
                 P[bs + rank] = r;
             }
         }
-        if (box) {
+        if (acc.box) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) cb.merge(shfl_down_box(cb, o));
             const Box c0{__shfl_sync(0xffffffffu, cb.ylo, 0), __shfl_sync(0xffffffffu, cb.yhi, 0),
                          __shfl_sync(0xffffffffu, cb.zlo, 0), __shfl_sync(0xffffffffu, cb.zhi, 0)};
-            if (lane == l) box->merge(c0);
+            if (lane == l) acc.box->merge(c0);
         }
     }
 }
@@ -399,7 +418,7 @@ __global__ __launch_bounds__(kThreads) void k_order(const uint32_t *__restrict__
                                                     const uint32_t *__restrict__ xq,
                                                     const float *__restrict__ C, int n, int dim,
                                                     uint32_t *__restrict__ perm,
-                                                    uint4 *__restrict__ P, int ncx,
+                                                    uint4 *__restrict__ P, int ncx, int ncy, int ncz,
                                                     uint4 *__restrict__ pencil)
 {
     pdl_wait();
@@ -413,9 +432,9 @@ __global__ __launch_bounds__(kThreads) void k_order(const uint32_t *__restrict__
     const bool valid = e > s && e <= (uint32_t)n;
     const PlainRec rec{xq, C, n, dim};
     Box box;
-    Box *bp = pencil ? &box : nullptr;
-    if (valid && e - s <= kSmallCell) order_small_cell(s, e, perm_tmp, perm, P, rec, bp);
-    order_big_cells(valid && e - s > kSmallCell, s, e, perm_tmp, perm, P, rec, bp);
+    const BoxAcc bacc{pencil ? &box : nullptr, (uint32_t)ncy, (uint32_t)ncz};
+    if (valid && e - s <= kSmallCell) order_small_cell(s, e, perm_tmp, perm, P, rec, bacc);
+    order_big_cells(valid && e - s > kSmallCell, s, e, perm_tmp, perm, P, rec, bacc);
     if (pencil) merge_pencils(c, ncells, ncx, box, pencil);
 }
 
@@ -430,7 +449,7 @@ __global__ __launch_bounds__(kThreads) void k_order_block(const uint32_t *__rest
                                                           const uint32_t *__restrict__ xq,
                                                           const float *__restrict__ C, int n, int dim,
                                                           uint32_t *__restrict__ perm, uint4 *__restrict__ P,
-                                                          int ncx, uint4 *__restrict__ pencil)
+                                                          int ncx, int ncy, int ncz, uint4 *__restrict__ pencil)
 {
     pdl_wait();
     pdl_trigger();
@@ -467,7 +486,7 @@ __global__ __launch_bounds__(kThreads) void k_order_block(const uint32_t *__rest
             if (k < e && s + rank[r] < e) {
                 perm[s + rank[r]] = v[r];
                 const uint4 q = rec(v[r]);
-                box.add(q);
+                if (pencil) box.add(cell_frac_bits(q.y, (uint32_t)ncy), cell_frac_bits(q.z, (uint32_t)ncz));
                 P[s + rank[r]] = q;
             }
         }
@@ -607,10 +626,10 @@ cudaError_t launch_build_cells(int dim, const uint32_t *xq, const float *C, int 
         if (e != cudaSuccess) return e;
         if ((long long)n >= 16ll * ncells)   // many particles per cell: one block per cell
             e = launch_pdl(k_order_block, ncells, kThreads, 0, s, w.cell_start, ncells, w.perm_tmp, xq, C, n,
-                           dim, w.perm, w.P0, nc[0], w.pencil);
+                           dim, w.perm, w.P0, nc[0], nc[1], nc[2], w.pencil);
         else
             e = launch_pdl(k_order, (ncells + kThreads - 1) / kThreads, kThreads, 0, s, w.cell_start, ncells,
-                           w.perm_tmp, xq, C, n, dim, w.perm, w.P0, nc[0], w.pencil);
+                           w.perm_tmp, xq, C, n, dim, w.perm, w.P0, nc[0], nc[1], nc[2], w.pencil);
     }
     return e;
 }

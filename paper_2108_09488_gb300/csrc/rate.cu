@@ -76,7 +76,9 @@ __global__ __launch_bounds__(kRateThreads) void k_rate(const uint4 *__restrict__
         a_pre = __ldg(perm + ii);
         if (a_pre - (uint32_t)prm.goff < (uint32_t)prm.n) C_pre = out.C[a_pre];
     }
-    const float rate = rate_direct<DIM, KERNEL, ISO, COUNT, BF, TRIM>(Pe, cs, pa, cx, cy, cz, prm, cnt);
+    __shared__ TrimRow srow[TRIM ? kMaxRows : 1];
+    if (TRIM) stage_trim_rows(srow, prm);
+    const float rate = rate_direct<DIM, KERNEL, ISO, COUNT, BF, TRIM>(Pe, cs, pa, cx, cy, cz, prm, cnt, srow);
     if (valid) {
         acc.cnt = cnt;
         epilogue<DIM, EPI, PRE>(i, rate, pa, perm, prm, out, acc, a_pre, C_pre);
@@ -248,15 +250,15 @@ __global__ __launch_bounds__(kTileThreads, 2) void k_rate_tiled(const uint4 *__r
                     float r2 = fmaf(dx, dx, dy * dy);
                     if (DIM == 3) r2 = fmaf(dz, dz, r2);
                     const float rinv = rsqrt_ftz(fmaxf(r2, 1.0f));
-                    const float omq = fmaxf(fmaf(-r2 * rinv, kc.invH, 1.f), 0.f);
+                    const float om = fmaf(-r2 * rinv, kc.invH, 1.f);
                     const float s = dcal<DIM>(dx, dy, dz, rinv, kc);
-                    const float w = r2 > 0.f ? shape<KERNEL>(omq) * s : 0.f;
+                    const float w = r2 > 0.f ? shape2x<KERNEL>(om + fabsf(om)) * s : 0.f;
                     rs = fmaf(w, Ca - __int_as_float(q.w), rs);
                     if (COUNT) cnt += in_support_fp64<DIM>(a.x - q.x, a.y - q.y, a.z - q.z, prm);
                 }
                 neumaier_add(sum, comp, rs);
             }
-            rate = prm.upf * (sum + comp);
+            rate = prm.upf * shape_unscale<KERNEL>() * (sum + comp);
         } else {
             rate = rate_direct<DIM, KERNEL, true, COUNT>(Pe, cs, pe, cx, cy, cz, prm, cnt);
         }

@@ -13,24 +13,41 @@ __device__ __forceinline__ float rsqrt_ftz(float x)
     return r;
 }
 
+// Compensated summation (Neumaier's scheme): sum += x, with the rounding error of that addition
+// accumulated in comp.  The error is taken with Knuth's branch-free two-sum, which yields exactly
+// (sum + x) - fl(sum + x), the same value as the magnitude-ordered form, in six FP32 additions.
 __device__ __forceinline__ void neumaier_add(float &sum, float &comp, float x)
 {
-    float t = sum + x;
-    if (fabsf(sum) >= fabsf(x))
-        comp += (sum - t) + x;
-    else
-        comp += (x - t) + sum;
+    const float t = sum + x;
+    const float bp = t - sum;
+    comp += (sum - (t - bp)) + (x - bp);
     sum = t;
 }
 
+// The walks clamp 1 - q at 0 as om + |om| = 2 max(om, 0) (one FP32 addition); the kernel shape
+// of twice the argument is an exact power-of-two multiple of the shape, undone once per particle.
+template <int KERNEL>
+__device__ __forceinline__ float shape_unscale()
+{
+    return KERNEL == ADE_WENDLAND_C2 ? 0.125f : 0.03125f;   // 1 / 2^3, 1 / 2^5
+}
+
 // Kernel shape factor f(q) with W'(r)/r = kc f(q); omq = 1 - q (clamped at 0 by the caller for the
-// branch-free form).
+// branch-free form).  shape2x takes 2 (1 - q) and returns 2^3 f (C2) or 2^5 f (C4) exactly.
 template <int KERNEL>
 __device__ __forceinline__ float shape(float omq)
 {
     if (KERNEL == ADE_WENDLAND_C2) return omq * omq * omq;
     float o2 = omq * omq;
     return o2 * o2 * omq * fmaf(-5.f, omq, 6.f);  // (1-q)^5 (1 + 5q), 1 + 5q = 6 - 5(1-q)
+}
+
+template <int KERNEL>
+__device__ __forceinline__ float shape2x(float w)
+{
+    if (KERNEL == ADE_WENDLAND_C2) return w * w * w;
+    float o2 = w * w;
+    return o2 * o2 * w * fmaf(-2.5f, w, 6.f);      // (2(1-q))^5 (6 - 5(1-q))
 }
 
 // Per-thread accumulators of the corrector's reductions: the sum of C as an unevaluated FP32 pair

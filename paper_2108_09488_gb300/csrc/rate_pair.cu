@@ -40,12 +40,14 @@ __global__ __launch_bounds__(kRateThreads, (BF && !TRIM) ? 10 : 0) void k_rate_p
     Acc acc{0.f, 0.f, __int_as_float(0x7f800000), __int_as_float(0xff800000), 0u};
     unsigned cnt = 0u;
     float r0, r1;
+    __shared__ TrimRow srow[TRIM ? kMaxRows : 1];
+    if (TRIM) stage_trim_rows(srow, prm);
     const bool paired = v1 && can_pair(cx0, cy0, cz0, cx1, cy1, cz1, prm.ncx);
     if (paired) {
-        rate_direct_pair<DIM, KERNEL, ISO, TRIM, BF>(Pe, cs, pa0, pa1, cx0, cx1, cy0, cz0, prm, r0, r1);
+        rate_direct_pair<DIM, KERNEL, ISO, TRIM, BF>(Pe, cs, pa0, pa1, cx0, cx1, cy0, cz0, prm, r0, r1, srow);
     } else {
-        r0 = rate_direct<DIM, KERNEL, ISO, false, BF, TRIM>(Pe, cs, pa0, cx0, cy0, cz0, prm, cnt);
-        r1 = v1 ? rate_direct<DIM, KERNEL, ISO, false, BF, TRIM>(Pe, cs, pa1, cx1, cy1, cz1, prm, cnt) : 0.f;
+        r0 = rate_direct<DIM, KERNEL, ISO, false, BF, TRIM>(Pe, cs, pa0, cx0, cy0, cz0, prm, cnt, srow);
+        r1 = v1 ? rate_direct<DIM, KERNEL, ISO, false, BF, TRIM>(Pe, cs, pa1, cx1, cy1, cz1, prm, cnt, srow) : 0.f;
     }
     if (v0) epilogue<DIM, EPI>(i0, r0, pa0, perm, prm, out, acc);
     if (v1) epilogue<DIM, EPI>(i1, r1, pa1, perm, prm, out, acc);

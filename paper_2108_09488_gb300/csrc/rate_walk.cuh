@@ -44,35 +44,160 @@ __device__ __forceinline__ float dcal(float dx, float dy, float dz, float rinv, 
     return fmaf(t, t, k.b);
 }
 
-// Lower bound, in fixed-point units of the x axis, of the transverse distance from a target at
-// build-relative coordinates (ya, za) to any particle of a pencil with box bb = {min y, max y,
-// min z, max z} (also build-relative); squared.  Differences are taken as int32 (minimum image).
-template <int DIM>
-__device__ __forceinline__ float pencil_gap2(const uint4 &bb, uint32_t ya, uint32_t za, float sy, float sz)
+// ---------------------------------------------------------------------------------------------
+// trimmed rows
+// ---------------------------------------------------------------------------------------------
+// Per-particle trimming of the stencil (walks with TRIM).  A stencil row (dy, dz, w) holds every
+// neighbour of any point of the cell; one particle needs only the cells within H of itself.  The
+// cell build records, per pencil (the cells of one (cy, cz) row along x), the transverse box of its
+// particles as fractions of a cell.  With the particle at fractions (f_y, f_z) of its own cell,
+// the pencil's particles lie at [dy + lo_y, dy + hi_y] cells from that cell's origin along y, so
+// the gap max(dy + lo_y - f_y, f_y - dy - hi_y, 0) (and along z) bounds the transverse distance e
+// from below, whatever the periodic wrap of the pencil index.  Rows with e >= H are skipped and
+// the x cell range shrinks to [floor(f_x - xe), floor(f_x + xe)], xe = sqrt(H^2 - e^2) / width.
+// The radius is widened by 2^-12 H (far above the FP32 rounding of these bounds), so a skipped
+// candidate lies beyond H by more than the evaluation's rounding and its term is exactly 0: the
+// sums are bitwise those of the full stencil.
+
+// One stencil row as the trimmed walks read it (staged in shared memory by the kernel): the offsets
+// as floats, the pencil-index offset dz ncy + dy (no wrap), and w | dy << 8 | dz << 16.
+struct TrimRow {
+    float fdy, fdz;
+    int off, wdd;
+};
+
+__device__ __forceinline__ void stage_trim_rows(TrimRow *srow, const RateParams &prm)
 {
-    const float ey = (float)max(max((int)(bb.x - ya), (int)(ya - bb.y)), 0) * sy;
+    for (int r = threadIdx.x; r < prm.nrows; r += blockDim.x) {
+        const StencilRow row = prm.rows[r];
+        TrimRow t;
+        t.fdy = (float)row.dy;
+        t.fdz = (float)row.dz;
+        t.off = (int)row.dz * prm.ncy + (int)row.dy;
+        t.wdd = ((int)row.w & 0xff) | (((int)row.dy & 0xff) << 8) | (((int)row.dz & 0xff) << 16);
+        srow[r] = t;
+    }
+    __syncthreads();
+}
+
+// Per-particle quantities of the trimming: fractional cell position (x, y, z), the index of the
+// particle's own pencil, and whether no stencil row of the particle's cell wraps along y or z.
+struct TrimSelf {
+    float fx, fy, fz;
+    int p0;
+    bool interior;
+};
+
+template <int DIM>
+__device__ __forceinline__ TrimSelf trim_self(const uint4 &pa, int cy, int cz, const RateParams &prm)
+{
+    const float inv32 = 2.3283064365386963e-10f;   // 2^-32
+    TrimSelf t;
+    t.fx = (float)((pa.x - prm.back[0]) * (uint32_t)prm.ncx) * inv32;
+    t.fy = (float)((pa.y - prm.back[1]) * (uint32_t)prm.ncy) * inv32;
+    t.fz = DIM == 3 ? (float)((pa.z - prm.back[2]) * (uint32_t)prm.ncz) * inv32 : 0.f;
+    t.p0 = cz * prm.ncy + cy;
+    t.interior = cy >= prm.k && cy < prm.ncy - prm.k && (DIM == 2 || (cz >= prm.k && cz < prm.ncz - prm.k));
+    return t;
+}
+
+// Pencil index of row r for a particle in pencil (cy, cz).
+template <int DIM>
+__device__ __forceinline__ int row_pencil(const TrimRow &r, const TrimSelf &me, int cy, int cz, const RateParams &prm)
+{
+    if (me.interior) return me.p0 + r.off;
+    int yy = cy + ((int)((unsigned)r.wdd << 16) >> 24);
+    yy += (yy < 0) ? prm.ncy : 0;
+    yy -= (yy >= prm.ncy) ? prm.ncy : 0;
+    int zz = 0;
+    if (DIM == 3) {
+        zz = cz + ((int)((unsigned)r.wdd << 8) >> 24);
+        zz += (zz < 0) ? prm.ncz : 0;
+        zz -= (zz >= prm.ncz) ? prm.ncz : 0;
+    }
+    return zz * prm.ncy + yy;
+}
+
+// Geometry shared by the rows: (H (1 + 2^-12))^2 rounded up in x-units^2, cells per x unit, and
+// half the y and z cell heights in x units (the gaps below are twice the gap in cells).
+struct TrimGeom {
+    float Hm2, inv_wx, hy, hz;
+    __device__ __forceinline__ explicit TrimGeom(const RateParams &prm)
+    {
+        const float two32 = 4294967296.f;
+        Hm2 = prm.H2 * (1.f + 1.f / 2048.f);
+        inv_wx = (float)prm.ncx * (1.f / two32);
+        hy = 0.5f * two32 / (float)prm.ncy * prm.sy;
+        hz = 0.5f * two32 / (float)prm.ncz * prm.sz;
+    }
+};
+
+// The x cell range [dlo, dhi] (relative to the particle's cell) of one row with pencil box bb for
+// one particle; false when the row is out of its reach.  2 gap = |lo - r| + |r - hi| - (hi - lo)
+// with r the particle's position relative to the row.
+template <int DIM>
+__device__ __forceinline__ bool trim_row(const float4 &bb, float wy, float wz, const TrimRow &r, int w,
+                                         const TrimSelf &me, const TrimGeom &g, int &dlo, int &dhi)
+{
+    const float ry = me.fy - r.fdy;
+    const float ey = ((fabsf(bb.x - ry) + fabsf(ry - bb.y)) - wy) * g.hy;
     float e2 = ey * ey;
     if (DIM == 3) {
-        const float ez = (float)max(max((int)(bb.z - za), (int)(za - bb.w)), 0) * sz;
+        const float rz = me.fz - r.fdz;
+        const float ez = ((fabsf(bb.z - rz) + fabsf(rz - bb.w)) - wz) * g.hz;
         e2 = fmaf(ez, ez, e2);
     }
-    return e2;
+    if (!(e2 < g.Hm2)) return false;
+    const float t = g.Hm2 - e2;
+    const float xe = fmaf(t * rsqrt_ftz(t), g.inv_wx, 1.f / 4096.f);   // half-extent in cells
+    dlo = max(__float2int_rd(me.fx - xe), -w);
+    dhi = min(__float2int_rd(me.fx + xe), w);
+    return true;
+}
+
+__device__ __forceinline__ float4 load_box(const RateParams &prm, int pidx)
+{
+    return __ldg(reinterpret_cast<const float4 *>(prm.pencil) + pidx);
+}
+
+// Candidate index ranges of cells [lo, hi) of the pencil row starting at cell `base` (two ranges
+// at a periodic seam).
+__device__ __forceinline__ void row_ranges(const uint32_t *__restrict__ cs, int base, int lo, int hi, int ncx,
+                                           int &s0, int &e0, int &s1, int &e1)
+{
+    s1 = e1 = 0;
+    if (lo < 0) {
+        s0 = __ldg(cs + base + lo + ncx);
+        e0 = __ldg(cs + base + ncx);
+        s1 = __ldg(cs + base);
+        e1 = __ldg(cs + base + hi);
+    } else if (hi > ncx) {
+        s0 = __ldg(cs + base + lo);
+        e0 = __ldg(cs + base + ncx);
+        s1 = __ldg(cs + base);
+        e1 = __ldg(cs + base + hi - ncx);
+    } else {
+        s0 = __ldg(cs + base + lo);
+        e0 = __ldg(cs + base + hi);
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
 // direct walk over global memory
 // ---------------------------------------------------------------------------------------------
 // One candidate range of the direct walk.  The evaluation is branch-free: outside the support
-// (1 - q) is clamped to 0, so the term is exactly 0; at zero separation (the particle itself, or a
-// coincident particle) rsqrt(0) = inf makes q and s NaN, and IEEE max-num (fmaxf returns the
-// non-NaN operand) turns them into (1 - q) = 0 and s = -FLT_MAX, so the weight is exactly 0 as
-// well.  In-support terms use the same operations as a branched evaluation, so adding the zero
-// terms leaves the sum unchanged.  The pair counter keeps an explicit FP64 test.
+// 1 - q is clamped to 0 (as om + |om| = 2 max(om, 0); the shape of twice the argument is an exact
+// power-of-two multiple, undone per particle), so the term is exactly 0; at zero separation (the
+// particle itself, or a coincident particle) rsqrt(0) = inf makes q and s NaN, and IEEE max-num
+// (fmaxf returns the non-NaN operand) turns them into 2 (1 - q) = 0 and s = -FLT_MAX, so the
+// weight is exactly 0 as well.  In-support terms use the same operations as a branched
+// evaluation, so adding the zero terms leaves the sum unchanged.  The pair counter keeps an
+// explicit FP64 test.
 // BF = false keeps the branch on r^2 < H^2 instead: a warp whose lanes all miss skips the term,
 // which pays off when warps are spatially coherent and the stencil is large (3D).
-// ZS = false drops the clamp of s: zero separation occurs only within the particle's own cell, so
-// rows other than the particle's own cell row (dy = dz = 0) never meet it, s is finite there and
-// the clamp changes nothing.
+// ZS = false drops both max-num clamps: zero separation occurs only within the particle's own
+// cell, so rows other than the particle's own cell row (dy = dz = 0) never meet it, q and s are
+// finite there and om + |om| clamps.
 template <int DIM, int KERNEL, bool ISO, bool COUNT, bool BF, bool ZS = true>
 __device__ __forceinline__ void pair_range_direct(const uint4 *__restrict__ P, int j0, int j1,
                                                   const uint4 &pa, float Ca, const PairConst &k,
@@ -94,45 +219,56 @@ __device__ __forceinline__ void pair_range_direct(const uint4 *__restrict__ P, i
         if (DIM == 3) r2 = fmaf(dz, dz, r2);
         if (BF) {
             const float rinv = rsqrt_ftz(r2);
-            const float omq = fmaxf(fmaf(-(r2 * rinv), k.invH, 1.f), 0.f);
+            const float om = fmaf(-(r2 * rinv), k.invH, 1.f);
+            const float omq2 = ZS ? fmaxf(om + om, 0.f) : om + fabsf(om);
             const float sr = dcal<DIM>(dx, dy, dz, rinv, k);
             const float s = ZS ? fmaxf(sr, -3.402823466e38f) : sr;
-            rs = fmaf(shape<KERNEL>(omq) * s, Ca - __uint_as_float(pb.w), rs);
+            rs = fmaf(shape2x<KERNEL>(omq2) * s, Ca - __uint_as_float(pb.w), rs);
         } else if (r2 < k.H2 && r2 > 0.f) {
             const float rinv = rsqrt_ftz(r2);
-            const float omq = fmaf(-(r2 * rinv), k.invH, 1.f);
+            const float om = fmaf(-(r2 * rinv), k.invH, 1.f);
             const float s = dcal<DIM>(dx, dy, dz, rinv, k);
-            rs = fmaf(shape<KERNEL>(omq) * s, Ca - __uint_as_float(pb.w), rs);
+            rs = fmaf(shape2x<KERNEL>(om + om) * s, Ca - __uint_as_float(pb.w), rs);
         }
     }
 }
 
 // Eq. 4 at one particle by the direct walk; (cx, cy, cz) is its cell.  TRIM: visit only the
-// stencil cells within reach of the particle itself (see below).
+// stencil cells within reach of the particle itself (rows from srow, staged by the kernel).
 template <int DIM, int KERNEL, bool ISO, bool COUNT, bool BF = true, bool TRIM = false>
 __device__ float rate_direct(const uint4 *__restrict__ Pe, const uint32_t *__restrict__ cs,
                              const uint4 &pa, int cx, int cy, int cz, const RateParams &prm,
-                             unsigned &cnt)
+                             unsigned &cnt, const TrimRow *srow = nullptr)
 {
     const int ncx = prm.ncx, ncy = prm.ncy, ncz = prm.ncz, nrows = prm.nrows;
     const PairConst kc(prm);
     const float Ca = __uint_as_float(pa.w);
     float acc = 0.f, comp = 0.f;
-    // Per-particle trimming of the stencil (TRIM).  The stencil row (dy, dz, w) holds every
-    // neighbour of any point of the cell; for this particle only the cells within H of its own
-    // position are needed.  The row's pencil box (the transverse extent of the particles in that
-    // y-z row of cells at the cell build) bounds the transverse distance e from below, so rows with
-    // e >= H are skipped, and the x cell range shrinks to [floor(f_x - xe), floor(f_x + xe)],
-    // xe = sqrt(H^2 - e^2) / width, f_x the particle's fractional cell coordinate (the low word of
-    // x nc: umulhi gives the cell, the low 32 bits the offset within it exactly).  The radius is
-    // widened by 2^-12 H (far above the FP32 rounding of these bounds), so a skipped candidate lies
-    // beyond H by more than the evaluation's rounding and its term is exactly 0: the sums are
-    // bitwise those of the full stencil.
-    const float two32 = 4294967296.f;
-    const float fx = (float)((pa.x - prm.back[0]) * (uint32_t)ncx) * (1.f / two32);
-    const uint32_t ya = pa.y - prm.back[1], za = pa.z - prm.back[2];
-    const float inv_wx = (float)ncx * (1.f / two32);              // cells per x unit
-    const float Hm2 = kc.H2 * (1.f + 1.f / 2048.f);                // (H (1 + 2^-12))^2, rounded up
+    if (TRIM) {
+        const TrimSelf me = trim_self<DIM>(pa, cy, cz, prm);
+        const TrimGeom g(prm);
+        for (int ri = 0; ri < nrows; ++ri) {
+            const TrimRow r = srow[ri];
+            const int pidx = row_pencil<DIM>(r, me, cy, cz, prm);
+            const float4 bb = load_box(prm, pidx);
+            if (!(bb.x <= bb.y)) continue;                          // empty pencil
+            int dlo, dhi;
+            if (!trim_row<DIM>(bb, bb.y - bb.x, bb.w - bb.z, r, r.wdd & 0xff, me, g, dlo, dhi))
+                continue;                                           // the whole row is out of reach
+            int s0, e0, s1, e1;
+            row_ranges(cs, pidx * ncx, cx + dlo, cx + dhi + 1, ncx, s0, e0, s1, e1);
+            float rs = 0.f;
+            if (r.off == 0) {                                       // the particle's own cell row
+                pair_range_direct<DIM, KERNEL, ISO, COUNT, BF, true>(Pe, s0, e0, pa, Ca, kc, prm, rs, cnt);
+                pair_range_direct<DIM, KERNEL, ISO, COUNT, BF, true>(Pe, s1, e1, pa, Ca, kc, prm, rs, cnt);
+            } else {
+                pair_range_direct<DIM, KERNEL, ISO, COUNT, BF, false>(Pe, s0, e0, pa, Ca, kc, prm, rs, cnt);
+                pair_range_direct<DIM, KERNEL, ISO, COUNT, BF, false>(Pe, s1, e1, pa, Ca, kc, prm, rs, cnt);
+            }
+            neumaier_add(acc, comp, rs);
+        }
+        return prm.upf * shape_unscale<KERNEL>() * (acc + comp);
+    }
     for (int ri = 0; ri < nrows; ++ri) {
         const StencilRow row = prm.rows[ri];
         int yy = cy + row.dy;
@@ -144,34 +280,8 @@ __device__ float rate_direct(const uint4 *__restrict__ Pe, const uint32_t *__res
             zz += (zz < 0) ? ncz : 0;
             zz -= (zz >= ncz) ? ncz : 0;
         }
-        int dlo = -(int)row.w, dhi = row.w;
-        if (TRIM) {
-            const uint4 bb = __ldg(prm.pencil + (zz * ncy + yy));
-            if (bb.x > bb.y) continue;                              // empty pencil
-            const float e2 = pencil_gap2<DIM>(bb, ya, za, kc.sy, kc.sz);
-            if (!(e2 < Hm2)) continue;                              // the whole row is out of reach
-            const float t = Hm2 - e2;
-            const float xe = t * rsqrt_ftz(t) * inv_wx + 1.f / 4096.f;  // half-extent in cells
-            dlo = max(__float2int_rd(fx - xe), dlo);
-            dhi = min(__float2int_rd(fx + xe), dhi);
-        }
-        const int base = (zz * ncy + yy) * ncx;
-        const int lo = cx + dlo, hi = cx + dhi + 1;
-        int s0, e0, s1 = 0, e1 = 0;
-        if (lo < 0) {
-            s0 = __ldg(cs + base + lo + ncx);
-            e0 = __ldg(cs + base + ncx);
-            s1 = __ldg(cs + base);
-            e1 = __ldg(cs + base + hi);
-        } else if (hi > ncx) {
-            s0 = __ldg(cs + base + lo);
-            e0 = __ldg(cs + base + ncx);
-            s1 = __ldg(cs + base);
-            e1 = __ldg(cs + base + hi - ncx);
-        } else {
-            s0 = __ldg(cs + base + lo);
-            e0 = __ldg(cs + base + hi);
-        }
+        int s0, e0, s1, e1;
+        row_ranges(cs, (zz * ncy + yy) * ncx, cx - (int)row.w, cx + row.w + 1, ncx, s0, e0, s1, e1);
         float rs = 0.f;
         if (row.dy == 0 && (DIM == 2 || row.dz == 0)) {      // the particle's own cell row
             pair_range_direct<DIM, KERNEL, ISO, COUNT, BF, true>(Pe, s0, e0, pa, Ca, kc, prm, rs, cnt);
@@ -182,7 +292,7 @@ __device__ float rate_direct(const uint4 *__restrict__ Pe, const uint32_t *__res
         }
         neumaier_add(acc, comp, rs);
     }
-    return prm.upf * (acc + comp);
+    return prm.upf * shape_unscale<KERNEL>() * (acc + comp);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -199,12 +309,12 @@ __device__ float rate_direct(const uint4 *__restrict__ Pe, const uint32_t *__res
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
 template <int KERNEL>
-__device__ __forceinline__ float2 shape2(float2 omq)
+__device__ __forceinline__ float2 shape2x2(float2 w)
 {
-    if (KERNEL == ADE_WENDLAND_C2) return __fmul2_rn(__fmul2_rn(omq, omq), omq);
-    const float2 o2 = __fmul2_rn(omq, omq);
-    const float2 t = __ffma2_rn(f2(-5.f, -5.f), omq, f2(6.f, 6.f));
-    return __fmul2_rn(__fmul2_rn(__fmul2_rn(o2, o2), omq), t);
+    if (KERNEL == ADE_WENDLAND_C2) return __fmul2_rn(__fmul2_rn(w, w), w);
+    const float2 o2 = __fmul2_rn(w, w);
+    const float2 t = __ffma2_rn(f2(-2.5f, -2.5f), w, f2(6.f, 6.f));
+    return __fmul2_rn(__fmul2_rn(__fmul2_rn(o2, o2), w), t);
 }
 
 // Packed per-pair constants (both halves equal).
@@ -230,13 +340,19 @@ __device__ __forceinline__ float2 dcal2(float2 dx, float2 dy, float2 dz, float2 
 // BF = false: the branched form -- the term is evaluated when either target is in support
 // (0 < r^2 < H^2), each half with the operations of pair_range_direct<BF = false>, and a half
 // whose target is not in support adds an exact zero.
-template <int DIM, int KERNEL, bool ISO, bool ZS, bool BF = true>
-__device__ __forceinline__ void pair_range_direct2(const uint4 *__restrict__ P, int j0, int j1,
+// The candidates are [s0, s0 + n0) followed by [s1, s1 + n1) (a row cut by the periodic seam of
+// the cell grid); MERGED walks both in one loop, so that a warp whose lanes cut rows at different
+// places keeps every lane busy, in the same candidate order as two loops.
+template <int DIM, int KERNEL, bool ISO, bool ZS, bool BF = true, bool MERGED = false>
+__device__ __forceinline__ void pair_range_direct2(const uint4 *__restrict__ P, int s0, int n0, int s1, int n1,
                                                    const uint4 &pa0, const uint4 &pa1, float2 Ca,
                                                    const PairConst2 &k, float2 &rs)
 {
+    const int nt = MERGED ? n0 + n1 : n0;
+    const int jump = s1 - (s0 + n0);
 #pragma unroll 4
-    for (int j = j0; j < j1; ++j) {
+    for (int t = 0; t < nt; ++t) {
+        const int j = s0 + t + (MERGED && t >= n0 ? jump : 0);
         const uint4 pb = __ldg(P + j);
         float2 dx = f2((float)(int)(pa0.x - pb.x), (float)(int)(pa1.x - pb.x));
         float2 dy = f2((float)(int)(pa0.y - pb.y), (float)(int)(pa1.y - pb.y));
@@ -252,8 +368,8 @@ __device__ __forceinline__ void pair_range_direct2(const uint4 *__restrict__ P, 
             const bool in0 = r2.x < k.H2 && r2.x > 0.f, in1 = r2.y < k.H2 && r2.y > 0.f;
             if (in0 || in1) {
                 const float2 rinv = f2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
-                const float2 omq = __ffma2_rn(__fmul2_rn(r2, rinv), k.ninvH, f2(1.f, 1.f));
-                const float2 w = __fmul2_rn(shape2<KERNEL>(omq), dcal2<DIM>(dx, dy, dz, rinv, k));
+                const float2 om = __ffma2_rn(__fmul2_rn(r2, rinv), k.ninvH, f2(1.f, 1.f));
+                const float2 w = __fmul2_rn(shape2x2<KERNEL>(__fadd2_rn(om, om)), dcal2<DIM>(dx, dy, dz, rinv, k));
                 const float nCb = -__uint_as_float(pb.w);
                 rs = __ffma2_rn(f2(in0 ? w.x : 0.f, in1 ? w.y : 0.f), __fadd2_rn(Ca, f2(nCb, nCb)), rs);
             }
@@ -261,110 +377,119 @@ __device__ __forceinline__ void pair_range_direct2(const uint4 *__restrict__ P, 
         }
         const float2 rinv = f2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
         const float2 om = __ffma2_rn(__fmul2_rn(r2, rinv), k.ninvH, f2(1.f, 1.f));
-        const float2 omq = f2(fmaxf(om.x, 0.f), fmaxf(om.y, 0.f));
+        const float2 omq2 = ZS ? f2(fmaxf(om.x + om.x, 0.f), fmaxf(om.y + om.y, 0.f))
+                               : f2(om.x + fabsf(om.x), om.y + fabsf(om.y));
         const float2 sr = dcal2<DIM>(dx, dy, dz, rinv, k);
         const float2 sc = ZS ? f2(fmaxf(sr.x, -3.402823466e38f), fmaxf(sr.y, -3.402823466e38f)) : sr;
         const float nCb = -__uint_as_float(pb.w);
-        rs = __ffma2_rn(__fmul2_rn(shape2<KERNEL>(omq), sc), __fadd2_rn(Ca, f2(nCb, nCb)), rs);
+        rs = __ffma2_rn(__fmul2_rn(shape2x2<KERNEL>(omq2), sc), __fadd2_rn(Ca, f2(nCb, nCb)), rs);
     }
 }
 
+// One row of the paired walks: the candidates [s0, e0) and [s1, e1).  Where no lane of the warp
+// meets the seam a single plain loop runs; otherwise every lane walks its two pieces in one loop.
+template <int DIM, int KERNEL, bool ISO, bool ZS, bool BF>
+__device__ __forceinline__ void pair_row2(const uint4 *__restrict__ P, int s0, int e0, int s1, int e1,
+                                          const uint4 &pa0, const uint4 &pa1, float2 Ca, const PairConst2 &k,
+                                          float2 &rs)
+{
+    const int n1 = e1 > s1 ? e1 - s1 : 0;
+    if (__any_sync(__activemask(), n1 > 0))
+        pair_range_direct2<DIM, KERNEL, ISO, ZS, BF, true>(P, s0, e0 - s0, s1, n1, pa0, pa1, Ca, k, rs);
+    else
+        pair_range_direct2<DIM, KERNEL, ISO, ZS, BF, false>(P, s0, e0 - s0, s1, 0, pa0, pa1, Ca, k, rs);
+}
+
+// Packed compensated addition: Neumaier's scheme per half with the two-sum error term (as
+// neumaier_add), in FP32x2 instructions.
+__device__ __forceinline__ void neumaier_add2(float2 &sum, float2 &comp, float2 x)
+{
+    const float2 t = __fadd2_rn(sum, x);
+    const float2 bp = __fadd2_rn(t, f2(-sum.x, -sum.y));
+    const float2 e = __fadd2_rn(__fadd2_rn(sum, f2(-(t.x - bp.x), -(t.y - bp.y))), __fadd2_rn(x, f2(-bp.x, -bp.y)));
+    comp = __fadd2_rn(comp, e);
+    sum = t;
+}
+
 // Eq. 4 at two particles of the same cell row by the paired walk; (cx0, cx1, cy, cz) their cells.
+// TRIM: one trimmed range per row serves both particles -- the pair's transverse interval
+// [min f, max f] against the pencil box bounds both particles' distances to the row from below,
+// and [min f_x - xe, max f_x + xe] (cells from cx0) contains both particles' own ranges -- so each
+// particle's row sum is bitwise that of rate_direct with TRIM (the extra candidates lie beyond
+// H (1 + 2^-12) of it and add exact zeros, and an empty or unreachable pencil gives a gap of
+// +inf).
 template <int DIM, int KERNEL, bool ISO, bool TRIM, bool BF = true>
 __device__ void rate_direct_pair(const uint4 *__restrict__ Pe, const uint32_t *__restrict__ cs,
                                  const uint4 &pa0, const uint4 &pa1, int cx0, int cx1, int cy, int cz,
-                                 const RateParams &prm, float &r0, float &r1)
+                                 const RateParams &prm, float &r0, float &r1, const TrimRow *srow = nullptr)
 {
     const int ncx = prm.ncx, ncy = prm.ncy, ncz = prm.ncz, nrows = prm.nrows;
     const PairConst kc(prm);
     const PairConst2 k2(kc);
     const float2 Ca = f2(__uint_as_float(pa0.w), __uint_as_float(pa1.w));
-    float acc0 = 0.f, comp0 = 0.f, acc1 = 0.f, comp1 = 0.f;
-    // the trimming of rate_direct, per target
-    const float two32 = 4294967296.f;
-    const float fx0 = (float)((pa0.x - prm.back[0]) * (uint32_t)ncx) * (1.f / two32);
-    const float fx1 = (float)((pa1.x - prm.back[0]) * (uint32_t)ncx) * (1.f / two32);
-    const uint32_t ya0 = pa0.y - prm.back[1], za0 = pa0.z - prm.back[2];
-    const uint32_t ya1 = pa1.y - prm.back[1], za1 = pa1.z - prm.back[2];
-    const float inv_wx = (float)ncx * (1.f / two32);
-    const float Hm2 = kc.H2 * (1.f + 1.f / 2048.f);
-    for (int ri = 0; ri < nrows; ++ri) {
-        const StencilRow row = prm.rows[ri];
-        int yy = cy + row.dy;
-        yy += (yy < 0) ? ncy : 0;
-        yy -= (yy >= ncy) ? ncy : 0;
-        int zz = 0;
-        if (DIM == 3) {
-            zz = cz + row.dz;
-            zz += (zz < 0) ? ncz : 0;
-            zz -= (zz >= ncz) ? ncz : 0;
+    float2 acc = f2(0.f, 0.f), comp = f2(0.f, 0.f);
+    if (TRIM) {
+        const TrimSelf m0 = trim_self<DIM>(pa0, cy, cz, prm), m1 = trim_self<DIM>(pa1, cy, cz, prm);
+        const TrimGeom g(prm);
+        const float ylo = fminf(m0.fy, m1.fy), yhi = fmaxf(m0.fy, m1.fy), pwy = yhi - ylo;
+        const float zlo = fminf(m0.fz, m1.fz), zhi = fmaxf(m0.fz, m1.fz), pwz = zhi - zlo;
+        const int dcx = cx1 - cx0;
+        // the pair's x extent in cell coordinates from cell cx0 (two particles of one cell are
+        // ordered by caller index, not by position)
+        const float xa = fminf(m0.fx, m1.fx + (float)dcx), xb = fmaxf(m0.fx, m1.fx + (float)dcx);
+        for (int ri = 0; ri < nrows; ++ri) {
+            const TrimRow r = srow[ri];
+            const int pidx = row_pencil<DIM>(r, m0, cy, cz, prm);
+            const float4 bb = load_box(prm, pidx);
+            // twice the gap between the pair's interval and the box: |b0 - a1| + |a0 - b1| - widths
+            const float ay0 = ylo - r.fdy, ay1 = yhi - r.fdy;
+            const float ey = ((fabsf(bb.x - ay1) + fabsf(ay0 - bb.y)) - ((bb.y - bb.x) + pwy)) * g.hy;
+            float e2 = ey * ey;
+            if (DIM == 3) {
+                const float az0 = zlo - r.fdz, az1 = zhi - r.fdz;
+                const float ez = ((fabsf(bb.z - az1) + fabsf(az0 - bb.w)) - ((bb.w - bb.z) + pwz)) * g.hz;
+                e2 = fmaf(ez, ez, e2);
+            }
+            if (!(e2 < g.Hm2)) continue;      // out of reach of both (or an empty pencil)
+            const float t = g.Hm2 - e2;
+            const float xe = fmaf(t * rsqrt_ftz(t), g.inv_wx, 1.f / 4096.f);
+            const int w = r.wdd & 0xff;
+            const int lo = cx0 + max(__float2int_rd(xa - xe), -w);
+            const int hi = cx0 + min(__float2int_rd(xb + xe), w + dcx) + 1;
+            int s0, e0, s1, e1;
+            row_ranges(cs, pidx * ncx, lo, hi, ncx, s0, e0, s1, e1);
+            float2 rs = f2(0.f, 0.f);
+            if (!BF || r.off == 0)   // the targets' own cell row
+                pair_row2<DIM, KERNEL, ISO, true, BF>(Pe, s0, e0, s1, e1, pa0, pa1, Ca, k2, rs);
+            else
+                pair_row2<DIM, KERNEL, ISO, false, BF>(Pe, s0, e0, s1, e1, pa0, pa1, Ca, k2, rs);
+            neumaier_add2(acc, comp, rs);
         }
-        int lo0 = cx0 - (int)row.w, hi0 = cx0 + row.w, lo1 = cx1 - (int)row.w, hi1 = cx1 + row.w;
-        bool in0 = true, in1 = true;       // the target reaches the row (rate_direct does not skip it)
-        bool ne0 = true, ne1 = true;       // ... and its cell range is not empty
-        if (TRIM) {
-            const uint4 bb = __ldg(prm.pencil + (zz * ncy + yy));
-            if (bb.x > bb.y) continue;      // empty pencil: rate_direct skips the row for both
-            const float e0 = pencil_gap2<DIM>(bb, ya0, za0, kc.sy, kc.sz);
-            const float e1 = pencil_gap2<DIM>(bb, ya1, za1, kc.sy, kc.sz);
-            in0 = e0 < Hm2;
-            in1 = e1 < Hm2;
-            const float t0 = in0 ? Hm2 - e0 : 1.f, t1 = in1 ? Hm2 - e1 : 1.f;
-            const float xe0 = t0 * rsqrt_ftz(t0) * inv_wx + 1.f / 4096.f;
-            const float xe1 = t1 * rsqrt_ftz(t1) * inv_wx + 1.f / 4096.f;
-            lo0 = cx0 + max(__float2int_rd(fx0 - xe0), -(int)row.w);
-            hi0 = cx0 + min(__float2int_rd(fx0 + xe0), (int)row.w);
-            lo1 = cx1 + max(__float2int_rd(fx1 - xe1), -(int)row.w);
-            hi1 = cx1 + min(__float2int_rd(fx1 + xe1), (int)row.w);
-            ne0 = in0 && lo0 <= hi0;
-            ne1 = in1 && lo1 <= hi1;
+    } else {
+        for (int ri = 0; ri < nrows; ++ri) {
+            const StencilRow row = prm.rows[ri];
+            int yy = cy + row.dy;
+            yy += (yy < 0) ? ncy : 0;
+            yy -= (yy >= ncy) ? ncy : 0;
+            int zz = 0;
+            if (DIM == 3) {
+                zz = cz + row.dz;
+                zz += (zz < 0) ? ncz : 0;
+                zz -= (zz >= ncz) ? ncz : 0;
+            }
+            int s0, e0, s1, e1;
+            row_ranges(cs, (zz * ncy + yy) * ncx, cx0 - (int)row.w, cx1 + row.w + 1, ncx, s0, e0, s1, e1);
+            float2 rs = f2(0.f, 0.f);
+            if (!BF || (row.dy == 0 && (DIM == 2 || row.dz == 0)))   // the targets' own cell row
+                pair_row2<DIM, KERNEL, ISO, true, BF>(Pe, s0, e0, s1, e1, pa0, pa1, Ca, k2, rs);
+            else
+                pair_row2<DIM, KERNEL, ISO, false, BF>(Pe, s0, e0, s1, e1, pa0, pa1, Ca, k2, rs);
+            neumaier_add2(acc, comp, rs);
         }
-        int lo, hi;
-        if (ne0 && ne1) {
-            lo = min(lo0, lo1);
-            hi = max(hi0, hi1) + 1;
-        } else if (ne0) {
-            lo = lo0;
-            hi = hi0 + 1;
-        } else if (ne1) {
-            lo = lo1;
-            hi = hi1 + 1;
-        } else {
-            // no candidate for either target; a reached row still adds its (zero) row sum
-            if (in0) neumaier_add(acc0, comp0, 0.f);
-            if (in1) neumaier_add(acc1, comp1, 0.f);
-            continue;
-        }
-        const int base = (zz * ncy + yy) * ncx;
-        int s0, e0, s1 = 0, e1 = 0;
-        if (lo < 0) {
-            s0 = __ldg(cs + base + lo + ncx);
-            e0 = __ldg(cs + base + ncx);
-            s1 = __ldg(cs + base);
-            e1 = __ldg(cs + base + hi);
-        } else if (hi > ncx) {
-            s0 = __ldg(cs + base + lo);
-            e0 = __ldg(cs + base + ncx);
-            s1 = __ldg(cs + base);
-            e1 = __ldg(cs + base + hi - ncx);
-        } else {
-            s0 = __ldg(cs + base + lo);
-            e0 = __ldg(cs + base + hi);
-        }
-        float2 rs = f2(0.f, 0.f);
-        if (!BF || (row.dy == 0 && (DIM == 2 || row.dz == 0))) {   // the targets' own cell row
-            pair_range_direct2<DIM, KERNEL, ISO, true, BF>(Pe, s0, e0, pa0, pa1, Ca, k2, rs);
-            pair_range_direct2<DIM, KERNEL, ISO, true, BF>(Pe, s1, e1, pa0, pa1, Ca, k2, rs);
-        } else {
-            pair_range_direct2<DIM, KERNEL, ISO, false, BF>(Pe, s0, e0, pa0, pa1, Ca, k2, rs);
-            pair_range_direct2<DIM, KERNEL, ISO, false, BF>(Pe, s1, e1, pa0, pa1, Ca, k2, rs);
-        }
-        // a target that does not reach the row (trimmed walk) skips it, as rate_direct does
-        if (in0) neumaier_add(acc0, comp0, rs.x);
-        if (in1) neumaier_add(acc1, comp1, rs.y);
     }
-    r0 = prm.upf * (acc0 + comp0);
-    r1 = prm.upf * (acc1 + comp1);
+    const float pf = prm.upf * shape_unscale<KERNEL>();
+    r0 = pf * (acc.x + comp.x);
+    r1 = pf * (acc.y + comp.y);
 }
 
 // ---------------------------------------------------------------------------------------------
