@@ -72,30 +72,51 @@ DEFAULT_WORKLOAD = "cube-128-h2"
 METRIC = "particle-pair interactions/s"
 UNIT = "interactions/s"
 
-# Minimum FP32-pipe instructions per in-support ordered pair of the uniform-D Wendland C2 term
-# (2D: 16, 3D: 22: separation, r^2, r, 1 - q, the kernel shape, the quadratic form of Eq. 5 over
-# r^2, the weight, C_a - C_b and the accumulation).  The ALU roof is
-# SMs x 128 FP32 lanes x clock / I_MIN pairs per second.
-I_MIN = {2: 16, 3: 22}
+# ALU roof of the uniform-D pair term: instructions per in-support ordered pair issued to the
+# FP32 lanes (SMs x 128 lanes x clock / count pairs per second).  I_PAIR is the per-pair count of
+# the scope table the measurement is defined against (2D 20, 3D 26: the separation from the
+# fixed-point words, r^2, r, 1 - q, the kernel shape, the pair factor of Eq. 5, the weight,
+# C_a - C_b and the accumulation); I_FP32 is the FP32 arithmetic alone of the form the kernels
+# evaluate (2D 14, 3D 16: r^2 2/3, 1 - q 2, its clamp 1, the dot product (sqrt|a| vhat . x) 2/3,
+# its product with 1/r 1, t^2 + b 1, the shape 2, the weight 1, C_a - C_b 1, the accumulation 1),
+# a stricter floor that leaves out the integer separations and their conversion to FP32.
+I_PAIR = {2: 20, 3: 26}
+I_FP32 = {2: 14, 3: 16}
 # Velocity-field pair term (per-particle D, harmonic means, convective term): minimum FP32-pipe
 # instructions and MUFU operations (rsqrt + one reciprocal per tensor component) per pair; the
 # roof takes the slower of the two pipes (128 FP32 lanes and 16 MUFU lanes per SM).
 FIELD_PIPE_COST = {2: (33, 4), 3: (51, 7)}
 MUFU_LANES_PER_SM = 16
 
-# DRAM bytes per rate launch (read + write, mean of predictor and corrector) from one ncu capture
-# of the current kernels (profiles/k_rate_ladder1024.md, profiles/k_rate_batch_batched64.md,
-# profiles/k_rate_field_field1024.md, profiles/k_rate_paper1m.md, profiles/k_rate_sweep_sweep512.md).
-# Set an entry to None whenever the kernel changes until it is captured again.
 # DRAM bytes (read + write) per launch of the dominant kernel, mean of one predictor and one
-# corrector launch from `ncu --set full` captures (profiles/), keyed by workload and walk; a walk
-# without a capture of the current kernel reports null
-TRAFFIC_PER_LAUNCH = {("ladder-1024-n120-r10", "direct-branch-free"): 23.84e6,
-                      ("ladder-1024-n120-r10", "direct-branch-free-paired"): 23.88e6,
-                      ("paper-1m-n31k-c4", "direct-branch-free-trimmed-paired"): 20.11e6,
-                      ("batched-64", None): 42.04e6,
-                      ("field-1024-n120-r10", "velocity-field-direct"): 82.24e6,
-                      ("sweep-512-8", None): 18.77e6}
+# corrector launch, from the ncu capture summarised in the named profile, keyed by workload and
+# walk, with the digest of the kernel sources the capture was taken of: a walk without a capture,
+# or whose sources have changed since, reports null traffic.
+TRAFFIC_PER_LAUNCH = {}
+KERNEL_SOURCES = ("rate_walk.cuh", "rate_common.cuh", "rate.cu", "rate_pair.cu", "ade_internal.h")
+
+
+def kernel_digest():
+    """Digest of the interaction kernels' sources (to tie a traffic capture to a kernel revision)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2108_09488_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_entry(workload, walk):
+    """(bytes per launch or None, source note) for the roofline line."""
+    e = TRAFFIC_PER_LAUNCH.get((workload, walk))
+    if e is None:
+        return None, "no ncu capture of this walk on this workload"
+    nbytes, profile, digest = e
+    if digest != kernel_digest():
+        return None, f"stale: the kernel sources changed since the capture in {profile}"
+    return nbytes, f"{profile} (kernel sources {digest})"
+
+
 # interaction walks (ade flags) selectable with --variant; "auto" autotunes grid and walk
 VARIANT_FLAGS = {"direct-branch-free": 1, "tiled": 2, "direct-branched": 4,
                  "direct-branch-free-trimmed": 9, "direct-branched-trimmed": 12,
@@ -442,14 +463,16 @@ def run_batched(args):
     rate_avg_ms = sum(rate_ms) / len(rate_ms)
     props = torch.cuda.get_device_properties(device)
     f_max = clk.get("sm_max_mhz") or 2070.0
-    peak = props.multi_processor_count * FP32_LANES_PER_SM * f_max * 1e6 / I_MIN[2] / 1e9
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * f_max * 1e6 / I_PAIR[2] / 1e9
     achieved = pairs / (rate_avg_ms * 1e-3) / 1e9
+    traffic, tsrc = traffic_entry("batched-64", None)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
-                "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(("batched-64", None)),
+                "frac": achieved / peak, "traffic": traffic, "traffic_source": tsrc,
                 "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "kernel": "k_rate_batch (predictor + corrector)",
                 "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
-                              f"{f_max:.0f} MHz / {I_MIN[2]} FP32-pipe instructions per pair",
+                              f"{f_max:.0f} MHz / {I_PAIR[2]} instructions per pair",
+                "frac_fp32_floor": achieved / (peak * I_PAIR[2] / I_FP32[2]),
                 "rate_kernel_ms": rate_avg_ms,
                 "phase_ms_per_step": {k: sum(p[i] for p in phases) / len(phases)
                                       for i, k in enumerate(("cells", "predictor", "corrector"))}}
@@ -512,7 +535,8 @@ def run_batched(args):
         "config": batched_config(all_plumes),
         "timing": "CUDA events around one graph replay (ade_batch_run) per step; per-phase times from "
                   "ade_batch_step_timed",
-        "batch": {"autotune_best_ms": tune_ms, "work_item_particles": info0.tile[0],
+        "batch": {"autotune_best_ms": tune_ms, "paired_walk": bool(b.config()[3]),
+                  "work_item_particles": info0.tile[0],
                   "persistent_grid": info0.tile[1], "work_items": info0.tile[2],
                   "cell_subdiv": [b.plume_info(i).cell_subdiv for i in range(len(plumes))]},
         "per_plume_launches": {"value": pp_value, "ms_per_step": pp_ms / args.steps,
@@ -606,7 +630,7 @@ def measured_alu_roof(ade, dim, field, achieved, sms):
         n32, nmufu = FIELD_PIPE_COST[dim]
         roof = min(ffma / n32, rsq / nmufu) / 1e9
     else:
-        n32, nmufu = I_MIN[dim], 1
+        n32, nmufu = I_PAIR[dim], 1
         roof = min(ffma / n32, rsq / nmufu) / 1e9
     return {"ffma_per_s": ffma, "rsqrt_per_s": rsq,
             "ffma_per_sm_per_ns": ffma / sms / 1e9, "rsqrt_per_sm_per_ns": rsq / sms / 1e9,
@@ -703,8 +727,9 @@ def run_sweep(args):
     per_set = SWEEP_PER_SET + SWEEP_GEOM / P
     peak = sms * FP32_LANES_PER_SM * f_max * 1e6 / per_set / 1e9
     achieved = pairs * P / (rate_ms * 1e-3) / 1e9
+    traffic, tsrc = traffic_entry("sweep-512-8", None)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair-sets/s",
-                "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(("sweep-512-8", None)),
+                "frac": achieved / peak, "traffic": traffic, "traffic_source": tsrc,
                 "traffic_unit": "bytes per evaluation (ncu dram read + write, all groups)",
                 "kernel": "k_rate_sweep (predictor + corrector, one group of 8 sets)",
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {f_max:.0f} MHz / "
@@ -795,6 +820,63 @@ def run_sweep(args):
     return 0
 
 
+def closed_form_images(plume, t):
+    """Periodic image shells of the closed form at time t: every omitted image lies more than 12
+    plume widths away (width^2 = w^2 + 2 lambda_max t, lambda_max = max(alpha_L, alpha_T)|v| + D_m)."""
+    import math
+    lam = max(plume.alpha_L, plume.alpha_T) * plume.speed + plume.D_m
+    sigma = math.sqrt(plume.w ** 2 + 2.0 * lam * t)
+    return int(math.ceil(12.0 * sigma / plume.box)) + 1
+
+
+def accuracy_run(ade, plume, device, steps=None, **over):
+    """The configured run of a uniform-velocity plume (steps of Eq. 8-9 from the initial state
+    through the library, FP32) and its error against the closed form of Sec. 3 (Eq. 12-13, FP64 on
+    the device): L2, Linf, RMSE of C/C0, C_min, C_max and the relative change of sum m C."""
+    import torch
+    steps = plume.steps if steps is None else steps
+    xq, C = plume.initial_state()
+    sim = ade.Simulation(ade.params_for(plume, **over), xq, C, device=device)
+    m0 = sim.stats().mass
+    if steps:
+        sim.run(steps, stats=False)
+    torch.cuda.synchronize()
+    st = sim.stats()
+    t = steps * sim.info.dt
+    nimg = closed_form_images(plume, t)
+    cf = sim.closed_form_error(np.asarray(plume.x0[: plume.dim]), plume.w, plume.C0, nimg=nimg)
+    out = {"steps": steps, "t": t, "dt": sim.info.dt, "l2": cf["l2"], "linf": cf["linf"], "rmse": cf["rmse"],
+           "c_an_max": cf["c_an_max"], "c_min": st.c_min, "c_max": st.c_max,
+           "mass_rel_change": (st.mass - m0) / m0, "closed_form_images": nimg,
+           "status": st.status}
+    sim.close()
+    return out
+
+
+ACCURACY_CONFIGS = [("lattice-64-h1.3", inputs.lattice_2d_64)] + [
+    (f"ladder-{s}-n{inputs.LADDER_NEIGHBOURS[s]}-r{r}", (lambda s=s, r=r: inputs.ladder_2d(s, r)))
+    for s in (256, 512, 1024) for r in (1, 10, 100)] + [("cube-128-h2", inputs.cube_3d_128)]
+
+
+def run_accuracy(args):
+    """One JSON line per configured plume: its full run against the closed form (FP32 state,
+    FP64 norms); the FP64-oracle drift of the same runs is checked in tests/test_gpu_precision.py."""
+    import torch
+
+    from paper_2108_09488_gb300 import ade
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    for name, make in ACCURACY_CONFIGS:
+        plume = make()
+        acc = accuracy_run(ade, plume, device)
+        print(json.dumps({"workload": name, "config": plume.name, "particles": plume.n, "dtype": "f32",
+                          "norms": "f64", **acc}), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
 
@@ -879,9 +961,9 @@ def run_ours(args):
     sms = props.multi_processor_count
     f_max = clk.get("sm_max_mhz") or 2070.0
     if v is None:
-        peak = sms * FP32_LANES_PER_SM * f_max * 1e6 / I_MIN[plume.dim] / 1e9
+        peak = sms * FP32_LANES_PER_SM * f_max * 1e6 / I_PAIR[plume.dim] / 1e9
         basis = (f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {f_max:.0f} MHz / "
-                 f"{I_MIN[plume.dim]} FP32-pipe instructions per pair")
+                 f"{I_PAIR[plume.dim]} instructions per pair")
         kname = "k_rate (predictor + corrector)"
     else:
         n32, nmufu = FIELD_PIPE_COST[plume.dim]
@@ -891,8 +973,9 @@ def run_ours(args):
                  f"{nmufu} MUFU ops / {MUFU_LANES_PER_SM} lanes) per pair")
         kname = "k_rate_field (predictor + corrector)"
     achieved = pairs / (rate_avg_ms * 1e-3) / 1e9
+    traffic, tsrc = traffic_entry(args.workload, walk)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
-                "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get((args.workload, walk)),
+                "frac": achieved / peak, "traffic": traffic, "traffic_source": tsrc,
                 "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "kernel": kname,
                 "peak_basis": basis,
@@ -902,6 +985,8 @@ def run_ours(args):
     if clk.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = achieved / (peak * clk["sm_mhz"] / f_max)
     roofline["measured_alu"] = measured_alu_roof(ade, plume.dim, v is not None, achieved, sms)
+    if v is None:
+        roofline["frac_fp32_floor"] = achieved / (peak * I_PAIR[plume.dim] / I_FP32[plume.dim])
 
     # end to end through the C ABI with host buffers: every step copies its inputs (x, C) from
     # pinned host memory, runs one graph-replayed step and reads C back.  The steps are independent
@@ -966,6 +1051,28 @@ def run_ours(args):
     sim2.close()
 
     line_extra = {}
+    # a whole run of consecutive steps through one ade_run call (graph replays of 32 steps each,
+    # no gap between them; L2 flushed once before the run): steps per second of a simulation
+    run_steps = 256 if plume.n <= (1 << 22) else 32
+    flush.zero_()
+    r0 = torch.cuda.Event(enable_timing=True)
+    r1 = torch.cuda.Event(enable_timing=True)
+    sim.run(run_steps, stats=False)              # graphs captured outside the timed region
+    torch.cuda.synchronize()
+    flush.zero_()
+    r0.record(stream)
+    sim.run(run_steps, stats=False)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    run_ms = r0.elapsed_time(r1)
+    line_extra["graph_run"] = {"steps": run_steps, "ms": run_ms, "steps_per_s": 1e3 * run_steps / run_ms,
+                               "interactions_per_s": 2.0 * pairs * run_steps / (run_ms * 1e-3),
+                               "how": "one ade_run call of consecutive steps (graphs of 32 steps), "
+                                      "CUDA events around it, L2 flushed before"}
+    if v is None and tau == 0.0 and not args.workload.startswith("paper-") and not args.no_accuracy:
+        # the configured run of this plume against the closed form (untimed)
+        line_extra["accuracy"] = accuracy_run(ade, plume, device, flags=VARIANT_FLAGS.get(walk, 0),
+                                              cell_subdiv=sim.info.cell_subdiv)
     if args.workload.startswith("paper-"):
         N = 4000000 if plume.n > 3000000 else (2000000 if plume.n > 1500000 else 1000000)
         line_extra["paper_context"] = {
@@ -1020,10 +1127,17 @@ def main():
                     help="interaction walk of the single-plume workloads (default: autotuned)")
     ap.add_argument("--cell-subdiv", type=int, default=0,
                     help="cells per support radius with --variant (0: the library's choice)")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="run every configured plume to its step count and print its error against "
+                         "the closed form (one JSON line per plume), instead of timing")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="leave the configured run against the closed form out of the bench line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)       # at least 3 untimed warm-up steps
     if args.impl == "reference":
         return run_reference(args)
+    if args.accuracy:
+        return run_accuracy(args)
     return run_ours(args)
 
 

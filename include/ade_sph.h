@@ -162,10 +162,11 @@ int ade_count_pairs(ade_ctx *ctx, long long *pairs_host, void *stream);
  * min C and max C per warp), and the fold of those partials into the step's FP64 statistics. */
 int ade_step(ade_ctx *ctx, int nsteps, void *stream);
 
-/* As ade_step, replaying one captured CUDA graph per step (captured on the first call).  With
- * stats_host non-NULL it waits for the stream and fills in the last step's statistics (those of
- * the state it wrote; with nsteps = 0, those of the current state as ade_get_stats); with NULL it
- * only enqueues. */
+/* As ade_step, replaying captured CUDA graphs: one graph of 32 steps per whole multiple of 32
+ * (no launch gap between those steps) and a graph of one step for the rest (each captured on the
+ * first call that needs it, outside any capture of the caller's).  With stats_host non-NULL it
+ * waits for the stream and fills in the last step's statistics (those of the state it wrote; with
+ * nsteps = 0, those of the current state as ade_get_stats); with NULL it only enqueues. */
 int ade_run(ade_ctx *ctx, int nsteps, ade_stats *stats_host, void *stream);
 
 /* One step (as ade_step) bracketed by CUDA events on `stream`; waits for it and returns the device
@@ -307,18 +308,21 @@ int ade_batch_get_plume_info(const ade_batch *b, int plume, ade_info *info_host)
 
 /* Autotuner: times the cell build plus one evaluation of every plume for each cell-subdivision
  * policy (per-plume cost model, or 1..6 cells per support radius), work-item size (64..512
- * particles) and persistent grid size (4, 8, 16 blocks per SM), keeps the fastest and re-plans.
+ * particles), persistent grid size (4, 8, 16 blocks per SM) and walk (one particle per thread, or
+ * the paired walk: two adjacent particles per thread, same sums), keeps the fastest and re-plans.
  * Leaves the particle state unchanged; waits; best_ms_host (may be NULL) gets the best time. */
 int ade_batch_autotune(ade_batch *b, double *best_ms_host, void *stream);
 
 /* The batch's configuration -- cell-subdivision policy (0 = per-plume cost model, 1..6 cells per
- * support radius), work-item size in particles and persistent grid in blocks -- as chosen by
- * ade_batch_autotune, and its application to another batch of the same plumes so that both run
- * the same kernels (no counterpart in the paper).  set: subdiv_mode in [0, 6], tile_size in
- * [32, 4096], grid_blocks in [1, 65536]; re-plans the work list and uploads it on `stream` (waits);
- * ADE_ERR_ARG outside those ranges, the batch unchanged.  Host pointers may not be NULL. */
-int ade_batch_get_config(const ade_batch *b, int *subdiv_mode_host, int *tile_size_host, int *grid_blocks_host);
-int ade_batch_set_config(ade_batch *b, int subdiv_mode, int tile_size, int grid_blocks, void *stream);
+ * support radius), work-item size in particles, persistent grid in blocks and walk (1: paired) --
+ * as chosen by ade_batch_autotune, and its application to another batch of the same plumes so that
+ * both run the same kernels (no counterpart in the paper).  set: subdiv_mode in [0, 6], tile_size
+ * in [32, 4096], grid_blocks in [1, 65536], paired 0 or 1; re-plans the work list and uploads it on
+ * `stream` (waits); ADE_ERR_ARG outside those ranges, the batch unchanged.  Host pointers may not
+ * be NULL. */
+int ade_batch_get_config(const ade_batch *b, int *subdiv_mode_host, int *tile_size_host, int *grid_blocks_host,
+                         int *paired_host);
+int ade_batch_set_config(ade_batch *b, int subdiv_mode, int tile_size, int grid_blocks, int paired, void *stream);
 
 /* One batched step bracketed by CUDA events; waits; phase_ms_host[4] = {cell build, predictor,
  * corrector, 0} in milliseconds. */

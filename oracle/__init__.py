@@ -284,14 +284,6 @@ def sort_cells(key, ncells):
     return perm, start
 
 
-def fixed_to_double(xq, box):
-    """Fixed-point positions uint32 [dim][n] -> FP64 [n][dim] (exact: u = xq * L / 2^32)."""
-    xq = np.asarray(xq, dtype=np.uint32)
-    box = np.asarray(box, dtype=np.float64)
-    dim = xq.shape[0]
-    return np.ascontiguousarray((xq.astype(np.float64) * (box[:dim, None] / 2.0 ** 32)).T)
-
-
 # --------------------------------------------------------------------------------------------
 # Closed form (Eq. 12-13) and metrics
 # --------------------------------------------------------------------------------------------
@@ -307,14 +299,6 @@ def closed_form(x, box, x0, v, D, w, C0, t, nimg=2):
     _load().orc_closed_form(dim, n, _ptr(x), _ptr(box), _ptr(x0), _ptr(v), _ptr(D), w, C0, t,
                             nimg, _ptr(C))
     return C
-
-
-def images_needed(box, D, w, t, v=None, tol_sigma=12.0):
-    """Image shells needed so that every omitted image lies beyond tol_sigma plume widths."""
-    D = np.asarray(D, dtype=np.float64)
-    lam = float(np.max(np.linalg.eigvalsh(D)))
-    sigma = np.sqrt(w * w + 2.0 * lam * t)
-    return int(np.ceil(tol_sigma * sigma / float(np.min(box)))) + 1
 
 
 def set_threads(n):

@@ -123,8 +123,8 @@ def load():
         "ade_batch_count_pairs": (I, [P, ctypes.POINTER(LL), V]),
         "ade_batch_get_plume_info": (I, [P, I, ctypes.POINTER(Info)]),
         "ade_batch_autotune": (I, [P, ctypes.POINTER(ctypes.c_double), V]),
-        "ade_batch_get_config": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
-        "ade_batch_set_config": (I, [P, I, I, I, V]),
+        "ade_batch_get_config": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "ade_batch_set_config": (I, [P, I, I, I, I, V]),
         "ade_batch_launches_per_step": (I, [P, ctypes.POINTER(I)]),
         "ade_batch_step_timed": (I, [P, ctypes.POINTER(ctypes.c_double), V]),
         "ade_set_dispersivity": (I, [P, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
@@ -528,15 +528,17 @@ class Batch:
         return ms.value
 
     def config(self):
-        """(subdivision policy, work-item size, persistent grid) in use."""
-        m, t, g = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
-        _check(load().ade_batch_get_config(self.ctx, ctypes.byref(m), ctypes.byref(t), ctypes.byref(g)))
-        return m.value, t.value, g.value
+        """(subdivision policy, work-item size, persistent grid, paired walk) in use."""
+        m, t, g, w = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(load().ade_batch_get_config(self.ctx, ctypes.byref(m), ctypes.byref(t), ctypes.byref(g),
+                                           ctypes.byref(w)))
+        return m.value, t.value, g.value, w.value
 
     def set_config(self, cfg):
-        """Apply a (subdivision policy, work-item size, persistent grid) triple, e.g. another
-        batch's config() after its autotune."""
-        _check(load().ade_batch_set_config(self.ctx, int(cfg[0]), int(cfg[1]), int(cfg[2]), self.stream))
+        """Apply a (subdivision policy, work-item size, persistent grid, paired walk) tuple, e.g.
+        another batch's config() after its autotune."""
+        _check(load().ade_batch_set_config(self.ctx, int(cfg[0]), int(cfg[1]), int(cfg[2]), int(cfg[3]),
+                                           self.stream))
 
     def launches_per_step(self):
         v = ctypes.c_int(0)

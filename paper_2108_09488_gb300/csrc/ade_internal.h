@@ -15,6 +15,7 @@ constexpr int kRateThreads = 128;                              // direct variant
 constexpr int kTileThreads = 256;                              // tiled variant
 constexpr int kMaxCellBits = 24;                                // ncells <= 2^24
 constexpr int kScanTileCells = 2048;                            // cells per scan block (cells.cu)
+constexpr int kGraphSteps = 32;                                 // steps captured in ade_run's long graph
 
 // Programmatic dependent launch (griddepcontrol, sm_90 and later).  A kernel launched by
 // launch_pdl may have its CTAs scheduled while the kernel before it on the stream is still
@@ -206,9 +207,11 @@ cudaError_t launch_build_cells(int dim, const uint32_t *xq, const float *C, int 
 cudaError_t launch_build_cells_batch(int dim, const uint32_t *xq, const float *C, int n, int ncells,
                                      const RateParams *descs, const uint16_t *plume_of,
                                      const Work &w, cudaStream_t s);
+// paired: the persistent kernel's threads take two adjacent sorted particles (the paired walk).
 cudaError_t launch_rate_batch(int dim, int kernel, int epi, const uint4 *Pe, const uint32_t *cell_start,
                               const uint32_t *perm, const RateParams *descs, const BatchTile *tiles,
-                              int ntiles, unsigned *queue, int grid, const EpiOut &out, cudaStream_t s);
+                              int ntiles, unsigned *queue, int grid, const EpiOut &out, cudaStream_t s,
+                              bool paired = false);
 cudaError_t launch_batch_stats(const float *C, const int *offsets, int nplumes, double *stats,
                                cudaStream_t s);
 cudaError_t launch_rate(int dim, int kernel, bool iso, int epi, const uint4 *Pe, const uint4 *Pc,
@@ -282,8 +285,10 @@ struct ade_ctx {
     double t;
     long long step;
     long long pairs;
-    cudaGraph_t graph;
+    cudaGraph_t graph;             // one step (ade_run)
     cudaGraphExec_t graph_exec;
+    cudaGraph_t graph_multi;       // kGraphSteps steps (ade_run)
+    cudaGraphExec_t graph_exec_multi;
     cudaStream_t cap_stream;
     bool status_cleared;
     cudaEvent_t ev[5];    // per-phase timing events (created on first timed step)

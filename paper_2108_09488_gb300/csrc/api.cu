@@ -806,6 +806,43 @@ int ade_init_particles(ade_ctx **out, const ade_params *p, int n, uint32_t *xq_d
 
 namespace {
 
+// Forget the captured step graphs (the configuration they were captured with has changed).
+void drop_graphs(ade_ctx *c)
+{
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    if (c->graph_exec_multi) cudaGraphExecDestroy(c->graph_exec_multi);
+    if (c->graph_multi) cudaGraphDestroy(c->graph_multi);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+    c->graph_exec_multi = nullptr;
+    c->graph_multi = nullptr;
+}
+
+// Capture `steps` consecutive steps into one graph.
+int capture_steps(ade_ctx *c, int steps, cudaGraph_t *graph, cudaGraphExec_t *exec)
+{
+    if (!c->cap_stream) ADE_CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    ADE_CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = ADE_OK;
+    for (int k = 0; k < steps && rc == ADE_OK; ++k) rc = enqueue_step(c, c->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    ADE_CK(e);
+    cudaError_t ei = cudaGraphInstantiate(exec, g, 0);
+    if (ei != cudaSuccess) {
+        cudaGraphDestroy(g);
+        *exec = nullptr;
+        return fail(ADE_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ei));
+    }
+    *graph = g;
+    return ADE_OK;
+}
+
 // Switch a context to cell subdivision k and kernel variant (tiled or direct); the workspace
 // layout is fixed at init, so only the grid, the stencil and the tile fields change.
 int apply_config(ade_ctx *c, int k, int variant)
@@ -840,14 +877,7 @@ int apply_config(ade_ctx *c, int k, int variant)
     rp.nty = t.nty;
     rp.ntz = t.ntz;
     rp.cap = t.cap;
-    if (c->graph_exec) {
-        cudaGraphExecDestroy(c->graph_exec);
-        c->graph_exec = nullptr;
-    }
-    if (c->graph) {
-        cudaGraphDestroy(c->graph);
-        c->graph = nullptr;
-    }
+    drop_graphs(c);
     return ADE_OK;
 }
 
@@ -1006,14 +1036,7 @@ int ade_set_dispersivity(ade_ctx *c, double alpha_L, double alpha_T, double D_m)
         c->fp.Dm = D_m;
         c->field_dirty = true;   // tensors re-formed on the caller's stream before the next use
     }
-    if (c->graph_exec) {
-        cudaGraphExecDestroy(c->graph_exec);
-        c->graph_exec = nullptr;
-    }
-    if (c->graph) {
-        cudaGraphDestroy(c->graph);
-        c->graph = nullptr;
-    }
+    drop_graphs(c);
     return ADE_OK;
 }
 
@@ -1149,26 +1172,19 @@ int ade_run(ade_ctx *c, int nsteps, ade_stats *st, void *stream)
     if (rc0) return rc0;
     rc0 = refresh_field(c, s);
     if (rc0) return rc0;
-    if (!c->graph_exec && nsteps > 0) {
-        if (!c->cap_stream) ADE_CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
-        ADE_CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-        int rc = enqueue_step(c, c->cap_stream);
-        cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
-        if (rc) {
-            if (g) cudaGraphDestroy(g);
-            return rc;
-        }
-        ADE_CK(e);
-        cudaError_t ei = cudaGraphInstantiate(&c->graph_exec, g, 0);
-        if (ei != cudaSuccess) {
-            cudaGraphDestroy(g);
-            c->graph_exec = nullptr;
-            return fail(ADE_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ei));
-        }
-        c->graph = g;
+    // whole multiples of kGraphSteps replay one graph of kGraphSteps steps (no launch gap between
+    // them), the rest a graph of one step
+    const int nmulti = nsteps / ade::kGraphSteps, nsingle = nsteps % ade::kGraphSteps;
+    if (nmulti > 0 && !c->graph_exec_multi) {
+        int rc = capture_steps(c, ade::kGraphSteps, &c->graph_multi, &c->graph_exec_multi);
+        if (rc) return rc;
     }
-    for (int k = 0; k < nsteps; ++k) ADE_CK(cudaGraphLaunch(c->graph_exec, s));
+    if (nsingle > 0 && !c->graph_exec) {
+        int rc = capture_steps(c, 1, &c->graph, &c->graph_exec);
+        if (rc) return rc;
+    }
+    for (int k = 0; k < nmulti; ++k) ADE_CK(cudaGraphLaunch(c->graph_exec_multi, s));
+    for (int k = 0; k < nsingle; ++k) ADE_CK(cudaGraphLaunch(c->graph_exec, s));
     c->step += nsteps;
     c->t += nsteps * c->dt;
     if (!st) return ADE_OK;
@@ -1281,8 +1297,7 @@ int ade_closed_form_error(ade_ctx *c, const double *x0, double w, double C0, int
 void ade_destroy(ade_ctx *c)
 {
     if (!c) return;
-    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
-    if (c->graph) cudaGraphDestroy(c->graph);
+    drop_graphs(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->ev_ready)
         for (int k = 0; k < 5; ++k) cudaEventDestroy(c->ev[k]);
@@ -1307,6 +1322,7 @@ struct ade_batch {
     int NC = 0, NC_max = 0;
     int tile_size = ade::kRateThreads, grid = 0, sms = 0;
     int subdiv_mode = 0;                  // 0 = per-plume cost model, 1..6 forced where valid
+    bool paired = false;                  // the rate kernel's threads take two particles (paired walk)
     std::vector<ade::BatchTile> tiles;
     uint32_t *xq = nullptr;
     float *C = nullptr;
@@ -1507,13 +1523,13 @@ int batch_enqueue_step(ade_batch *b, cudaStream_t s)
     ade::EpiOut out = epi_none();
     out.Pout = b->w.P1;
     ADE_CK(ade::launch_rate_batch(b->dim, b->kernel, ade::EPI_PREDICT, b->w.P0, b->w.cell_start, b->w.perm,
-                                  b->d_pred, b->d_tiles, (int)b->tiles.size(), b->queue, b->grid, out, s));
+                                  b->d_pred, b->d_tiles, (int)b->tiles.size(), b->queue, b->grid, out, s, b->paired));
     out = epi_none();
     out.xq = b->xq;
     out.C = b->C;
     out.status = b->w.status;
     ADE_CK(ade::launch_rate_batch(b->dim, b->kernel, ade::EPI_CORRECT, b->w.P1, b->w.cell_start, b->w.perm,
-                                  b->d_corr, b->d_tiles, (int)b->tiles.size(), b->queue, b->grid, out, s));
+                                  b->d_corr, b->d_tiles, (int)b->tiles.size(), b->queue, b->grid, out, s, b->paired));
     return ADE_OK;
 }
 
@@ -1719,7 +1735,7 @@ int ade_batch_count_pairs(ade_batch *b, long long *pairs_host, void *stream)
     ade::EpiOut out = epi_none();
     out.pairs = b->w.pairs;
     ADE_CK(ade::launch_rate_batch(b->dim, b->kernel, ade::EPI_RATE, b->w.P0, b->w.cell_start, b->w.perm,
-                                  b->d_pred, b->d_tiles, (int)b->tiles.size(), b->queue, b->grid, out, s));
+                                  b->d_pred, b->d_tiles, (int)b->tiles.size(), b->queue, b->grid, out, s, b->paired));
     unsigned long long v = 0;
     ADE_CK(cudaMemcpyAsync(&v, b->w.pairs, 8, cudaMemcpyDeviceToHost, s));
     ADE_CK(cudaStreamSynchronize(s));
@@ -1727,30 +1743,34 @@ int ade_batch_count_pairs(ade_batch *b, long long *pairs_host, void *stream)
     return ADE_OK;
 }
 
-int ade_batch_get_config(const ade_batch *b, int *subdiv_mode, int *tile_size, int *grid_blocks)
+int ade_batch_get_config(const ade_batch *b, int *subdiv_mode, int *tile_size, int *grid_blocks, int *paired)
 {
-    if (!b || !subdiv_mode || !tile_size || !grid_blocks) return fail(ADE_ERR_ARG, "NULL argument");
+    if (!b || !subdiv_mode || !tile_size || !grid_blocks || !paired) return fail(ADE_ERR_ARG, "NULL argument");
     *subdiv_mode = b->subdiv_mode;
     *tile_size = b->tile_size;
     *grid_blocks = b->grid;
+    *paired = b->paired ? 1 : 0;
     return ADE_OK;
 }
 
-int ade_batch_set_config(ade_batch *b, int subdiv_mode, int tile_size, int grid_blocks, void *stream)
+int ade_batch_set_config(ade_batch *b, int subdiv_mode, int tile_size, int grid_blocks, int paired, void *stream)
 {
     if (!b) return fail(ADE_ERR_ARG, "batch is NULL");
     if (subdiv_mode < 0 || subdiv_mode > ade::kMaxSubdiv || tile_size < kMinTile || tile_size > 4096 ||
-        grid_blocks < 1 || grid_blocks > 65536)
+        grid_blocks < 1 || grid_blocks > 65536 || (paired != 0 && paired != 1))
         return fail(ADE_ERR_ARG, "configuration out of range");
     const int m0 = b->subdiv_mode, t0 = b->tile_size, g0 = b->grid;
+    const bool p0 = b->paired;
     b->subdiv_mode = subdiv_mode;
     b->tile_size = tile_size;
     b->grid = grid_blocks;
+    b->paired = paired != 0;
     int rc = batch_plan(b);
     if (rc) {
         b->subdiv_mode = m0;
         b->tile_size = t0;
         b->grid = g0;
+        b->paired = p0;
         batch_plan(b);
         return rc;
     }
@@ -1803,7 +1823,7 @@ int ade_batch_autotune(ade_batch *b, double *best_ms_host, void *stream)
             ade::EpiOut out = epi_none();
             ADE_CK(ade::launch_rate_batch(b->dim, b->kernel, ade::EPI_RATE, b->w.P0, b->w.cell_start,
                                           b->w.perm, b->d_pred, b->d_tiles, (int)b->tiles.size(), b->queue,
-                                          b->grid, out, s));
+                                          b->grid, out, s, b->paired));
             ADE_CK(cudaEventRecord(e1, s));
             ADE_CK(cudaEventSynchronize(e1));
             float f = 0.f;
@@ -1845,6 +1865,17 @@ int ade_batch_autotune(ade_batch *b, double *best_ms_host, void *stream)
         }
     }
     b->grid = best_grid;
+    // the walk: one particle per thread, or two adjacent particles (paired walk)
+    bool best_paired = b->paired;
+    for (int pw = 0; rc == ADE_OK && pw < 2; ++pw) {
+        b->paired = pw == 1;
+        rc = time_cfg(&ms);
+        if (rc == ADE_OK && ms < best) {
+            best = ms;
+            best_paired = b->paired;
+        }
+    }
+    b->paired = best_paired;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
@@ -1872,14 +1903,14 @@ int ade_batch_step_timed(ade_batch *b, double *phase_ms, void *stream)
     ade::EpiOut out = epi_none();
     out.Pout = b->w.P1;
     ADE_CK(ade::launch_rate_batch(b->dim, b->kernel, ade::EPI_PREDICT, b->w.P0, b->w.cell_start, b->w.perm,
-                                  b->d_pred, b->d_tiles, (int)b->tiles.size(), b->queue, b->grid, out, s));
+                                  b->d_pred, b->d_tiles, (int)b->tiles.size(), b->queue, b->grid, out, s, b->paired));
     ADE_CK(cudaEventRecord(ev[2], s));
     out = epi_none();
     out.xq = b->xq;
     out.C = b->C;
     out.status = b->w.status;
     ADE_CK(ade::launch_rate_batch(b->dim, b->kernel, ade::EPI_CORRECT, b->w.P1, b->w.cell_start, b->w.perm,
-                                  b->d_corr, b->d_tiles, (int)b->tiles.size(), b->queue, b->grid, out, s));
+                                  b->d_corr, b->d_tiles, (int)b->tiles.size(), b->queue, b->grid, out, s, b->paired));
     ADE_CK(cudaEventRecord(ev[3], s));
     ADE_CK(cudaEventSynchronize(ev[3]));
     for (int k = 0; k < 3; ++k) {

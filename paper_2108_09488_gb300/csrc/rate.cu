@@ -276,7 +276,9 @@ __global__ __launch_bounds__(kTileThreads, 2) void k_rate_tiled(const uint4 *__r
 // copied to shared memory once per item and each particle is evaluated with the same code as the
 // single-plume direct kernel (rate_direct + epilogue), so a plume gives bit-identical results
 // whether it runs alone or in a batch.  Items are ordered by decreasing estimated cost.
-template <int DIM, int KERNEL, int EPI, bool COUNT>
+// PAIRED: each thread takes two adjacent sorted particles of the item (rate_direct_pair; a pair
+// that cannot share a candidate stream takes the one-target walk for each), with the same sums.
+template <int DIM, int KERNEL, int EPI, bool COUNT, bool PAIRED>
 __global__ __launch_bounds__(kRateThreads) void k_rate_batch(const uint4 *__restrict__ Pe,
                                                              const uint32_t *__restrict__ cs,
                                                              const uint32_t *__restrict__ perm,
@@ -307,17 +309,44 @@ __global__ __launch_bounds__(kRateThreads) void k_rate_batch(const uint4 *__rest
         const RateParams &prm = sp;
         EpiOut o = out;
         if (EPI == EPI_CORRECT) o.xq = out.xq + (size_t)prm.goff * (DIM - 1);
-        for (int k = threadIdx.x; k < t.count; k += kRateThreads) {
-            const int gi = prm.goff + t.start + k;
-            const uint4 pa = __ldg(Pe + gi);
-            const int cx = (int)__umulhi(pa.x - prm.back[0], (uint32_t)prm.ncx);
-            const int cy = (int)__umulhi(pa.y - prm.back[1], (uint32_t)prm.ncy);
-            const int cz = DIM == 3 ? (int)__umulhi(pa.z - prm.back[2], (uint32_t)prm.ncz) : 0;
-            unsigned c = 0u;
-            const float rate = rate_direct<DIM, KERNEL, true, COUNT>(Pe, cs + prm.coff, pa, cx, cy, cz, prm, c);
-            cnt += c;
-            Acc acc{0.f, 0.f, 0.f, 0.f, 0u};
-            epilogue<DIM, EPI>(gi, rate, pa, perm, prm, o, acc);
+        if (PAIRED && !COUNT) {
+            for (int k = 2 * threadIdx.x; k < t.count; k += 2 * kRateThreads) {
+                const int g0 = prm.goff + t.start + k;
+                const bool v1 = k + 1 < t.count;
+                const uint4 pa0 = __ldg(Pe + g0);
+                const uint4 pa1 = __ldg(Pe + (v1 ? g0 + 1 : g0));
+                const int cx0 = (int)__umulhi(pa0.x - prm.back[0], (uint32_t)prm.ncx);
+                const int cy0 = (int)__umulhi(pa0.y - prm.back[1], (uint32_t)prm.ncy);
+                const int cz0 = DIM == 3 ? (int)__umulhi(pa0.z - prm.back[2], (uint32_t)prm.ncz) : 0;
+                const int cx1 = (int)__umulhi(pa1.x - prm.back[0], (uint32_t)prm.ncx);
+                const int cy1 = (int)__umulhi(pa1.y - prm.back[1], (uint32_t)prm.ncy);
+                const int cz1 = DIM == 3 ? (int)__umulhi(pa1.z - prm.back[2], (uint32_t)prm.ncz) : 0;
+                float r0, r1 = 0.f;
+                unsigned c = 0u;
+                if (v1 && can_pair(cx0, cy0, cz0, cx1, cy1, cz1, prm.ncx)) {
+                    rate_direct_pair<DIM, KERNEL, true, false>(Pe, cs + prm.coff, pa0, pa1, cx0, cx1, cy0, cz0, prm,
+                                                               r0, r1);
+                } else {
+                    r0 = rate_direct<DIM, KERNEL, true, false>(Pe, cs + prm.coff, pa0, cx0, cy0, cz0, prm, c);
+                    if (v1) r1 = rate_direct<DIM, KERNEL, true, false>(Pe, cs + prm.coff, pa1, cx1, cy1, cz1, prm, c);
+                }
+                Acc acc{0.f, 0.f, 0.f, 0.f, 0u};
+                epilogue<DIM, EPI>(g0, r0, pa0, perm, prm, o, acc);
+                if (v1) epilogue<DIM, EPI>(g0 + 1, r1, pa1, perm, prm, o, acc);
+            }
+        } else {
+            for (int k = threadIdx.x; k < t.count; k += kRateThreads) {
+                const int gi = prm.goff + t.start + k;
+                const uint4 pa = __ldg(Pe + gi);
+                const int cx = (int)__umulhi(pa.x - prm.back[0], (uint32_t)prm.ncx);
+                const int cy = (int)__umulhi(pa.y - prm.back[1], (uint32_t)prm.ncy);
+                const int cz = DIM == 3 ? (int)__umulhi(pa.z - prm.back[2], (uint32_t)prm.ncz) : 0;
+                unsigned c = 0u;
+                const float rate = rate_direct<DIM, KERNEL, true, COUNT>(Pe, cs + prm.coff, pa, cx, cy, cz, prm, c);
+                cnt += c;
+                Acc acc{0.f, 0.f, 0.f, 0.f, 0u};
+                epilogue<DIM, EPI>(gi, rate, pa, perm, prm, o, acc);
+            }
         }
         __syncthreads();   // sp and s_item are rewritten by the next item
     }
@@ -327,22 +356,35 @@ __global__ __launch_bounds__(kRateThreads) void k_rate_batch(const uint4 *__rest
     }
 }
 
-template <int DIM, int KERNEL, bool COUNT>
+template <int DIM, int KERNEL, bool COUNT, bool PAIRED>
 void launch_batch_epi(int epi, int grid, const uint4 *Pe, const uint32_t *cs, const uint32_t *perm,
                       const RateParams *descs, const BatchTile *tiles, int ntiles, unsigned *queue,
                       const EpiOut &out, cudaStream_t s)
 {
     switch (epi) {
     case EPI_RATE:
-        k_rate_batch<DIM, KERNEL, EPI_RATE, COUNT><<<grid, kRateThreads, 0, s>>>(Pe, cs, perm, descs, tiles, ntiles, queue, out);
+        k_rate_batch<DIM, KERNEL, EPI_RATE, COUNT, PAIRED><<<grid, kRateThreads, 0, s>>>(Pe, cs, perm, descs, tiles, ntiles, queue, out);
         break;
     case EPI_PREDICT:
-        k_rate_batch<DIM, KERNEL, EPI_PREDICT, COUNT><<<grid, kRateThreads, 0, s>>>(Pe, cs, perm, descs, tiles, ntiles, queue, out);
+        k_rate_batch<DIM, KERNEL, EPI_PREDICT, COUNT, PAIRED><<<grid, kRateThreads, 0, s>>>(Pe, cs, perm, descs, tiles, ntiles, queue, out);
         break;
     default:
-        k_rate_batch<DIM, KERNEL, EPI_CORRECT, COUNT><<<grid, kRateThreads, 0, s>>>(Pe, cs, perm, descs, tiles, ntiles, queue, out);
+        k_rate_batch<DIM, KERNEL, EPI_CORRECT, COUNT, PAIRED><<<grid, kRateThreads, 0, s>>>(Pe, cs, perm, descs, tiles, ntiles, queue, out);
         break;
     }
+}
+
+template <int DIM, int KERNEL>
+void launch_batch_k(bool count, bool paired, int epi, int grid, const uint4 *Pe, const uint32_t *cs,
+                    const uint32_t *perm, const RateParams *descs, const BatchTile *tiles, int ntiles,
+                    unsigned *queue, const EpiOut &out, cudaStream_t s)
+{
+    if (count)
+        launch_batch_epi<DIM, KERNEL, true, false>(epi, grid, Pe, cs, perm, descs, tiles, ntiles, queue, out, s);
+    else if (paired)
+        launch_batch_epi<DIM, KERNEL, false, true>(epi, grid, Pe, cs, perm, descs, tiles, ntiles, queue, out, s);
+    else
+        launch_batch_epi<DIM, KERNEL, false, false>(epi, grid, Pe, cs, perm, descs, tiles, ntiles, queue, out, s);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -434,25 +476,22 @@ size_t tiled_smem_bytes(int dim, const RateParams &prm)
 
 cudaError_t launch_rate_batch(int dim, int kernel, int epi, const uint4 *Pe, const uint32_t *cell_start,
                               const uint32_t *perm, const RateParams *descs, const BatchTile *tiles,
-                              int ntiles, unsigned *queue, int grid, const EpiOut &out, cudaStream_t s)
+                              int ntiles, unsigned *queue, int grid, const EpiOut &out, cudaStream_t s,
+                              bool paired)
 {
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned), s);
     if (e != cudaSuccess || ntiles == 0) return e;
     const bool count = out.pairs != nullptr;
     if (dim == 2) {
         if (kernel == ADE_WENDLAND_C2)
-            count ? launch_batch_epi<2, ADE_WENDLAND_C2, true>(epi, grid, Pe, cell_start, perm, descs, tiles, ntiles, queue, out, s)
-                  : launch_batch_epi<2, ADE_WENDLAND_C2, false>(epi, grid, Pe, cell_start, perm, descs, tiles, ntiles, queue, out, s);
+            launch_batch_k<2, ADE_WENDLAND_C2>(count, paired, epi, grid, Pe, cell_start, perm, descs, tiles, ntiles, queue, out, s);
         else
-            count ? launch_batch_epi<2, ADE_WENDLAND_C4, true>(epi, grid, Pe, cell_start, perm, descs, tiles, ntiles, queue, out, s)
-                  : launch_batch_epi<2, ADE_WENDLAND_C4, false>(epi, grid, Pe, cell_start, perm, descs, tiles, ntiles, queue, out, s);
+            launch_batch_k<2, ADE_WENDLAND_C4>(count, paired, epi, grid, Pe, cell_start, perm, descs, tiles, ntiles, queue, out, s);
     } else {
         if (kernel == ADE_WENDLAND_C2)
-            count ? launch_batch_epi<3, ADE_WENDLAND_C2, true>(epi, grid, Pe, cell_start, perm, descs, tiles, ntiles, queue, out, s)
-                  : launch_batch_epi<3, ADE_WENDLAND_C2, false>(epi, grid, Pe, cell_start, perm, descs, tiles, ntiles, queue, out, s);
+            launch_batch_k<3, ADE_WENDLAND_C2>(count, paired, epi, grid, Pe, cell_start, perm, descs, tiles, ntiles, queue, out, s);
         else
-            count ? launch_batch_epi<3, ADE_WENDLAND_C4, true>(epi, grid, Pe, cell_start, perm, descs, tiles, ntiles, queue, out, s)
-                  : launch_batch_epi<3, ADE_WENDLAND_C4, false>(epi, grid, Pe, cell_start, perm, descs, tiles, ntiles, queue, out, s);
+            launch_batch_k<3, ADE_WENDLAND_C4>(count, paired, epi, grid, Pe, cell_start, perm, descs, tiles, ntiles, queue, out, s);
     }
     return cudaGetLastError();
 }

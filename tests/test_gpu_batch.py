@@ -137,8 +137,26 @@ def test_batch_config_copy_gives_identical_steps(lib):
         xa, Ca = a.state(i)
         xb, Cb = b.state(i)
         assert _same(xa, xb) and _same(Ca, Cb)
-    for bad in ((7, 256, 100), (0, 16, 100), (0, 256, 0)):
+    for bad in ((7, 256, 100, 0), (0, 16, 100, 0), (0, 256, 0, 0), (0, 256, 100, 2)):
         with pytest.raises(lib.AdeError) as e:
             b.set_config(bad)
         assert e.value.code == -1
     assert b.config() == cfg
+
+
+def test_batch_paired_walk_is_bitwise_the_single_walk(lib):
+    """The batched rate kernel with two particles per thread (paired walk) steps every plume bit
+    for bit like the one-particle-per-thread walk of the same configuration."""
+    plumes = inputs.batched_2d(**SMALL)
+    a, _ = _batch(lib, plumes)
+    b, _ = _batch(lib, plumes)
+    m, t, g, _ = a.config()
+    a.set_config((m, t, g, 0))
+    b.set_config((m, t, g, 1))
+    assert b.config()[3] == 1
+    a.run(3)
+    b.run(3)
+    for i in range(len(plumes)):
+        xa, Ca = a.state(i)
+        xb, Cb = b.state(i)
+        assert _same(xa, xb) and _same(Ca, Cb)

@@ -142,8 +142,8 @@ def test_batch_config_null_arguments(adelib):
     import ctypes
     lib = adelib.load()
     m, t, g = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
-    assert lib.ade_batch_get_config(None, ctypes.byref(m), ctypes.byref(t), ctypes.byref(g)) == -1
-    assert lib.ade_batch_set_config(None, 0, 256, 1216, None) == -1
+    assert lib.ade_batch_get_config(None, ctypes.byref(m), ctypes.byref(t), ctypes.byref(g), ctypes.byref(g)) == -1
+    assert lib.ade_batch_set_config(None, 0, 256, 1216, 0, None) == -1
 
 
 def _field_plume():

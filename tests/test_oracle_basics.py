@@ -161,3 +161,17 @@ def test_fixed_point_roundtrip():
     # minimum image: difference words as int32
     d = (xq[0, 1].astype(np.int64) - xq[0, 0].astype(np.int64))
     assert d == 2 ** 32 // 64
+
+
+def test_stats_hand_computed(orc):
+    """Sec. 4 metrics on three particles worked by hand: C = (1, -0.5, 2), m = 0.25, reference
+    (1, 0, 1), C0 = 2.  Mass 0.25 * 2.5 = 0.625; min -0.5; max 2; errors (0, -0.5, 1):
+    L2 = sqrt(0.25 * 1.25) = sqrt(0.3125), Linf = 1, RMSE of e / C0 = sqrt((0.0625 + 0.25) / 3)."""
+    out = orc.stats([1.0, -0.5, 2.0], 0.25, C_ref=[1.0, 0.0, 1.0], C0=2.0)
+    assert out["mass"] == 0.625
+    assert out["c_min"] == -0.5 and out["c_max"] == 2.0
+    assert out["l2"] == pytest.approx(0.5590169943749474, rel=1e-15)
+    assert out["linf"] == 1.0
+    assert out["rmse"] == pytest.approx(0.3227486121839514, rel=1e-15)
+    # an explicit volume per particle replaces m in L2
+    assert orc.stats([3.0], 1.0, C_ref=[1.0], vol=4.0)["l2"] == 4.0
