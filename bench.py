@@ -92,7 +92,10 @@ MUFU_LANES_PER_SM = 16
 # corrector launch, from the ncu capture summarised in the named profile, keyed by workload and
 # walk, with the digest of the kernel sources the capture was taken of: a walk without a capture,
 # or whose sources have changed since, reports null traffic.
-TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_PER_LAUNCH = {
+    ("cube-128-h2", "direct-branch-free-trimmed-paired"): (53.71e6, "profiles/k_rate_cube128.md", "cef281b65d7181d9"),
+    ("ladder-1024-n120-r10", "direct-branch-free-paired"): (37.95e6, "profiles/k_rate_ladder1024.md", "cef281b65d7181d9"),
+}
 KERNEL_SOURCES = ("rate_walk.cuh", "rate_common.cuh", "rate.cu", "rate_pair.cu", "ade_internal.h")
 
 

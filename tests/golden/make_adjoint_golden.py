@@ -57,8 +57,8 @@ def main():
         fd.append((Jp - Jm) / (2 * e[k]))
     with open(OUT, "w") as f:
         f.write("# FP64 oracle values, written by tests/golden/make_adjoint_golden.py (see its docstring)\n")
-        f.write(f"# 2D {SIDE}^2 lattice, h = {H_DX} dx, Wendland C2, {NSTEPS} steps of Eq. 8-9; theta = {list(THETA)}, "
-                f"theta* = {list(THETA_STAR)}; target rounded to FP32\n")
+        f.write(f"# 2D {SIDE}^2 lattice, h = {H_DX} dx, Wendland C2, {NSTEPS} steps of Eq. 8-9; theta = "
+                f"{[float(t) for t in THETA]}, theta* = {[float(t) for t in THETA_STAR]}; target rounded to FP32\n")
         f.write(f"dt {kw['dt']!r}\n")
         f.write(f"J {J!r}\n")
         f.write("grad_tlm " + " ".join(repr(float(v)) for v in g) + "\n")

@@ -1,12 +1,18 @@
 """The hand-written adjoint (ade_adjoint) against the FP64 oracle: the misfit, its gradient with
 respect to (alpha_L, alpha_T, D_m) against the oracle's tangent-linear gradient and central finite
-differences, and dJ/dC0 along random directions against finite differences; bitwise independence
-of the checkpoint interval; an adjoint dot-product identity at the full 512^2 x 400-step size; the
-torch.autograd.Function wrapper."""
+differences, and dJ/dC0 along random directions against finite differences; the configured
+inversion problem (512^2, 400 steps, checkpoints every 40) against stored FP64 oracle values;
+bitwise independence of the checkpoint interval; an adjoint dot-product identity at the full
+size; the torch.autograd.Function wrapper."""
+import importlib.util
+import os
+
 import numpy as np
 import pytest
 
 from paper_2108_09488_gb300 import inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
 
 pytestmark = pytest.mark.gpu
 
@@ -42,7 +48,7 @@ def test_adjoint_against_oracle_tlm_and_fd(adelib, orc, torch_cuda):
                                      target=target, **kw)
     assert J == pytest.approx(Jo, rel=1e-5)
     for k in range(3):
-        assert abs(g[k] - go[k]) <= GRAD_TOL * max(abs(go[k]), 1e-3 * np.max(np.abs(go)))
+        assert g[k] == pytest.approx(go[k], rel=GRAD_TOL)
     # alpha_L by FP64 central differences (eps = 1e-4 relative)
     eps = 1e-4 * THETA[0]
     Jp, _ = orc.misfit(x, p.velocity, C.astype(np.float64), theta=THETA + [eps, 0, 0], target=target, **kw)
@@ -68,13 +74,48 @@ def test_adjoint_checkpoint_interval_is_bitwise_irrelevant(adelib, orc, torch_cu
 
 
 def test_adjoint_512_theta_gradient(adelib, orc, torch_cuda):
-    """The 512^2 plume (BASELINE adjoint configuration size) over 20 steps against the oracle TLM."""
+    """The 512^2 plume of the inversion problem over 20 steps against the oracle TLM."""
     p, sim, x, C, target, kw = _problem(adelib, orc, 512, 20)
     J, g, _, _ = sim.adjoint(target.astype(np.float32), 20, 40)
     Jo, go = orc.misfit_gradient_tlm(x, p.velocity, C.astype(np.float64), theta=THETA, target=target, **kw)
     assert J == pytest.approx(Jo, rel=1e-5)
-    for k in range(2):
+    for k in range(3):
         assert g[k] == pytest.approx(go[k], rel=GRAD_TOL)
+
+
+def _adjoint_golden():
+    vals = {}
+    with open(os.path.join(HERE, "golden", "adjoint_512_400.txt")) as f:
+        for line in f:
+            if not line.startswith("#"):
+                key, *v = line.split()
+                vals[key] = [float(t) for t in v]
+    return vals
+
+
+def test_adjoint_configured_problem_against_stored_oracle(adelib, orc, torch_cuda):
+    """The inversion problem at its configured size: 512^2 lattice, 400 steps, checkpoints every
+    40, target from the oracle at theta* = (2e-2, 2e-3, 1e-6).  J within 1e-5 and each component of
+    dJ/d(alpha_L, alpha_T, D_m) within 1e-4 of the FP64 oracle's tangent-linear gradient and of its
+    FP64 central differences (eps = 1e-4 theta_k), stored by tests/golden/make_adjoint_golden.py;
+    the target is recomputed here by the same function of that script."""
+    spec = importlib.util.spec_from_file_location("make_adjoint_golden",
+                                                  os.path.join(HERE, "golden", "make_adjoint_golden.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    gold = _adjoint_golden()
+    p, x, C, kw, target = mk.problem()
+    assert kw["dt"] == pytest.approx(gold["dt"][0], rel=1e-14)
+    sim = adelib.Simulation(adelib.params_for(p, dt=gold["dt"][0]), *p.initial_state())
+    J, g, _, _ = sim.adjoint(target.astype(np.float32), mk.NSTEPS, 40, want_dC0=False)
+    rel = lambda a, b: abs(a - b) / abs(b)
+    print(f"\n512^2 x 400: J rel err {rel(J, gold['J'][0]):.2e}; dJ/dtheta rel err vs TLM "
+          + ", ".join(f"{rel(g[k], gold['grad_tlm'][k]):.2e}" for k in range(3)) + "; vs FD "
+          + ", ".join(f"{rel(g[k], gold['grad_fd'][k]):.2e}" for k in range(3)))
+    assert J == pytest.approx(gold["J"][0], rel=1e-5)
+    for k in range(3):
+        assert g[k] == pytest.approx(gold["grad_tlm"][k], rel=GRAD_TOL)
+        assert g[k] == pytest.approx(gold["grad_fd"][k], rel=GRAD_TOL)
 
 
 def test_adjoint_dot_product_identity_full_size(adelib, torch_cuda):
