@@ -307,7 +307,7 @@ int ade_batch_count_pairs(ade_batch *b, long long *pairs_host, void *stream);
 int ade_batch_get_plume_info(const ade_batch *b, int plume, ade_info *info_host);
 
 /* Autotuner: times the cell build plus one evaluation of every plume for each cell-subdivision
- * policy (per-plume cost model, or 1..6 cells per support radius), work-item size (64..512
+ * policy (per-plume cost model, or 1..6 cells per support radius), work-item size (64..1024
  * particles), persistent grid size (4, 8, 16 blocks per SM) and walk (one particle per thread, or
  * the paired walk: two adjacent particles per thread, same sums), keeps the fastest and re-plans.
  * Leaves the particle state unchanged; waits; best_ms_host (may be NULL) gets the best time. */

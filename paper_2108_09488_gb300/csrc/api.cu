@@ -1845,8 +1845,8 @@ int ade_batch_autotune(ade_batch *b, double *best_ms_host, void *stream)
         }
     }
     b->subdiv_mode = best_mode;
-    const int tile_sizes[] = {64, 128, 256, 512};
-    for (int ti = 0; rc == ADE_OK && ti < 4; ++ti) {
+    const int tile_sizes[] = {64, 128, 256, 512, 1024};
+    for (int ti = 0; rc == ADE_OK && ti < 5; ++ti) {
         b->tile_size = tile_sizes[ti];
         rc = time_cfg(&ms);
         if (rc == ADE_OK && ms < best) {

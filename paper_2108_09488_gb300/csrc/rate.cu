@@ -271,9 +271,9 @@ __global__ __launch_bounds__(kTileThreads, 2) void k_rate_tiled(const uint4 *__r
 // ---------------------------------------------------------------------------------------------
 // batched plumes: persistent kernel over a queue of (plume, range) work items
 // ---------------------------------------------------------------------------------------------
-// Every CTA takes work items from an atomic counter until the list is exhausted (no CTA waits on
-// another).  An item is a range of one plume's cell-sorted particles; the plume's constants are
-// copied to shared memory once per item and each particle is evaluated with the same code as the
+// Every warp takes work items from an atomic counter until the list is exhausted (no warp waits
+// on another).  An item is a range of one plume's cell-sorted particles; the plume's constants are
+// copied to the warp's shared-memory slot when the plume changes and each particle is evaluated with the same code as the
 // single-plume direct kernel (rate_direct + epilogue), so a plume gives bit-identical results
 // whether it runs alone or in a batch.  Items are ordered by decreasing estimated cost.
 // PAIRED: each thread takes two adjacent sorted particles of the item (rate_direct_pair; a pair
@@ -287,30 +287,33 @@ __global__ __launch_bounds__(kRateThreads) void k_rate_batch(const uint4 *__rest
                                                              int ntiles, unsigned *queue,
                                                              const EpiOut out)
 {
-    __shared__ RateParams sp;
-    __shared__ int s_item;
+    // Every warp takes work items on its own (no block barrier): its plume's constants live in
+    // the warp's own shared-memory slot, refreshed when the plume changes.
+    __shared__ RateParams sp[kRateThreads / 32];
     constexpr int kWords = (int)(sizeof(RateParams) / sizeof(int));
     static_assert(sizeof(RateParams) % sizeof(int) == 0, "RateParams is copied word by word");
+    const int lane = threadIdx.x & 31;
+    RateParams &mine = sp[threadIdx.x >> 5];
     int cur = -1;
     unsigned cnt = 0u;
     for (;;) {
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(queue, 1u);
-        __syncthreads();
-        const int item = s_item;
+        int item = 0;
+        if (lane == 0) item = (int)atomicAdd(queue, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= ntiles) break;
         const BatchTile t = tiles[item];
         if (t.plume != cur) {
             const int *src = reinterpret_cast<const int *>(descs + t.plume);
-            int *dst = reinterpret_cast<int *>(&sp);
-            for (int w = threadIdx.x; w < kWords; w += kRateThreads) dst[w] = __ldg(src + w);
+            int *dst = reinterpret_cast<int *>(&mine);
+            for (int w = lane; w < kWords; w += 32) dst[w] = __ldg(src + w);
             cur = t.plume;
+            __syncwarp();
         }
-        __syncthreads();
-        const RateParams &prm = sp;
+        const RateParams &prm = mine;
         EpiOut o = out;
         if (EPI == EPI_CORRECT) o.xq = out.xq + (size_t)prm.goff * (DIM - 1);
         if (PAIRED && !COUNT) {
-            for (int k = 2 * threadIdx.x; k < t.count; k += 2 * kRateThreads) {
+            for (int k = 2 * lane; k < t.count; k += 64) {
                 const int g0 = prm.goff + t.start + k;
                 const bool v1 = k + 1 < t.count;
                 const uint4 pa0 = __ldg(Pe + g0);
@@ -335,7 +338,7 @@ __global__ __launch_bounds__(kRateThreads) void k_rate_batch(const uint4 *__rest
                 if (v1) epilogue<DIM, EPI>(g0 + 1, r1, pa1, perm, prm, o, acc);
             }
         } else {
-            for (int k = threadIdx.x; k < t.count; k += kRateThreads) {
+            for (int k = lane; k < t.count; k += 32) {
                 const int gi = prm.goff + t.start + k;
                 const uint4 pa = __ldg(Pe + gi);
                 const int cx = (int)__umulhi(pa.x - prm.back[0], (uint32_t)prm.ncx);
@@ -348,7 +351,7 @@ __global__ __launch_bounds__(kRateThreads) void k_rate_batch(const uint4 *__rest
                 epilogue<DIM, EPI>(gi, rate, pa, perm, prm, o, acc);
             }
         }
-        __syncthreads();   // sp and s_item are rewritten by the next item
+        __syncwarp();   // the warp's slot may be rewritten by its next item
     }
     if (COUNT) {
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
