@@ -85,6 +85,7 @@ struct RateParams {
     double H2d;      // FP64 support radius squared (pair counting decides support in FP64)
     int goff;        // batched plumes: first particle (caller and sorted order) of this plume
     int coff;        // batched plumes: first cell of this plume in the global cell table
+    int m1;               // -1: the multiplier of the walks' separations (see sep in rate_common.cuh)
     const uint4 *pencil;  // trimmed walks: per pencil (cy, cz) the transverse bounding box
                           // {min y, max y, min z, max z} of its particles at the cell build
 };

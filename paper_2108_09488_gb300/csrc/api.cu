@@ -641,6 +641,7 @@ int plume_constants(const ade_params *p, int n, const Derived &d, double *D, dou
     const int dm = p->dim;
     rp.pf = (float)(0.5 * (p->mass / p->rho) * kernel_kc(p->kernel, dm, d.H));
     ade::rate_pair_consts(dm, gamma, p->v, p->alpha_L, p->alpha_T, p->D_m, &rp);
+    rp.m1 = -1;
     rp.variant = d.tiles.variant == 1 ? 1 : ((p->flags & ADE_FLAG_BRANCHED) ? 2 : 0);
     if (rp.variant != 1 && (p->flags & ADE_FLAG_TRIMMED)) rp.variant = rp.variant == 2 ? 4 : 3;  // trimmed rows
     if (p->flags & ADE_FLAG_PAIRED)                                                           // paired walks

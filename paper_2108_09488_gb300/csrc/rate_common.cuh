@@ -16,6 +16,15 @@ __device__ __forceinline__ float rsqrt_ftz(float x)
 // Compensated summation (Neumaier's scheme): sum += x, with the rounding error of that addition
 // accumulated in comp.  The error is taken with Knuth's branch-free two-sum, which yields exactly
 // (sum + x) - fl(sum + x), the same value as the magnitude-ordered form, in six FP32 additions.
+// Minimum-image separation of two fixed-point words as an FP32 value: the int32 difference a - b
+// as the multiply-add a + m b with m = -1 read at run time (so it stays an integer multiply-add,
+// which this architecture issues to the FMA pipe rather than the ALU pipe), converted with
+// round-to-nearest.
+__device__ __forceinline__ float sep(uint32_t a, uint32_t b, int m)
+{
+    return (float)((int)a + m * (int)b);
+}
+
 __device__ __forceinline__ void neumaier_add(float &sum, float &comp, float x)
 {
     const float t = sum + x;

@@ -24,10 +24,11 @@ __device__ __forceinline__ unsigned in_support_fp64(int ix, int iy, int iz, cons
 struct PairConst {
     float H2, invH, sy, sz;
     float w0, w1, w2, b;
+    int m1;
     template <class P>
     __device__ __forceinline__ explicit PairConst(const P &prm)
         : H2(prm.H2), invH(prm.invH), sy(prm.sy), sz(prm.sz), w0(prm.uw[0]), w1(prm.uw[1]), w2(prm.uw[2]),
-          b(prm.ub)
+          b(prm.ub), m1(prm.m1)
     {
     }
 };
@@ -207,10 +208,11 @@ __device__ __forceinline__ void pair_range_direct(const uint4 *__restrict__ P, i
     for (int j = j0; j < j1; ++j) {
         const uint4 pb = __ldg(P + j);
         if (COUNT) cnt += in_support_fp64<DIM>((int)(pa.x - pb.x), (int)(pa.y - pb.y), (int)(pa.z - pb.z), prm);
-        float dx = (float)(int)(pa.x - pb.x);
-        float dy = (float)(int)(pa.y - pb.y);
+        const int m = DIM == 3 ? k.m1 : -1;   // as in pair_range_direct2
+        float dx = sep(pa.x, pb.x, m);
+        float dy = sep(pa.y, pb.y, m);
         float dz = 0.f;
-        if (DIM == 3) dz = (float)(int)(pa.z - pb.z);
+        if (DIM == 3) dz = sep(pa.z, pb.z, m);
         if (!ISO) {
             dy *= k.sy;
             if (DIM == 3) dz *= k.sz;
@@ -321,9 +323,10 @@ __device__ __forceinline__ float2 shape2x2(float2 w)
 struct PairConst2 {
     float2 w0, w1, w2, b, ninvH, sy, sz;
     float H2;
-    __device__ __forceinline__ explicit PairConst2(const PairConst &k)
+    int m1;     // -1 (see sep)
+    __device__ __forceinline__ explicit PairConst2(const PairConst &k, int m1_)
         : w0(f2(k.w0, k.w0)), w1(f2(k.w1, k.w1)), w2(f2(k.w2, k.w2)), b(f2(k.b, k.b)),
-          ninvH(f2(-k.invH, -k.invH)), sy(f2(k.sy, k.sy)), sz(f2(k.sz, k.sz)), H2(k.H2)
+          ninvH(f2(-k.invH, -k.invH)), sy(f2(k.sy, k.sy)), sz(f2(k.sz, k.sz)), H2(k.H2), m1(m1_)
     {
     }
 };
@@ -354,10 +357,13 @@ __device__ __forceinline__ void pair_range_direct2(const uint4 *__restrict__ P, 
     for (int t = 0; t < nt; ++t) {
         const int j = s0 + t + (MERGED && t >= n0 ? jump : 0);
         const uint4 pb = __ldg(P + j);
-        float2 dx = f2((float)(int)(pa0.x - pb.x), (float)(int)(pa1.x - pb.x));
-        float2 dy = f2((float)(int)(pa0.y - pb.y), (float)(int)(pa1.y - pb.y));
+        // 3D walks are bound by the ALU pipe, so their separations take the multiply-add form;
+        // in 2D (neither pipe saturated) a plain subtraction is cheaper
+        const int m = DIM == 3 ? k.m1 : -1;
+        float2 dx = f2(sep(pa0.x, pb.x, m), sep(pa1.x, pb.x, m));
+        float2 dy = f2(sep(pa0.y, pb.y, m), sep(pa1.y, pb.y, m));
         float2 dz = f2(0.f, 0.f);
-        if (DIM == 3) dz = f2((float)(int)(pa0.z - pb.z), (float)(int)(pa1.z - pb.z));
+        if (DIM == 3) dz = f2(sep(pa0.z, pb.z, m), sep(pa1.z, pb.z, m));
         if (!ISO) {
             dy = __fmul2_rn(dy, k.sy);
             if (DIM == 3) dz = __fmul2_rn(dz, k.sz);
@@ -425,7 +431,7 @@ __device__ void rate_direct_pair(const uint4 *__restrict__ Pe, const uint32_t *_
 {
     const int ncx = prm.ncx, ncy = prm.ncy, ncz = prm.ncz, nrows = prm.nrows;
     const PairConst kc(prm);
-    const PairConst2 k2(kc);
+    const PairConst2 k2(kc, kc.m1);
     const float2 Ca = f2(__uint_as_float(pa0.w), __uint_as_float(pa1.w));
     float2 acc = f2(0.f, 0.f), comp = f2(0.f, 0.f);
     if (TRIM) {
