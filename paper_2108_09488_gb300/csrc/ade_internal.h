@@ -170,6 +170,9 @@ struct Work {
     uint4 *P0;             // [n] sorted {x, y, z, C} at level l
     uint4 *P1;             // [n] sorted state at level l + 1/2
     uint4 *pencil = nullptr;  // [ncy * ncz] transverse bounding boxes of the pencils (NULL: not built)
+    unsigned long long *scan_flags = nullptr;  // [scan blocks] look-back flags of the one-pass scan
+                                               // (NULL: the two-launch scan)
+    uint32_t *scan_state = nullptr;            // [2] ticket counter and epoch of the one-pass scan
     double *partials;      // per-block reduction partials (state statistics)
     float4 *wpart;         // per-warp partials of the corrector (EpiOut::wpart)
     double *stats;         // {sum C, min C, max C, -, closed-form slots}
@@ -198,8 +201,9 @@ void rate_pair_consts(int dim, double gamma, const double *v, double alpha_L, do
 
 // Launchers (cells.cu, rate.cu, reduce.cu).  All return cudaGetLastError() of the launches.
 int scan_blocks(int m);
-// Kernel launches of one launch_build_cells (the scan of small grids takes two, of large three).
-int cell_build_launches(int n, int ncells);
+// Kernel launches of one launch_build_cells (the scan takes one launch with look-back flags, else
+// two, or three on large grids).
+int cell_build_launches(int n, int ncells, bool onepass);
 // count_zero: w.count[0, ncells) is known to be zero (every build leaves it zero), so the memset
 // that otherwise starts the build is skipped.
 cudaError_t launch_build_cells(int dim, const uint32_t *xq, const float *C, int n, const int *nc,

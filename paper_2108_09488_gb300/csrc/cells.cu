@@ -189,6 +189,155 @@ __global__ __launch_bounds__(kThreads) void k_scan_apply(uint32_t *__restrict__ 
     if (base <= m - 1 && m - 1 < base + kScanItems) start[m] = run;  // holder of the last element
 }
 
+// One-pass exclusive scan of count[0..m) into start[0..m] with decoupled look-back, replacing
+// k_scan_blocks + k_scan_apply where the workspace holds the look-back flags.  A block takes a
+// ticket (so every block it waits on has started), sums its tile, publishes the sum (state 1) or,
+// once it knows everything before it, its inclusive prefix (state 2), and a warp of it looks back
+// 32 tiles at a time: sums of ready tiles up to the first inclusive one give the block's offset.
+// Flags are {epoch, state, value} words; the epoch (state[1]) changes after every scan, so flags of
+// an earlier scan never count and nothing is cleared between builds.  The last block to take a
+// ticket resets the ticket counter (state[0]) and advances the epoch.  Every wait is bounded: after
+// kScanSpinMax polls the block records bit 1 in *status and uses what it has (the result is then
+// wrong and the host reports ADE_ERR_TIMEOUT); it never blocks a later block, which it still
+// publishes for.  A ticket beyond the grid (state not initialised) makes the block record bit 1
+// and return without touching memory.  Also clears count, like k_scan_apply.
+constexpr uint32_t kScanSpinMax = 1u << 22;
+
+__device__ __forceinline__ void flag_store(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long flag_load(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long flag_word(uint32_t epoch, uint32_t st, uint32_t value)
+{
+    return ((unsigned long long)epoch << 32) | ((unsigned long long)st << 30) | (unsigned long long)value;
+}
+
+constexpr int kOnepassItems = 32;                           // cells per thread
+constexpr int kOnepassTile = kThreads * kOnepassItems;       // cells per block (8192)
+
+int onepass_blocks(int m) { return (m + kOnepassTile - 1) / kOnepassTile; }
+
+__global__ __launch_bounds__(kThreads) void k_scan_onepass(uint32_t *__restrict__ count, int m,
+                                                           uint32_t *__restrict__ start,
+                                                           unsigned long long *__restrict__ flags,
+                                                           uint32_t *__restrict__ state, int nb, int *status)
+{
+    pdl_wait();
+    pdl_trigger();
+    __shared__ uint32_t s_b, s_epoch, s_prefix, total;
+    if (threadIdx.x == 0) {
+        s_b = atomicAdd(state, 1u);
+        s_epoch = *(volatile uint32_t *)(state + 1);
+    }
+    __syncthreads();
+    const uint32_t b = s_b, epoch = s_epoch;
+    if (b >= (uint32_t)nb) {   // a ticket counter that was not reset: touch nothing, report it
+        if (threadIdx.x == 0 && status) atomicOr(status, 2);
+        return;
+    }
+    const int base = (int)b * kOnepassTile + threadIdx.x * kOnepassItems;
+    uint32_t v[kOnepassItems];
+    uint32_t sum = 0u;
+    const bool whole = base + kOnepassItems <= m;   // vector loads and stores (16-byte aligned)
+    if (whole) {
+        uint4 *c4 = reinterpret_cast<uint4 *>(count + base);
+#pragma unroll
+        for (int q = 0; q < kOnepassItems / 4; ++q) {
+            const uint4 t = c4[q];
+            v[4 * q] = t.x;
+            v[4 * q + 1] = t.y;
+            v[4 * q + 2] = t.z;
+            v[4 * q + 3] = t.w;
+            c4[q] = make_uint4(0u, 0u, 0u, 0u);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kOnepassItems; ++k) {
+            v[k] = 0u;
+            if (base + k < m) {
+                v[k] = count[base + k];
+                count[base + k] = 0u;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kOnepassItems; ++k) sum += v[k];
+    uint32_t run = block_exclusive_scan(sum, &total);
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const uint32_t agg = total;
+        if (lane == 0) flag_store(flags + b, flag_word(epoch, b == 0 ? 2u : 1u, agg));
+        uint32_t prefix = 0u;
+        bool timed_out = false;
+        int j = (int)b - 1;
+        uint32_t polls = 0u;
+        while (j >= 0) {
+            const int idx = j - lane;
+            unsigned long long w = idx >= 0 ? flag_load(flags + idx) : flag_word(epoch, 2u, 0u);
+            bool ready = (uint32_t)(w >> 32) == epoch && ((uint32_t)w >> 30) != 0u;
+            if (__ballot_sync(0xffffffffu, !ready)) {   // some tile of the window has not published
+                if (++polls > kScanSpinMax) {
+                    timed_out = true;
+                    break;
+                }
+                __nanosleep(32);
+                continue;
+            }
+            const unsigned incl = __ballot_sync(0xffffffffu, ((uint32_t)w >> 30) == 2u);
+            const int first = incl ? __ffs(incl) - 1 : 31;   // the most recent inclusive tile
+            uint32_t val = lane <= first ? ((uint32_t)w & 0x3fffffffu) : 0u;
+            for (int o = 16; o > 0; o >>= 1) val += __shfl_down_sync(0xffffffffu, val, o);
+            prefix += __shfl_sync(0xffffffffu, val, 0);
+            if (incl) break;
+            j -= 32;
+        }
+        if (lane == 0) {
+            if (b > 0) flag_store(flags + b, flag_word(epoch, 2u, prefix + agg));
+            if (timed_out && status) atomicOr(status, 2);
+            s_prefix = prefix;
+        }
+    }
+    __syncthreads();
+    run += s_prefix;
+    if (whole) {
+        uint4 *s4 = reinterpret_cast<uint4 *>(start + base);
+#pragma unroll
+        for (int q = 0; q < kOnepassItems / 4; ++q) {
+            uint4 t;
+            t.x = run;
+            run += v[4 * q];
+            t.y = run;
+            run += v[4 * q + 1];
+            t.z = run;
+            run += v[4 * q + 2];
+            t.w = run;
+            run += v[4 * q + 3];
+            s4[q] = t;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kOnepassItems; ++k) {
+            if (base + k < m) start[base + k] = run;
+            run += v[k];
+        }
+    }
+    if (base <= m - 1 && m - 1 < base + kOnepassItems) start[m] = run;  // holder of the last element
+    if (threadIdx.x == 0 && b == (uint32_t)nb - 1) {
+        // every block has taken its ticket and read the epoch (all published before this look-back
+        // completed): reset the tickets and open the next epoch
+        state[0] = 0u;
+        atomicAdd(state + 1, 1u);
+    }
+}
+
 __global__ __launch_bounds__(kThreads) void k_place(const uint32_t *__restrict__ keys,
                                                     const uint32_t *__restrict__ rank, int n,
                                                     const uint32_t *__restrict__ start,
@@ -575,9 +724,9 @@ __global__ __launch_bounds__(kThreads) void k_order_batch(const uint32_t *__rest
 
 int scan_blocks(int m) { return (m + kScanTile - 1) / kScanTile; }
 
-int cell_build_launches(int n, int ncells)
+int cell_build_launches(int n, int ncells, bool onepass)
 {
-    const int scans = scan_blocks(ncells) <= kScanFoldBlocks ? 2 : 3;
+    const int scans = onepass ? 1 : (scan_blocks(ncells) <= kScanFoldBlocks ? 2 : 3);
     return scans + (n > 0 ? 3 : 0);   // k_count, k_place, k_order (or k_order_block)
 }
 
@@ -612,8 +761,15 @@ cudaError_t launch_build_cells(int dim, const uint32_t *xq, const float *C, int 
         e = launch_pdl(k_count, nb, kThreads, 0, s, xq, n, dim, nc[0], nc[1], nc[2], w.keys, w.rank, w.count,
                        w.pencil, ncells / nc[0]);
     const int sb = scan_blocks(ncells);
-    if (e == cudaSuccess) e = launch_pdl(k_scan_blocks, sb, kThreads, 0, s, w.count, ncells, w.block_sums);
-    if (sb <= kScanFoldBlocks) {
+    if (w.scan_flags) {
+        const int ob = onepass_blocks(ncells);
+        if (e == cudaSuccess)
+            e = launch_pdl(k_scan_onepass, ob, kThreads, 0, s, w.count, ncells, w.cell_start, w.scan_flags,
+                           w.scan_state, ob, w.status);
+    } else if (e == cudaSuccess)
+        e = launch_pdl(k_scan_blocks, sb, kThreads, 0, s, w.count, ncells, w.block_sums);
+    if (w.scan_flags) {
+    } else if (sb <= kScanFoldBlocks) {
         if (e == cudaSuccess)
             e = launch_pdl(k_scan_apply<true>, sb, kThreads, 0, s, w.count, ncells, w.block_sums, w.cell_start);
     } else {

@@ -168,10 +168,8 @@ def test_velocity_field_mode_time_step_skin_and_grid(adelib, orc, rule):
         k = info.cell_subdiv
         assert info.nc[0] == math.floor(k / (info.support + info.skin))
         assert info.variant == 0
-        # count, scan (2 launches up to 1024 scan blocks of 2048 cells, else 3), place, order,
-        # field gather, predictor, corrector, statistics fold
-        scans = 2 if -(-info.ncells // 2048) <= 1024 else 3
-        assert adelib.launches_per_step(ctx) == 3 + scans + 4
+        # count, the one-pass scan, place, order, field gather, predictor, corrector, statistics fold
+        assert adelib.launches_per_step(ctx) == 3 + 1 + 4
         assert nbytes >= (64 + 32) * plume.n   # caller-order and sorted V, D records + 2 sorted states
     finally:
         adelib.destroy(ctx)
