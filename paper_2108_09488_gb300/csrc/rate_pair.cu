@@ -43,8 +43,13 @@ __global__ __launch_bounds__(kRateThreads, (BF && !TRIM) ? 10 : 0) void k_rate_p
     __shared__ TrimRow srow[TRIM ? kMaxRows : 1];
     if (TRIM) stage_trim_rows(srow, prm);
     const bool paired = v1 && can_pair(cx0, cy0, cz0, cx1, cy1, cz1, prm.ncx);
+    bool coop = false;   // every lane of the warp holds a pair of one pencil: rows tested once per warp
+    if (TRIM) {
+        const int cyw = __shfl_sync(0xffffffffu, cy0, 0), czw = __shfl_sync(0xffffffffu, cz0, 0);
+        coop = __all_sync(0xffffffffu, paired && cy0 == cyw && cz0 == czw);
+    }
     if (paired) {
-        rate_direct_pair<DIM, KERNEL, ISO, TRIM, BF>(Pe, cs, pa0, pa1, cx0, cx1, cy0, cz0, prm, r0, r1, srow);
+        rate_direct_pair<DIM, KERNEL, ISO, TRIM, BF>(Pe, cs, pa0, pa1, cx0, cx1, cy0, cz0, prm, r0, r1, srow, coop);
     } else {
         r0 = rate_direct<DIM, KERNEL, ISO, false, BF, TRIM>(Pe, cs, pa0, cx0, cy0, cz0, prm, cnt, srow);
         r1 = v1 ? rate_direct<DIM, KERNEL, ISO, false, BF, TRIM>(Pe, cs, pa1, cx1, cy1, cz1, prm, cnt, srow) : 0.f;

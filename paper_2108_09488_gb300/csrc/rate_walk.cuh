@@ -407,14 +407,56 @@ __device__ __forceinline__ void pair_row2(const uint4 *__restrict__ P, int s0, i
 }
 
 // Packed compensated addition: Neumaier's scheme per half with the two-sum error term (as
-// neumaier_add), in FP32x2 instructions.
+// neumaier_add), in FP32x2 instructions; a - b is taken as fma(b, -1, a), the same correctly
+// rounded difference.
 __device__ __forceinline__ void neumaier_add2(float2 &sum, float2 &comp, float2 x)
 {
+    const float2 m1 = f2(-1.f, -1.f);
     const float2 t = __fadd2_rn(sum, x);
-    const float2 bp = __fadd2_rn(t, f2(-sum.x, -sum.y));
-    const float2 e = __fadd2_rn(__fadd2_rn(sum, f2(-(t.x - bp.x), -(t.y - bp.y))), __fadd2_rn(x, f2(-bp.x, -bp.y)));
+    const float2 bp = __ffma2_rn(sum, m1, t);                                  // t - sum
+    const float2 e = __fadd2_rn(__ffma2_rn(__ffma2_rn(bp, m1, t), m1, sum),    // sum - (t - bp)
+                                __ffma2_rn(bp, m1, x));                        // x - bp
     comp = __fadd2_rn(comp, e);
     sum = t;
+}
+
+// One trimmed row of the paired walk: cells [cx0 + floor(xa - xe), cx0 + floor(xb + xe)] of pencil
+// pidx, clipped to the row's half-width w = wx & 0xff; bit 24 of wx marks the targets' own pencil.
+template <int DIM, int KERNEL, bool ISO, bool BF>
+__device__ __forceinline__ void pair_trim_row(const uint4 *__restrict__ Pe, const uint32_t *__restrict__ cs,
+                                              int pidx, int wx, float xe, float xa, float xb, int cx0, int dcx,
+                                              int ncx, const uint4 &pa0, const uint4 &pa1, float2 Ca,
+                                              const PairConst2 &k2, float2 &acc, float2 &comp)
+{
+    const int w = wx & 0xff;
+    const int lo = cx0 + max(__float2int_rd(xa - xe), -w);
+    const int hi = cx0 + min(__float2int_rd(xb + xe), w + dcx) + 1;
+    int s0, e0, s1, e1;
+    row_ranges(cs, pidx * ncx, lo, hi, ncx, s0, e0, s1, e1);
+    float2 rs = f2(0.f, 0.f);
+    if (!BF || (wx >> 24) != 0)   // the targets' own cell row
+        pair_row2<DIM, KERNEL, ISO, true, BF>(Pe, s0, e0, s1, e1, pa0, pa1, Ca, k2, rs);
+    else
+        pair_row2<DIM, KERNEL, ISO, false, BF>(Pe, s0, e0, s1, e1, pa0, pa1, Ca, k2, rs);
+    neumaier_add2(acc, comp, rs);
+}
+
+// Twice the gap (squared, in x units^2) between the transverse interval [ylo, ylo + py] x
+// [zlo, zlo + pz] (cell fractions from the particles' cell) and the box bb of row r:
+// 2 gap = |b0 - a1| + |a0 - b1| - (b1 - b0) - (a1 - a0) per axis.
+template <int DIM>
+__device__ __forceinline__ float row_gap2(const float4 &bb, const TrimRow &r, float ylo, float yhi, float py,
+                                          float zlo, float zhi, float pz, const TrimGeom &g)
+{
+    const float ay0 = ylo - r.fdy, ay1 = yhi - r.fdy;
+    const float ey = ((fabsf(bb.x - ay1) + fabsf(ay0 - bb.y)) - ((bb.y - bb.x) + py)) * g.hy;
+    float e2 = ey * ey;
+    if (DIM == 3) {
+        const float az0 = zlo - r.fdz, az1 = zhi - r.fdz;
+        const float ez = ((fabsf(bb.z - az1) + fabsf(az0 - bb.w)) - ((bb.w - bb.z) + pz)) * g.hz;
+        e2 = fmaf(ez, ez, e2);
+    }
+    return e2;
 }
 
 // Eq. 4 at two particles of the same cell row by the paired walk; (cx0, cx1, cy, cz) their cells.
@@ -422,12 +464,17 @@ __device__ __forceinline__ void neumaier_add2(float2 &sum, float2 &comp, float2 
 // [min f, max f] against the pencil box bounds both particles' distances to the row from below,
 // and [min f_x - xe, max f_x + xe] (cells from cx0) contains both particles' own ranges -- so each
 // particle's row sum is bitwise that of rate_direct with TRIM (the extra candidates lie beyond
-// H (1 + 2^-12) of it and add exact zeros, and an empty or unreachable pencil gives a gap of
-// +inf).
+// H (1 + 2^-12) of it and add exact zeros, a row that is out of reach of one particle adds an exact
+// zero to its sum, and an empty or unreachable pencil gives a gap of +inf).
+// COOP (every lane of the warp holds a pair of the same pencil, so all lanes share the stencil
+// rows and their boxes): the rows are tested once per warp, each lane one row, against the
+// warp's transverse interval (which contains every pair's, so the same argument holds); the
+// reachable rows, in stencil order, are then walked by all lanes with the pair's own x extent.
 template <int DIM, int KERNEL, bool ISO, bool TRIM, bool BF = true>
 __device__ void rate_direct_pair(const uint4 *__restrict__ Pe, const uint32_t *__restrict__ cs,
                                  const uint4 &pa0, const uint4 &pa1, int cx0, int cx1, int cy, int cz,
-                                 const RateParams &prm, float &r0, float &r1, const TrimRow *srow = nullptr)
+                                 const RateParams &prm, float &r0, float &r1, const TrimRow *srow = nullptr,
+                                 bool coop = false)
 {
     const int ncx = prm.ncx, ncy = prm.ncy, ncz = prm.ncz, nrows = prm.nrows;
     const PairConst kc(prm);
@@ -437,39 +484,57 @@ __device__ void rate_direct_pair(const uint4 *__restrict__ Pe, const uint32_t *_
     if (TRIM) {
         const TrimSelf m0 = trim_self<DIM>(pa0, cy, cz, prm), m1 = trim_self<DIM>(pa1, cy, cz, prm);
         const TrimGeom g(prm);
-        const float ylo = fminf(m0.fy, m1.fy), yhi = fmaxf(m0.fy, m1.fy), pwy = yhi - ylo;
-        const float zlo = fminf(m0.fz, m1.fz), zhi = fmaxf(m0.fz, m1.fz), pwz = zhi - zlo;
+        float ylo = fminf(m0.fy, m1.fy), yhi = fmaxf(m0.fy, m1.fy);
+        float zlo = fminf(m0.fz, m1.fz), zhi = fmaxf(m0.fz, m1.fz);
         const int dcx = cx1 - cx0;
         // the pair's x extent in cell coordinates from cell cx0 (two particles of one cell are
         // ordered by caller index, not by position)
         const float xa = fminf(m0.fx, m1.fx + (float)dcx), xb = fmaxf(m0.fx, m1.fx + (float)dcx);
-        for (int ri = 0; ri < nrows; ++ri) {
-            const TrimRow r = srow[ri];
-            const int pidx = row_pencil<DIM>(r, m0, cy, cz, prm);
-            const float4 bb = load_box(prm, pidx);
-            // twice the gap between the pair's interval and the box: |b0 - a1| + |a0 - b1| - widths
-            const float ay0 = ylo - r.fdy, ay1 = yhi - r.fdy;
-            const float ey = ((fabsf(bb.x - ay1) + fabsf(ay0 - bb.y)) - ((bb.y - bb.x) + pwy)) * g.hy;
-            float e2 = ey * ey;
-            if (DIM == 3) {
-                const float az0 = zlo - r.fdz, az1 = zhi - r.fdz;
-                const float ez = ((fabsf(bb.z - az1) + fabsf(az0 - bb.w)) - ((bb.w - bb.z) + pwz)) * g.hz;
-                e2 = fmaf(ez, ez, e2);
+        if (coop) {
+            constexpr unsigned kFull = 0xffffffffu;
+            for (int o = 16; o > 0; o >>= 1) {
+                ylo = fminf(ylo, __shfl_xor_sync(kFull, ylo, o));
+                yhi = fmaxf(yhi, __shfl_xor_sync(kFull, yhi, o));
+                if (DIM == 3) {
+                    zlo = fminf(zlo, __shfl_xor_sync(kFull, zlo, o));
+                    zhi = fmaxf(zhi, __shfl_xor_sync(kFull, zhi, o));
+                }
             }
-            if (!(e2 < g.Hm2)) continue;      // out of reach of both (or an empty pencil)
-            const float t = g.Hm2 - e2;
-            const float xe = fmaf(t * rsqrt_ftz(t), g.inv_wx, 1.f / 4096.f);
-            const int w = r.wdd & 0xff;
-            const int lo = cx0 + max(__float2int_rd(xa - xe), -w);
-            const int hi = cx0 + min(__float2int_rd(xb + xe), w + dcx) + 1;
-            int s0, e0, s1, e1;
-            row_ranges(cs, pidx * ncx, lo, hi, ncx, s0, e0, s1, e1);
-            float2 rs = f2(0.f, 0.f);
-            if (!BF || r.off == 0)   // the targets' own cell row
-                pair_row2<DIM, KERNEL, ISO, true, BF>(Pe, s0, e0, s1, e1, pa0, pa1, Ca, k2, rs);
-            else
-                pair_row2<DIM, KERNEL, ISO, false, BF>(Pe, s0, e0, s1, e1, pa0, pa1, Ca, k2, rs);
-            neumaier_add2(acc, comp, rs);
+            const float py = yhi - ylo, pz = zhi - zlo;
+            const int lane = threadIdx.x & 31;
+            for (int rb = 0; rb < nrows; rb += 32) {
+                const int ri = rb + lane;
+                float xe = 0.f;
+                int pidx = 0, wx = 0;
+                bool reach = false;
+                if (ri < nrows) {
+                    const TrimRow r = srow[ri];
+                    pidx = row_pencil<DIM>(r, m0, cy, cz, prm);
+                    const float e2 = row_gap2<DIM>(load_box(prm, pidx), r, ylo, yhi, py, zlo, zhi, pz, g);
+                    reach = e2 < g.Hm2;
+                    const float t = fmaxf(g.Hm2 - e2, 0.f);
+                    xe = fmaf(t * rsqrt_ftz(t), g.inv_wx, 1.f / 4096.f);
+                    wx = r.wdd | (r.off == 0 ? 1 << 24 : 0);
+                }
+                for (unsigned mask = __ballot_sync(kFull, reach); mask != 0u; mask &= mask - 1u) {
+                    const int b = __ffs(mask) - 1;
+                    pair_trim_row<DIM, KERNEL, ISO, BF>(Pe, cs, __shfl_sync(kFull, pidx, b), __shfl_sync(kFull, wx, b),
+                                                        __shfl_sync(kFull, xe, b), xa, xb, cx0, dcx, ncx, pa0, pa1,
+                                                        Ca, k2, acc, comp);
+                }
+            }
+        } else {
+            const float py = yhi - ylo, pz = zhi - zlo;
+            for (int ri = 0; ri < nrows; ++ri) {
+                const TrimRow r = srow[ri];
+                const int pidx = row_pencil<DIM>(r, m0, cy, cz, prm);
+                const float e2 = row_gap2<DIM>(load_box(prm, pidx), r, ylo, yhi, py, zlo, zhi, pz, g);
+                if (!(e2 < g.Hm2)) continue;      // out of reach of both (or an empty pencil)
+                const float t = g.Hm2 - e2;
+                const float xe = fmaf(t * rsqrt_ftz(t), g.inv_wx, 1.f / 4096.f);
+                pair_trim_row<DIM, KERNEL, ISO, BF>(Pe, cs, pidx, r.wdd | (r.off == 0 ? 1 << 24 : 0), xe, xa, xb,
+                                                    cx0, dcx, ncx, pa0, pa1, Ca, k2, acc, comp);
+            }
         }
     } else {
         for (int ri = 0; ri < nrows; ++ri) {
