@@ -78,7 +78,12 @@ __global__ __launch_bounds__(kRateThreads) void k_rate(const uint4 *__restrict__
     }
     __shared__ TrimRow srow[TRIM ? kMaxRows : 1];
     if (TRIM) stage_trim_rows(srow, prm);
-    const float rate = rate_direct<DIM, KERNEL, ISO, COUNT, BF, TRIM>(Pe, cs, pa, cx, cy, cz, prm, cnt, srow);
+    bool coop = false;   // every lane of the warp in one pencil: rows tested once per warp
+    if (TRIM) {
+        const int cyw = __shfl_sync(0xffffffffu, cy, 0), czw = __shfl_sync(0xffffffffu, cz, 0);
+        coop = __all_sync(0xffffffffu, cy == cyw && cz == czw);
+    }
+    const float rate = rate_direct<DIM, KERNEL, ISO, COUNT, BF, TRIM>(Pe, cs, pa, cx, cy, cz, prm, cnt, srow, coop);
     if (valid) {
         acc.cnt = cnt;
         epilogue<DIM, EPI, PRE>(i, rate, pa, perm, prm, out, acc, a_pre, C_pre);

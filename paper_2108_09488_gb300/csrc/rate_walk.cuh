@@ -161,26 +161,21 @@ __device__ __forceinline__ float4 load_box(const RateParams &prm, int pidx)
     return __ldg(reinterpret_cast<const float4 *>(prm.pencil) + pidx);
 }
 
-// Candidate index ranges of cells [lo, hi) of the pencil row starting at cell `base` (two ranges
-// at a periodic seam).
+// Candidate index ranges of cells [lo, hi) of the pencil row starting at cell `base`: [s0, e0) and,
+// at a periodic seam (lo < 0 or hi > ncx), [s1, e1) for the wrapped part; without a seam
+// s1 = e1.  Branch-free (the lanes of a warp meet the seam at different rows), with the same four
+// cell-table reads for every lane.
 __device__ __forceinline__ void row_ranges(const uint32_t *__restrict__ cs, int base, int lo, int hi, int ncx,
                                            int &s0, int &e0, int &s1, int &e1)
 {
-    s1 = e1 = 0;
-    if (lo < 0) {
-        s0 = __ldg(cs + base + lo + ncx);
-        e0 = __ldg(cs + base + ncx);
-        s1 = __ldg(cs + base);
-        e1 = __ldg(cs + base + hi);
-    } else if (hi > ncx) {
-        s0 = __ldg(cs + base + lo);
-        e0 = __ldg(cs + base + ncx);
-        s1 = __ldg(cs + base);
-        e1 = __ldg(cs + base + hi - ncx);
-    } else {
-        s0 = __ldg(cs + base + lo);
-        e0 = __ldg(cs + base + hi);
-    }
+    const bool wl = lo < 0, wh = hi > ncx;
+    const int a0 = wl ? lo + ncx : lo;            // first piece [a0, b0)
+    const int b0 = (wl || wh) ? ncx : hi;
+    const int b1 = wl ? hi : (wh ? hi - ncx : 0); // second piece [0, b1)
+    s0 = __ldg(cs + base + a0);
+    e0 = __ldg(cs + base + b0);
+    s1 = __ldg(cs + base);
+    e1 = __ldg(cs + base + b1);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -235,17 +230,105 @@ __device__ __forceinline__ void pair_range_direct(const uint4 *__restrict__ P, i
     }
 }
 
+// Twice the gap (squared, in x units^2) between the transverse interval [ylo, yhi] x [zlo, zhi]
+// (cell fractions from the particles' cell; widths py, pz) and the box bb of row r:
+// 2 gap = |b0 - a1| + |a0 - b1| - (b1 - b0) - (a1 - a0) per axis, 0 where they overlap.
+template <int DIM>
+__device__ __forceinline__ float row_gap2(const float4 &bb, const TrimRow &r, float ylo, float yhi, float py,
+                                          float zlo, float zhi, float pz, const TrimGeom &g)
+{
+    const float ay0 = ylo - r.fdy, ay1 = yhi - r.fdy;
+    const float ey = ((fabsf(bb.x - ay1) + fabsf(ay0 - bb.y)) - ((bb.y - bb.x) + py)) * g.hy;
+    float e2 = ey * ey;
+    if (DIM == 3) {
+        const float az0 = zlo - r.fdz, az1 = zhi - r.fdz;
+        const float ez = ((fabsf(bb.z - az1) + fabsf(az0 - bb.w)) - ((bb.w - bb.z) + pz)) * g.hz;
+        e2 = fmaf(ez, ez, e2);
+    }
+    return e2;
+}
+
+// Rows tested once per warp (every lane in the same pencil, so all lanes share the stencil rows
+// and their boxes): lane l takes row rb + l, tests it against the warp's transverse interval and
+// returns through `reach` / xe / pidx / wx (bit 24 of wx marks the lanes' own pencil) the row's
+// reachability, x half-extent in cells, pencil and row word.
+template <int DIM>
+__device__ __forceinline__ bool warp_row_test(int rb, const TrimRow *srow, int nrows, const TrimSelf &me, int cy,
+                                              int cz, const RateParams &prm, const TrimGeom &g, float ylo, float yhi,
+                                              float zlo, float zhi, float &xe, int &pidx, int &wx)
+{
+    const int ri = rb + (threadIdx.x & 31);
+    xe = 0.f;
+    pidx = wx = 0;
+    if (ri >= nrows) return false;
+    const TrimRow r = srow[ri];
+    pidx = row_pencil<DIM>(r, me, cy, cz, prm);
+    const float e2 = row_gap2<DIM>(load_box(prm, pidx), r, ylo, yhi, yhi - ylo, zlo, zhi, zhi - zlo, g);
+    const float t = fmaxf(g.Hm2 - e2, 0.f);
+    xe = fmaf(t * rsqrt_ftz(t), g.inv_wx, 1.f / 4096.f);
+    wx = r.wdd | (r.off == 0 ? 1 << 24 : 0);
+    return e2 < g.Hm2;
+}
+
+// Warp-wide transverse interval [ylo, yhi] x [zlo, zhi] (in place).
+template <int DIM>
+__device__ __forceinline__ void warp_interval(float &ylo, float &yhi, float &zlo, float &zhi)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        ylo = fminf(ylo, __shfl_xor_sync(0xffffffffu, ylo, o));
+        yhi = fmaxf(yhi, __shfl_xor_sync(0xffffffffu, yhi, o));
+        if (DIM == 3) {
+            zlo = fminf(zlo, __shfl_xor_sync(0xffffffffu, zlo, o));
+            zhi = fmaxf(zhi, __shfl_xor_sync(0xffffffffu, zhi, o));
+        }
+    }
+}
+
 // Eq. 4 at one particle by the direct walk; (cx, cy, cz) is its cell.  TRIM: visit only the
 // stencil cells within reach of the particle itself (rows from srow, staged by the kernel).
+// COOP (every lane of the warp in the particle's pencil): the rows are tested once per warp
+// against the warp's transverse interval, which contains the particle's, so a row or candidate
+// that only the wider test admits lies beyond H (1 + 2^-12) of the particle and adds an exact zero:
+// the sum is bitwise that of the per-particle test.
 template <int DIM, int KERNEL, bool ISO, bool COUNT, bool BF = true, bool TRIM = false>
 __device__ float rate_direct(const uint4 *__restrict__ Pe, const uint32_t *__restrict__ cs,
                              const uint4 &pa, int cx, int cy, int cz, const RateParams &prm,
-                             unsigned &cnt, const TrimRow *srow = nullptr)
+                             unsigned &cnt, const TrimRow *srow = nullptr, bool coop = false)
 {
     const int ncx = prm.ncx, ncy = prm.ncy, ncz = prm.ncz, nrows = prm.nrows;
     const PairConst kc(prm);
     const float Ca = __uint_as_float(pa.w);
     float acc = 0.f, comp = 0.f;
+    if (TRIM && coop) {
+        const TrimSelf me = trim_self<DIM>(pa, cy, cz, prm);
+        const TrimGeom g(prm);
+        float ylo = me.fy, yhi = me.fy, zlo = me.fz, zhi = me.fz;
+        warp_interval<DIM>(ylo, yhi, zlo, zhi);
+        for (int rb = 0; rb < nrows; rb += 32) {
+            float xe;
+            int pidx, wx;
+            const bool reach = warp_row_test<DIM>(rb, srow, nrows, me, cy, cz, prm, g, ylo, yhi, zlo, zhi, xe, pidx, wx);
+            for (unsigned mask = __ballot_sync(0xffffffffu, reach); mask != 0u; mask &= mask - 1u) {
+                const int b = __ffs(mask) - 1;
+                const float xeb = __shfl_sync(0xffffffffu, xe, b);
+                const int pb = __shfl_sync(0xffffffffu, pidx, b), wb = __shfl_sync(0xffffffffu, wx, b);
+                const int w = wb & 0xff;
+                int s0, e0, s1, e1;
+                row_ranges(cs, pb * ncx, cx + max(__float2int_rd(me.fx - xeb), -w),
+                           cx + min(__float2int_rd(me.fx + xeb), w) + 1, ncx, s0, e0, s1, e1);
+                float rs = 0.f;
+                if ((wb >> 24) != 0) {                              // the particle's own cell row
+                    pair_range_direct<DIM, KERNEL, ISO, COUNT, BF, true>(Pe, s0, e0, pa, Ca, kc, prm, rs, cnt);
+                    pair_range_direct<DIM, KERNEL, ISO, COUNT, BF, true>(Pe, s1, e1, pa, Ca, kc, prm, rs, cnt);
+                } else {
+                    pair_range_direct<DIM, KERNEL, ISO, COUNT, BF, false>(Pe, s0, e0, pa, Ca, kc, prm, rs, cnt);
+                    pair_range_direct<DIM, KERNEL, ISO, COUNT, BF, false>(Pe, s1, e1, pa, Ca, kc, prm, rs, cnt);
+                }
+                neumaier_add(acc, comp, rs);
+            }
+        }
+        return prm.upf * shape_unscale<KERNEL>() * (acc + comp);
+    }
     if (TRIM) {
         const TrimSelf me = trim_self<DIM>(pa, cy, cz, prm);
         const TrimGeom g(prm);
@@ -441,24 +524,6 @@ __device__ __forceinline__ void pair_trim_row(const uint4 *__restrict__ Pe, cons
     neumaier_add2(acc, comp, rs);
 }
 
-// Twice the gap (squared, in x units^2) between the transverse interval [ylo, ylo + py] x
-// [zlo, zlo + pz] (cell fractions from the particles' cell) and the box bb of row r:
-// 2 gap = |b0 - a1| + |a0 - b1| - (b1 - b0) - (a1 - a0) per axis.
-template <int DIM>
-__device__ __forceinline__ float row_gap2(const float4 &bb, const TrimRow &r, float ylo, float yhi, float py,
-                                          float zlo, float zhi, float pz, const TrimGeom &g)
-{
-    const float ay0 = ylo - r.fdy, ay1 = yhi - r.fdy;
-    const float ey = ((fabsf(bb.x - ay1) + fabsf(ay0 - bb.y)) - ((bb.y - bb.x) + py)) * g.hy;
-    float e2 = ey * ey;
-    if (DIM == 3) {
-        const float az0 = zlo - r.fdz, az1 = zhi - r.fdz;
-        const float ez = ((fabsf(bb.z - az1) + fabsf(az0 - bb.w)) - ((bb.w - bb.z) + pz)) * g.hz;
-        e2 = fmaf(ez, ez, e2);
-    }
-    return e2;
-}
-
 // Eq. 4 at two particles of the same cell row by the paired walk; (cx0, cx1, cy, cz) their cells.
 // TRIM: one trimmed range per row serves both particles -- the pair's transverse interval
 // [min f, max f] against the pencil box bounds both particles' distances to the row from below,
@@ -492,30 +557,11 @@ __device__ void rate_direct_pair(const uint4 *__restrict__ Pe, const uint32_t *_
         const float xa = fminf(m0.fx, m1.fx + (float)dcx), xb = fmaxf(m0.fx, m1.fx + (float)dcx);
         if (coop) {
             constexpr unsigned kFull = 0xffffffffu;
-            for (int o = 16; o > 0; o >>= 1) {
-                ylo = fminf(ylo, __shfl_xor_sync(kFull, ylo, o));
-                yhi = fmaxf(yhi, __shfl_xor_sync(kFull, yhi, o));
-                if (DIM == 3) {
-                    zlo = fminf(zlo, __shfl_xor_sync(kFull, zlo, o));
-                    zhi = fmaxf(zhi, __shfl_xor_sync(kFull, zhi, o));
-                }
-            }
-            const float py = yhi - ylo, pz = zhi - zlo;
-            const int lane = threadIdx.x & 31;
+            warp_interval<DIM>(ylo, yhi, zlo, zhi);
             for (int rb = 0; rb < nrows; rb += 32) {
-                const int ri = rb + lane;
-                float xe = 0.f;
-                int pidx = 0, wx = 0;
-                bool reach = false;
-                if (ri < nrows) {
-                    const TrimRow r = srow[ri];
-                    pidx = row_pencil<DIM>(r, m0, cy, cz, prm);
-                    const float e2 = row_gap2<DIM>(load_box(prm, pidx), r, ylo, yhi, py, zlo, zhi, pz, g);
-                    reach = e2 < g.Hm2;
-                    const float t = fmaxf(g.Hm2 - e2, 0.f);
-                    xe = fmaf(t * rsqrt_ftz(t), g.inv_wx, 1.f / 4096.f);
-                    wx = r.wdd | (r.off == 0 ? 1 << 24 : 0);
-                }
+                float xe;
+                int pidx, wx;
+                const bool reach = warp_row_test<DIM>(rb, srow, nrows, m0, cy, cz, prm, g, ylo, yhi, zlo, zhi, xe, pidx, wx);
                 for (unsigned mask = __ballot_sync(kFull, reach); mask != 0u; mask &= mask - 1u) {
                     const int b = __ffs(mask) - 1;
                     pair_trim_row<DIM, KERNEL, ISO, BF>(Pe, cs, __shfl_sync(kFull, pidx, b), __shfl_sync(kFull, wx, b),
