@@ -547,6 +547,8 @@ def run_batched(args):
                                "batched_speedup": value / pp_value},
         "steps_per_s": 1e3 / ms_per_step, "interactions_per_step": all_units / args.steps,
         "roofline": roofline, "e2e": e2e, "clocks": clk,
+        "cell_build": cell_build_roof(sum(b.ns), sum(b.plume_info(i).ncells for i in range(len(plumes))), 2,
+                                      roofline["phase_ms_per_step"]["cells"]),
         "gpu_launches": b.launches_per_step() * args.steps,
         "shard": {"rank0_plumes": len(mine), "ranks": world},
     }
@@ -623,6 +625,30 @@ def run_adjoint(args):
         print(json.dumps(line))
     dist.close()
     return 0
+
+
+def hbm_peak_gbs():
+    """HBM copy bandwidth measured on this machine's GPUs (MEASURED_PEAKS.json), else 6800 GB/s."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, a device copy)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6800 GB/s"
+
+
+def cell_build_roof(n, ncells, dim, cells_ms):
+    """The cell build against HBM bandwidth.  Algorithmic bytes per particle: k_count reads the dim
+    position words and writes key and rank (4 dim + 8); k_place reads key and rank, gathers the
+    cell's start and writes the provisional slot (16); k_order reads that slot, gathers the position
+    words and C and writes the permutation and the 16-byte sorted record (4 dim + 28).  Per cell:
+    the counting atomics read and write the count (8), the scan reads it, clears it and writes the
+    start (12), k_order reads the start (4)."""
+    nbytes = n * (8 * dim + 52) + ncells * 24
+    gbs = nbytes / (cells_ms * 1e-3) / 1e9
+    peak, src = hbm_peak_gbs()
+    return {"bound": "hbm", "bytes_per_build": nbytes, "ms": cells_ms, "achieved": gbs, "peak": peak,
+            "unit": "GB/s", "frac": gbs / peak, "peak_source": src,
+            "bytes_basis": "n (8 dim + 52) + 24 ncells"}
 
 
 def measured_alu_roof(ade, dim, field, achieved, sms):
@@ -1097,6 +1123,8 @@ def run_ours(args):
         "steps_per_s": 1e3 / ms_per_step * world,
         "interactions_per_step": 2 * pairs,
         "roofline": roofline, "e2e": e2e, "clocks": clk,
+        "cell_build": cell_build_roof(plume.n, sim.info.ncells, plume.dim,
+                                      roofline["phase_ms_per_step"]["cells"]),
         "gpu_launches": launches * args.steps,
         **line_extra,
     }
