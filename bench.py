@@ -93,8 +93,10 @@ MUFU_LANES_PER_SM = 16
 # walk, with the digest of the kernel sources the capture was taken of: a walk without a capture,
 # or whose sources have changed since, reports null traffic.
 TRAFFIC_PER_LAUNCH = {
-    ("cube-128-h2", "direct-branch-free-trimmed-paired"): (53.71e6, "profiles/k_rate_cube128.md", "cef281b65d7181d9"),
-    ("ladder-1024-n120-r10", "direct-branch-free-paired"): (37.95e6, "profiles/k_rate_ladder1024.md", "cef281b65d7181d9"),
+    ("cube-128-h2", "direct-branch-free-trimmed-paired"): (53.72e6, "profiles/k_rate_cube128.md", "0d9df1f939492d19"),
+    ("ladder-1024-n120-r10", "direct-branch-free-paired"): (23.90e6, "profiles/k_rate_ladder1024.md", "0d9df1f939492d19"),
+    ("batched-64", None): (42.27e6, "profiles/k_rate_batch_batched64.md", "0d9df1f939492d19"),
+    ("paper-1m-n31k-c4", "direct-branch-free-trimmed-paired"): (16.09e6, "profiles/k_rate_paper1m.md", "0d9df1f939492d19"),
 }
 KERNEL_SOURCES = ("rate_walk.cuh", "rate_common.cuh", "rate.cu", "rate_pair.cu", "ade_internal.h")
 
