@@ -170,9 +170,8 @@ struct Work {
     uint4 *P0;             // [n] sorted {x, y, z, C} at level l
     uint4 *P1;             // [n] sorted state at level l + 1/2
     uint4 *pencil = nullptr;  // [ncy * ncz] transverse bounding boxes of the pencils (NULL: not built)
-    unsigned long long *scan_flags = nullptr;  // [scan blocks] look-back flags of the one-pass scan
-                                               // (NULL: the two-launch scan)
-    uint32_t *scan_state = nullptr;            // [2] ticket counter and epoch of the one-pass scan
+    uint32_t *tile_sums = nullptr;             // [tiles of 4096 cells, 128 B apart] totals for the one-pass scan
+                                               // (k_count adds, k_place clears; null: multi-launch scan)
     double *partials;      // per-block reduction partials (state statistics)
     float4 *wpart;         // per-warp partials of the corrector (EpiOut::wpart)
     double *stats;         // {sum C, min C, max C, -, closed-form slots}
@@ -203,6 +202,8 @@ void rate_pair_consts(int dim, double gamma, const double *v, double alpha_L, do
 int scan_blocks(int m);
 // Kernel launches of one launch_build_cells (the scan takes one launch with look-back flags, else
 // two, or three on large grids).
+int tile_blocks(int m);          // tiles of the one-pass scan
+size_t tile_sums_bytes(int m);   // their totals (one 128-byte line each)
 int cell_build_launches(int n, int ncells, bool onepass);
 // count_zero: w.count[0, ncells) is known to be zero (every build leaves it zero), so the memset
 // that otherwise starts the build is skipped.

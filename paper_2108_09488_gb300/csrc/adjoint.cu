@@ -391,12 +391,8 @@ extern "C" int ade_adjoint(ade_ctx *c, const float *C_target_dev, int nsteps, in
     const int nb = blocks(n);
     cudaStream_t s = A.s;
 
-    // frozen geometry: one cell list at the current positions (with the two-launch scan: the
-    // one-pass scan's flags are initialised by the context's own step path, not here)
-    ade::Work wb = c->w;
-    wb.scan_flags = nullptr;
-    wb.scan_state = nullptr;
-    cudaError_t e = ade::launch_build_cells(c->dim, c->xq, c->C, n, c->nc, c->ncells, wb, s);
+    // frozen geometry: one cell list at the current positions (counts and tile totals cleared first)
+    cudaError_t e = ade::launch_build_cells(c->dim, c->xq, c->C, n, c->nc, c->ncells, c->w, s);
     if (e != cudaSuccess) return ade::report_error(ADE_ERR_CUDA, cudaGetErrorString(e));
     ADJ_CK(cudaMemsetAsync(done, 0, sizeof(unsigned), s));
     k_sorted_C<<<nb, kT, 0, s>>>(ckpt, c->w.P0, n);

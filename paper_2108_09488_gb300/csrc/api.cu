@@ -305,7 +305,7 @@ void choose_tiles(int dim, int n, const Grid &g, bool iso, unsigned flags, ade::
 
 struct Layout {
     size_t keys, rank, count, block_sums, perm_tmp, perm, cell_start, P0, P1, partials, wpart, stats,
-        cf_partials, status, pairs, pencil, scan_flags, scan_state, fVc, fDAc, fDBc, fIncC, fV, fDA, fDB, fInc,
+        cf_partials, status, pairs, pencil, tile_sums, fVc, fDAc, fDBc, fIncC, fV, fDA, fDB, fInc,
         fbits, Q, Qh, total;
 };
 
@@ -338,8 +338,7 @@ Layout layout(int n, int ncells, int nb_partials, int nw_partials, int field_dim
     L.status = take(64);
     L.pairs = take(64);
     L.pencil = npencils > 0 ? take((size_t)npencils * 16) : 0;
-    L.scan_flags = take((size_t)ade::scan_blocks(ncells) * 8);
-    L.scan_state = take(64);
+    L.tile_sums = take(ade::tile_sums_bytes(ncells));
     L.fVc = L.fDAc = L.fDBc = L.fIncC = L.fV = L.fDA = L.fDB = L.fInc = L.fbits = 0;
     if (field_dim) {
         const size_t rec = (size_t)n * 16, rec3 = field_dim == 3 ? (size_t)n * 16 : 16;
@@ -470,8 +469,7 @@ int clean_counts(ade_ctx *c, cudaStream_t s)
     if (!c->count_clean) {
         ADE_CK(cudaMemsetAsync(c->w.count, 0, (size_t)c->ncells_cap * sizeof(uint32_t), s));
         // the one-pass scan's flags and {ticket, epoch}: from then on each scan leaves them valid
-        ADE_CK(cudaMemsetAsync(c->w.scan_flags, 0, (size_t)ade::scan_blocks(c->ncells_cap) * 8, s));
-        ADE_CK(cudaMemsetAsync(c->w.scan_state, 0, 2 * sizeof(uint32_t), s));
+        ADE_CK(cudaMemsetAsync(c->w.tile_sums, 0, ade::tile_sums_bytes(c->ncells_cap), s));
         c->count_clean = true;
     }
     return ADE_OK;
@@ -775,8 +773,7 @@ int ade_init_particles(ade_ctx **out, const ade_params *p, int n, uint32_t *xq_d
     c->w.status = at<int>(workspace_dev, d.L.status);
     c->w.pairs = at<unsigned long long>(workspace_dev, d.L.pairs);
     c->w.pencil = d.pencils_cap > 0 ? at<uint4>(workspace_dev, d.L.pencil) : nullptr;
-    c->w.scan_flags = at<unsigned long long>(workspace_dev, d.L.scan_flags);
-    c->w.scan_state = at<uint32_t>(workspace_dev, d.L.scan_state);
+    c->w.tile_sums = at<uint32_t>(workspace_dev, d.L.tile_sums);
 
     rc = plume_constants(p, n, d, c->D, &c->dt, c->inc, c->inc_half, &c->rp, &c->iso);
     if (rc) {
@@ -1156,10 +1153,6 @@ static int read_stats(ade_ctx *c, ade_stats *st, cudaStream_t s)
     st->t = c->t;
     st->step = c->step;
     st->pairs = c->pairs;
-    if (status & 2) {
-        st->status = ADE_ERR_TIMEOUT;
-        return fail(ADE_ERR_TIMEOUT, "cell-list scan: a bounded wait for another block gave up");
-    }
     st->status = status ? ADE_ERR_NUMERIC : ADE_OK;
     return status ? fail(ADE_ERR_NUMERIC, "non-finite concentration produced") : ADE_OK;
 }
@@ -1254,7 +1247,7 @@ int ade_launches_per_step(const ade_ctx *c, int *launches)
     if (!c || !launches) return fail(ADE_ERR_ARG, "NULL argument");
     // the cell build (count, 2 or 3 scan launches, place, order), [velocity-field gather,]
     // predictor, corrector, fold of the corrector's partials
-    *launches = ade::cell_build_launches(c->n, c->ncells, c->w.scan_flags != nullptr) + (c->n > 0 ? 3 + (c->field ? 1 : 0) : 0);
+    *launches = ade::cell_build_launches(c->n, c->ncells, c->w.tile_sums != nullptr) + (c->n > 0 ? 3 + (c->field ? 1 : 0) : 0);
     return ADE_OK;
 }
 
@@ -2354,7 +2347,7 @@ int ade_sweep_launches_per_step(const ade_sweep *sw, int *launches)
     if (!sw || !launches) return fail(ADE_ERR_ARG, "NULL argument");
     // the cell build (count, 2 or 3 scan launches, place, order), gather; one predictor and one
     // corrector per group
-    *launches = ade::cell_build_launches(sw->n, sw->ncells, sw->w.scan_flags != nullptr) + (sw->n > 0 ? 1 + 2 * (int)sw->groups.size() : 0);
+    *launches = ade::cell_build_launches(sw->n, sw->ncells, sw->w.tile_sums != nullptr) + (sw->n > 0 ? 1 + 2 * (int)sw->groups.size() : 0);
     return ADE_OK;
 }
 

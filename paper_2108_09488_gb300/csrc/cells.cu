@@ -9,7 +9,8 @@
 // the particle set:
 //   k_count   key of every particle; atomic count per cell (the returned slot is a provisional
 //             rank of the particle inside its cell)
-//   scan      exclusive scan of the counts -> cell_start[0..ncells] (three launches)
+//   scan      exclusive scan of the counts -> cell_start[0..ncells]: one launch over tiles of 4096
+//             cells whose totals k_count accumulated (two or three launches without them)
 //   k_place   provisional position cell_start[key] + rank
 //   k_order   one thread per cell sorts its segment by caller index (insertion sort; cells hold a
 //             handful of particles) and writes the sorted copy {x, y, z, C}; cells of more than
@@ -46,23 +47,60 @@ __device__ __forceinline__ uint32_t cell_key(const uint32_t *__restrict__ xq, in
 
 constexpr int kThreads = 256;
 constexpr uint32_t kInfBits = 0x7f800000u;   // +inf: the lower bound of an empty pencil box
+constexpr int kTileItems = 16;                        // cells per thread of the one-pass scan
+constexpr int kTileCells = kThreads * kTileItems;     // cells per tile (one scan block): 4096
+constexpr int kTileStride = 32;   // words between two tile totals: one 128-byte line each, so the
+                                  // totals' atomics spread over the L2 slices
+constexpr int kTileWindow = 8;    // tiles a block aggregates in shared memory (from its lowest)
 
 __global__ __launch_bounds__(kThreads) void k_count(const uint32_t *__restrict__ xq, int n, int dim,
                                                     int ncx, int ncy, int ncz,
                                                     uint32_t *__restrict__ keys,
                                                     uint32_t *__restrict__ rank,
                                                     uint32_t *__restrict__ count,
-                                                    uint4 *__restrict__ pencil, int npencils)
+                                                    uint4 *__restrict__ pencil, int npencils,
+                                                    uint32_t *__restrict__ tile_sums)
 {
     pdl_wait();
     pdl_trigger();
     const int i = blockIdx.x * kThreads + threadIdx.x;
     if (pencil)   // empty boxes {min y, max y, min z, max z} = {+inf, 0, +inf, 0}: k_order merges into them
         for (int q = i; q < npencils; q += gridDim.x * kThreads) pencil[q] = make_uint4(kInfBits, 0u, kInfBits, 0u);
-    if (i >= n) return;
-    const uint32_t key = cell_key(xq, n, i, dim, ncx, ncy, ncz);
-    keys[i] = key;
-    rank[i] = atomicAdd(count + key, 1u);
+    uint32_t tile = 0xffffffffu;
+    if (i < n) {
+        const uint32_t key = cell_key(xq, n, i, dim, ncx, ncy, ncz);
+        keys[i] = key;
+        rank[i] = atomicAdd(count + key, 1u);
+        tile = key / (uint32_t)kTileCells;
+    }
+    if (!tile_sums) return;
+    // Every particle also counts toward its tile's total.  Particles of a block mostly fall in a
+    // few neighbouring tiles: a warp whose particles share one tile adds once, the block sums
+    // tiles [t0, t0 + kTileWindow) in shared memory (t0 its lowest tile) and adds each once.
+    __shared__ uint32_t s_win[kTileWindow], s_t0;
+    const int lane = threadIdx.x & 31;
+    uint32_t lo = tile;
+    for (int o = 16; o > 0; o >>= 1) lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    if (threadIdx.x < kTileWindow) s_win[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) s_t0 = 0xffffffffu;
+    __syncthreads();
+    if (lane == 0) atomicMin(&s_t0, lo);
+    __syncthreads();
+    const uint32_t t0 = s_t0;
+    const bool one = __all_sync(0xffffffffu, tile == lo || tile == 0xffffffffu);
+    if (one) {
+        const uint32_t cnt = (uint32_t)__popc(__ballot_sync(0xffffffffu, tile != 0xffffffffu));
+        if (lane == 0 && cnt) {
+            if (lo - t0 < (uint32_t)kTileWindow) atomicAdd(&s_win[lo - t0], cnt);
+            else atomicAdd(tile_sums + (size_t)lo * kTileStride, cnt);
+        }
+    } else if (tile != 0xffffffffu) {
+        if (tile - t0 < (uint32_t)kTileWindow) atomicAdd(&s_win[tile - t0], 1u);
+        else atomicAdd(tile_sums + (size_t)tile * kTileStride, 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < kTileWindow && s_win[threadIdx.x])
+        atomicAdd(tile_sums + (size_t)(t0 + threadIdx.x) * kTileStride, s_win[threadIdx.x]);
 }
 
 // Three-launch exclusive scan of count[0..m) into start[0..m] (start[m] = total).
@@ -189,68 +227,31 @@ __global__ __launch_bounds__(kThreads) void k_scan_apply(uint32_t *__restrict__ 
     if (base <= m - 1 && m - 1 < base + kScanItems) start[m] = run;  // holder of the last element
 }
 
-// One-pass exclusive scan of count[0..m) into start[0..m] with decoupled look-back, replacing
-// k_scan_blocks + k_scan_apply where the workspace holds the look-back flags.  A block takes a
-// ticket (so every block it waits on has started), sums its tile, publishes the sum (state 1) or,
-// once it knows everything before it, its inclusive prefix (state 2), and a warp of it looks back
-// 32 tiles at a time: sums of ready tiles up to the first inclusive one give the block's offset.
-// Flags are {epoch, state, value} words; the epoch (state[1]) changes after every scan, so flags of
-// an earlier scan never count and nothing is cleared between builds.  The last block to take a
-// ticket resets the ticket counter (state[0]) and advances the epoch.  Every wait is bounded: after
-// kScanSpinMax polls the block records bit 1 in *status and uses what it has (the result is then
-// wrong and the host reports ADE_ERR_TIMEOUT); it never blocks a later block, which it still
-// publishes for.  A ticket beyond the grid (state not initialised) makes the block record bit 1
-// and return without touching memory.  Also clears count, like k_scan_apply.
-constexpr uint32_t kScanSpinMax = 1u << 22;
-
-__device__ __forceinline__ void flag_store(unsigned long long *p, unsigned long long v)
-{
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long flag_load(const unsigned long long *p)
-{
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ unsigned long long flag_word(uint32_t epoch, uint32_t st, uint32_t value)
-{
-    return ((unsigned long long)epoch << 32) | ((unsigned long long)st << 30) | (unsigned long long)value;
-}
-
-constexpr int kOnepassItems = 32;                           // cells per thread
-constexpr int kOnepassTile = kThreads * kOnepassItems;       // cells per block (8192)
-
-int onepass_blocks(int m) { return (m + kOnepassTile - 1) / kOnepassTile; }
-
-__global__ __launch_bounds__(kThreads) void k_scan_onepass(uint32_t *__restrict__ count, int m,
-                                                           uint32_t *__restrict__ start,
-                                                           unsigned long long *__restrict__ flags,
-                                                           uint32_t *__restrict__ state, int nb, int *status)
+// One-pass exclusive scan of count[0..m) into start[0..m] (start[m] = total), replacing
+// k_scan_blocks + k_scan_apply where the workspace holds the tile totals.  k_count has already
+// added every particle to the total of its key's tile of kTileCells cells (tile_sums), so a block
+// needs no other block: it sums the totals of the tiles before its own (its offset), scans its
+// tile's counts and writes their starts.  No block waits on another.  Also clears count, like
+// k_scan_apply; k_place clears the tile totals once every block has read them.
+__global__ __launch_bounds__(kThreads) void k_scan_tiles(uint32_t *__restrict__ count, int m,
+                                                         uint32_t *__restrict__ start,
+                                                         const uint32_t *__restrict__ tile_sums)
 {
     pdl_wait();
     pdl_trigger();
-    __shared__ uint32_t s_b, s_epoch, s_prefix, total;
-    if (threadIdx.x == 0) {
-        s_b = atomicAdd(state, 1u);
-        s_epoch = *(volatile uint32_t *)(state + 1);
-    }
-    __syncthreads();
-    const uint32_t b = s_b, epoch = s_epoch;
-    if (b >= (uint32_t)nb) {   // a ticket counter that was not reset: touch nothing, report it
-        if (threadIdx.x == 0 && status) atomicOr(status, 2);
-        return;
-    }
-    const int base = (int)b * kOnepassTile + threadIdx.x * kOnepassItems;
-    uint32_t v[kOnepassItems];
-    uint32_t sum = 0u;
-    const bool whole = base + kOnepassItems <= m;   // vector loads and stores (16-byte aligned)
+    __shared__ uint32_t s_part[kThreads / 32], total;
+    const int b = blockIdx.x;
+    uint32_t off = 0u;
+    for (int q = threadIdx.x; q < b; q += kThreads) off += tile_sums[(size_t)q * kTileStride];
+    for (int o = 16; o > 0; o >>= 1) off += __shfl_down_sync(0xffffffffu, off, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = off;
+    const int base = b * kTileCells + threadIdx.x * kTileItems;
+    uint32_t v[kTileItems];
+    const bool whole = base + kTileItems <= m;   // vector loads and stores (16-byte aligned)
     if (whole) {
         uint4 *c4 = reinterpret_cast<uint4 *>(count + base);
 #pragma unroll
-        for (int q = 0; q < kOnepassItems / 4; ++q) {
+        for (int q = 0; q < kTileItems / 4; ++q) {
             const uint4 t = c4[q];
             v[4 * q] = t.x;
             v[4 * q + 1] = t.y;
@@ -260,7 +261,7 @@ __global__ __launch_bounds__(kThreads) void k_scan_onepass(uint32_t *__restrict_
         }
     } else {
 #pragma unroll
-        for (int k = 0; k < kOnepassItems; ++k) {
+        for (int k = 0; k < kTileItems; ++k) {
             v[k] = 0u;
             if (base + k < m) {
                 v[k] = count[base + k];
@@ -268,49 +269,18 @@ __global__ __launch_bounds__(kThreads) void k_scan_onepass(uint32_t *__restrict_
             }
         }
     }
+    uint32_t sum = 0u;
 #pragma unroll
-    for (int k = 0; k < kOnepassItems; ++k) sum += v[k];
-    uint32_t run = block_exclusive_scan(sum, &total);
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        const uint32_t agg = total;
-        if (lane == 0) flag_store(flags + b, flag_word(epoch, b == 0 ? 2u : 1u, agg));
-        uint32_t prefix = 0u;
-        bool timed_out = false;
-        int j = (int)b - 1;
-        uint32_t polls = 0u;
-        while (j >= 0) {
-            const int idx = j - lane;
-            unsigned long long w = idx >= 0 ? flag_load(flags + idx) : flag_word(epoch, 2u, 0u);
-            bool ready = (uint32_t)(w >> 32) == epoch && ((uint32_t)w >> 30) != 0u;
-            if (__ballot_sync(0xffffffffu, !ready)) {   // some tile of the window has not published
-                if (++polls > kScanSpinMax) {
-                    timed_out = true;
-                    break;
-                }
-                __nanosleep(32);
-                continue;
-            }
-            const unsigned incl = __ballot_sync(0xffffffffu, ((uint32_t)w >> 30) == 2u);
-            const int first = incl ? __ffs(incl) - 1 : 31;   // the most recent inclusive tile
-            uint32_t val = lane <= first ? ((uint32_t)w & 0x3fffffffu) : 0u;
-            for (int o = 16; o > 0; o >>= 1) val += __shfl_down_sync(0xffffffffu, val, o);
-            prefix += __shfl_sync(0xffffffffu, val, 0);
-            if (incl) break;
-            j -= 32;
-        }
-        if (lane == 0) {
-            if (b > 0) flag_store(flags + b, flag_word(epoch, 2u, prefix + agg));
-            if (timed_out && status) atomicOr(status, 2);
-            s_prefix = prefix;
-        }
-    }
-    __syncthreads();
-    run += s_prefix;
+    for (int k = 0; k < kTileItems; ++k) sum += v[k];
+    uint32_t run = block_exclusive_scan(sum, &total);   // its barriers also publish s_part
+    uint32_t boff = 0u;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) boff += s_part[w];
+    run += boff;
     if (whole) {
         uint4 *s4 = reinterpret_cast<uint4 *>(start + base);
 #pragma unroll
-        for (int q = 0; q < kOnepassItems / 4; ++q) {
+        for (int q = 0; q < kTileItems / 4; ++q) {
             uint4 t;
             t.x = run;
             run += v[4 * q];
@@ -324,27 +294,24 @@ __global__ __launch_bounds__(kThreads) void k_scan_onepass(uint32_t *__restrict_
         }
     } else {
 #pragma unroll
-        for (int k = 0; k < kOnepassItems; ++k) {
+        for (int k = 0; k < kTileItems; ++k) {
             if (base + k < m) start[base + k] = run;
             run += v[k];
         }
     }
-    if (base <= m - 1 && m - 1 < base + kOnepassItems) start[m] = run;  // holder of the last element
-    if (threadIdx.x == 0 && b == (uint32_t)nb - 1) {
-        // every block has taken its ticket and read the epoch (all published before this look-back
-        // completed): reset the tickets and open the next epoch
-        state[0] = 0u;
-        atomicAdd(state + 1, 1u);
-    }
+    if (base <= m - 1 && m - 1 < base + kTileItems) start[m] = run;  // holder of the last element
 }
 
 __global__ __launch_bounds__(kThreads) void k_place(const uint32_t *__restrict__ keys,
                                                     const uint32_t *__restrict__ rank, int n,
                                                     const uint32_t *__restrict__ start,
-                                                    uint32_t *__restrict__ perm_tmp)
+                                                    uint32_t *__restrict__ perm_tmp,
+                                                    uint32_t *__restrict__ tile_sums, int ntiles)
 {
     pdl_wait();
     pdl_trigger();
+    if (tile_sums && blockIdx.x == 0)   // the scan has read them: clear for the next build
+        for (int q = threadIdx.x; q < ntiles; q += kThreads) tile_sums[(size_t)q * kTileStride] = 0u;
     const int i = blockIdx.x * kThreads + threadIdx.x;
     if (i >= n) return;
     const uint32_t pos = __ldg(start + __ldg(keys + i)) + __ldg(rank + i);
@@ -724,6 +691,9 @@ __global__ __launch_bounds__(kThreads) void k_order_batch(const uint32_t *__rest
 
 int scan_blocks(int m) { return (m + kScanTile - 1) / kScanTile; }
 
+int tile_blocks(int m) { return (m + kTileCells - 1) / kTileCells; }
+size_t tile_sums_bytes(int m) { return (size_t)tile_blocks(m) * kTileStride * sizeof(uint32_t); }
+
 int cell_build_launches(int n, int ncells, bool onepass)
 {
     const int scans = onepass ? 1 : (scan_blocks(ncells) <= kScanFoldBlocks ? 2 : 3);
@@ -744,7 +714,7 @@ cudaError_t launch_build_cells_batch(int dim, const uint32_t *xq, const float *C
     k_scan_top<<<1, kThreads, 0, s>>>(w.block_sums, sb);
     k_scan_apply<false><<<sb, kThreads, 0, s>>>(w.count, ncells, w.block_sums, w.cell_start);
     if (nb > 0) {
-        k_place<<<nb, kThreads, 0, s>>>(w.keys, w.rank, n, w.cell_start, w.perm_tmp);
+        k_place<<<nb, kThreads, 0, s>>>(w.keys, w.rank, n, w.cell_start, w.perm_tmp, nullptr, 0);
         k_order_batch<<<(ncells + kThreads - 1) / kThreads, kThreads, 0, s>>>(
             w.cell_start, ncells, w.perm_tmp, xq, C, n, dim, descs, plume_of, w.perm, w.P0);
     }
@@ -754,31 +724,32 @@ cudaError_t launch_build_cells_batch(int dim, const uint32_t *xq, const float *C
 cudaError_t launch_build_cells(int dim, const uint32_t *xq, const float *C, int n, const int *nc,
                                int ncells, const Work &w, cudaStream_t s, bool count_zero)
 {
+    const int nt = tile_blocks(ncells);
     cudaError_t e = count_zero ? cudaSuccess : cudaMemsetAsync(w.count, 0, (size_t)ncells * sizeof(uint32_t), s);
+    if (e == cudaSuccess && !count_zero && w.tile_sums)
+        e = cudaMemsetAsync(w.tile_sums, 0, (size_t)nt * kTileStride * 4, s);
     if (e != cudaSuccess) return e;
     const int nb = (n + kThreads - 1) / kThreads;
     if (nb > 0 && e == cudaSuccess)
         e = launch_pdl(k_count, nb, kThreads, 0, s, xq, n, dim, nc[0], nc[1], nc[2], w.keys, w.rank, w.count,
-                       w.pencil, ncells / nc[0]);
+                       w.pencil, ncells / nc[0], w.tile_sums);
     const int sb = scan_blocks(ncells);
-    if (w.scan_flags) {
-        const int ob = onepass_blocks(ncells);
+    if (w.tile_sums) {
         if (e == cudaSuccess)
-            e = launch_pdl(k_scan_onepass, ob, kThreads, 0, s, w.count, ncells, w.cell_start, w.scan_flags,
-                           w.scan_state, ob, w.status);
-    } else if (e == cudaSuccess)
-        e = launch_pdl(k_scan_blocks, sb, kThreads, 0, s, w.count, ncells, w.block_sums);
-    if (w.scan_flags) {
+            e = launch_pdl(k_scan_tiles, nt, kThreads, 0, s, w.count, ncells, w.cell_start,
+                           (const uint32_t *)w.tile_sums);
     } else if (sb <= kScanFoldBlocks) {
+        if (e == cudaSuccess) e = launch_pdl(k_scan_blocks, sb, kThreads, 0, s, w.count, ncells, w.block_sums);
         if (e == cudaSuccess)
             e = launch_pdl(k_scan_apply<true>, sb, kThreads, 0, s, w.count, ncells, w.block_sums, w.cell_start);
     } else {
+        if (e == cudaSuccess) e = launch_pdl(k_scan_blocks, sb, kThreads, 0, s, w.count, ncells, w.block_sums);
         if (e == cudaSuccess) e = launch_pdl(k_scan_top, 1, kThreads, 0, s, w.block_sums, sb);
         if (e == cudaSuccess)
             e = launch_pdl(k_scan_apply<false>, sb, kThreads, 0, s, w.count, ncells, w.block_sums, w.cell_start);
     }
     if (nb > 0 && e == cudaSuccess) {
-        e = launch_pdl(k_place, nb, kThreads, 0, s, w.keys, w.rank, n, w.cell_start, w.perm_tmp);
+        e = launch_pdl(k_place, nb, kThreads, 0, s, w.keys, w.rank, n, w.cell_start, w.perm_tmp, w.tile_sums, nt);
         if (e != cudaSuccess) return e;
         if ((long long)n >= 16ll * ncells)   // many particles per cell: one block per cell
             e = launch_pdl(k_order_block, ncells, kThreads, 0, s, w.cell_start, ncells, w.perm_tmp, xq, C, n,
