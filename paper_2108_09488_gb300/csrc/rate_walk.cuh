@@ -352,30 +352,30 @@ __device__ float rate_direct(const uint4 *__restrict__ Pe, const uint32_t *__res
             }
             neumaier_add(acc, comp, rs);
         }
-        return prm.upf * shape_unscale<KERNEL>() * (acc + comp);
-    }
-    for (int ri = 0; ri < nrows; ++ri) {
-        const StencilRow row = prm.rows[ri];
-        int yy = cy + row.dy;
-        yy += (yy < 0) ? ncy : 0;
-        yy -= (yy >= ncy) ? ncy : 0;
-        int zz = 0;
-        if (DIM == 3) {
-            zz = cz + row.dz;
-            zz += (zz < 0) ? ncz : 0;
-            zz -= (zz >= ncz) ? ncz : 0;
+    } else {
+        for (int ri = 0; ri < nrows; ++ri) {
+            const StencilRow row = prm.rows[ri];
+            int yy = cy + row.dy;
+            yy += (yy < 0) ? ncy : 0;
+            yy -= (yy >= ncy) ? ncy : 0;
+            int zz = 0;
+            if (DIM == 3) {
+                zz = cz + row.dz;
+                zz += (zz < 0) ? ncz : 0;
+                zz -= (zz >= ncz) ? ncz : 0;
+            }
+            int s0, e0, s1, e1;
+            row_ranges(cs, (zz * ncy + yy) * ncx, cx - (int)row.w, cx + row.w + 1, ncx, s0, e0, s1, e1);
+            float rs = 0.f;
+            if (row.dy == 0 && (DIM == 2 || row.dz == 0)) {      // the particle's own cell row
+                pair_range_direct<DIM, KERNEL, ISO, COUNT, BF, true>(Pe, s0, e0, pa, Ca, kc, prm, rs, cnt);
+                pair_range_direct<DIM, KERNEL, ISO, COUNT, BF, true>(Pe, s1, e1, pa, Ca, kc, prm, rs, cnt);
+            } else {
+                pair_range_direct<DIM, KERNEL, ISO, COUNT, BF, false>(Pe, s0, e0, pa, Ca, kc, prm, rs, cnt);
+                pair_range_direct<DIM, KERNEL, ISO, COUNT, BF, false>(Pe, s1, e1, pa, Ca, kc, prm, rs, cnt);
+            }
+            neumaier_add(acc, comp, rs);
         }
-        int s0, e0, s1, e1;
-        row_ranges(cs, (zz * ncy + yy) * ncx, cx - (int)row.w, cx + row.w + 1, ncx, s0, e0, s1, e1);
-        float rs = 0.f;
-        if (row.dy == 0 && (DIM == 2 || row.dz == 0)) {      // the particle's own cell row
-            pair_range_direct<DIM, KERNEL, ISO, COUNT, BF, true>(Pe, s0, e0, pa, Ca, kc, prm, rs, cnt);
-            pair_range_direct<DIM, KERNEL, ISO, COUNT, BF, true>(Pe, s1, e1, pa, Ca, kc, prm, rs, cnt);
-        } else {
-            pair_range_direct<DIM, KERNEL, ISO, COUNT, BF, false>(Pe, s0, e0, pa, Ca, kc, prm, rs, cnt);
-            pair_range_direct<DIM, KERNEL, ISO, COUNT, BF, false>(Pe, s1, e1, pa, Ca, kc, prm, rs, cnt);
-        }
-        neumaier_add(acc, comp, rs);
     }
     return prm.upf * shape_unscale<KERNEL>() * (acc + comp);
 }
