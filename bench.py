@@ -93,12 +93,15 @@ MUFU_LANES_PER_SM = 16
 # walk, with the digest of the kernel sources the capture was taken of: a walk without a capture,
 # or whose sources have changed since, reports null traffic.
 TRAFFIC_PER_LAUNCH = {
-    ("cube-128-h2", "direct-branch-free-trimmed-paired"): (53.72e6, "profiles/k_rate_cube128.md", "0d9df1f939492d19"),
-    ("ladder-1024-n120-r10", "direct-branch-free-paired"): (23.90e6, "profiles/k_rate_ladder1024.md", "0d9df1f939492d19"),
-    ("batched-64", None): (42.27e6, "profiles/k_rate_batch_batched64.md", "0d9df1f939492d19"),
-    ("paper-1m-n31k-c4", "direct-branch-free-trimmed-paired"): (16.09e6, "profiles/k_rate_paper1m.md", "0d9df1f939492d19"),
+    ("cube-128-h2", "direct-branch-free-trimmed-paired"): (53.73e6, "profiles/k_rate_cube128.md", "05e611b359adae95"),
+    ("ladder-1024-n120-r10", "direct-branch-free-paired"): (23.88e6, "profiles/k_rate_ladder1024.md", "05e611b359adae95"),
+    ("batched-64", None): (42.26e6, "profiles/k_rate_batch_batched64.md", "05e611b359adae95"),
+    ("paper-1m-n31k-c4", "direct-branch-free-trimmed-paired"): (16.10e6, "profiles/k_rate_paper1m.md", "05e611b359adae95"),
+    ("field-1024-n120-r10", "velocity-field-direct"): (82.34e6, "profiles/k_rate_field_field1024.md", "05e611b359adae95"),
+    ("sweep-512-8", None): (18.25e6, "profiles/k_rate_sweep_sweep512.md", "05e611b359adae95"),
 }
-KERNEL_SOURCES = ("rate_walk.cuh", "rate_common.cuh", "rate.cu", "rate_pair.cu", "ade_internal.h")
+KERNEL_SOURCES = ("rate_walk.cuh", "rate_common.cuh", "rate.cu", "rate_pair.cu", "rate_field.cu", "sweep.cu",
+                  "ade_internal.h")
 
 
 def kernel_digest():
