@@ -97,6 +97,28 @@ def test_cells_bit_exact_every_subdivision(lib, orc, k):
     assert np.array_equal(perm, perm_o) and np.array_equal(cs, cs_o)
 
 
+@pytest.mark.parametrize("order", ["lattice", "shuffled"])
+def test_cells_bit_exact_many_scan_tiles(lib, orc, order):
+    """A sparse 3D grid of 240^3 = 13.8 M cells (thousands of one-pass scan tiles) over 512,000
+    particles, in lattice order (a block's particles in one or two tiles) and in a seeded shuffled
+    order (every warp's particles spread over many tiles), bit-exact against the oracle's counting
+    sort; built twice, so the second build runs on the counts and tile totals the first one
+    cleared."""
+    plume = _plume(dim=3, side=80, h_dx=1.0)
+    xq, C = plume.initial_state()
+    if order == "shuffled":
+        p = np.random.default_rng(11).permutation(xq.shape[1])
+        xq, C = np.ascontiguousarray(xq[:, p]), np.ascontiguousarray(C[p])
+    sim = _sim(lib, plume, xq, C, cell_subdiv=6)
+    assert sim.info.ncells == 240 ** 3
+    key = orc.cell_keys(xq, np.array(sim.info.nc))
+    perm_o, cs_o = orc.sort_cells(key, sim.info.ncells)
+    for _ in range(2):
+        sim.build_cells()
+        perm, cs = sim.cells()
+        assert np.array_equal(perm, perm_o) and np.array_equal(cs, cs_o)
+
+
 # ADE_FLAG_TILED, _DIRECT, _BRANCHED, the two direct walks with _TRIMMED rows, and the _PAIRED
 # branch-free walk (full and trimmed rows)
 VARIANTS = {"tiled": 2, "direct": 1, "branched": 4, "direct-trimmed": 9, "branched-trimmed": 12,
