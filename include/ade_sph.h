@@ -41,7 +41,8 @@ extern "C" {
 #define ADE_ERR_ARG (-1)      /* invalid argument or unsupported configuration */
 #define ADE_ERR_CUDA (-2)     /* a CUDA runtime call failed */
 #define ADE_ERR_NUMERIC (-3)  /* a NaN or Inf concentration was produced */
-#define ADE_ERR_TIMEOUT (-4)  /* a bounded device wait gave up */
+#define ADE_ERR_TIMEOUT (-4)  /* a bounded device wait gave up (reserved: no kernel of this
+                                 * version waits on another block) */
 #define ADE_ERR_CAPACITY (-5) /* workspace or a static limit too small */
 #define ADE_ERR_STATE (-6)    /* call out of order (e.g. no particles bound) */
 
@@ -174,9 +175,9 @@ int ade_run(ade_ctx *ctx, int nsteps, ade_stats *stats_host, void *stream);
  * the statistics} (milliseconds).  Used for per-kernel roofline measurements. */
 int ade_step_timed(ade_ctx *ctx, double *phase_ms_host, void *stream);
 
-/* Kernel launches one step enqueues: the cell build (count, two scan launches -- three above 1024
- * scan blocks of 2048 cells --, placement, ordering), the velocity-field gather in velocity-field
- * mode, the two rate launches and the statistics fold. */
+/* Kernel launches one step enqueues: the cell build (count, one scan launch over tiles of 4096
+ * cells, placement, ordering), the velocity-field gather in velocity-field mode, the two rate
+ * launches and the statistics fold. */
 int ade_launches_per_step(const ade_ctx *ctx, int *launches);
 
 /* FP64 mass, min and max of the current concentrations (recomputed from C, so a caller's own

@@ -2153,6 +2153,7 @@ int ade_sweep_init(ade_sweep **out, const ade_params *p, int n, int ntheta, cons
     sw->w.perm_tmp = at<uint32_t>(workspace_dev, W.perm_tmp);
     sw->w.perm = at<uint32_t>(workspace_dev, W.perm);
     sw->w.cell_start = at<uint32_t>(workspace_dev, W.cell_start);
+    sw->w.tile_sums = at<uint32_t>(workspace_dev, W.tile_sums);   // cleared with the counts every build
     sw->w.P0 = at<uint4>(workspace_dev, W.P0);
     sw->w.P1 = at<uint4>(workspace_dev, W.P1);
     sw->w.partials = at<double>(workspace_dev, W.partials);

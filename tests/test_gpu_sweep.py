@@ -113,8 +113,8 @@ def test_sweep_run_graph_equals_step_bitwise_and_stats(lib):
         c = Cb[k].astype(np.float64)
         assert st[k].mass == pytest.approx(plume.mass * c.sum(), rel=1e-12)
         assert st[k].c_min == c.min() and st[k].c_max == c.max() and st[k].status == 0
-    scans = 2 if -(-a.info.ncells // 2048) <= 1024 else 3    # the cell build's scan launches
-    assert a.launches_per_step() == 4 + scans + 2 * 3
+    # count, the one-pass scan, place, order; the sets' gather; 2 per group (3 groups)
+    assert a.launches_per_step() == 4 + 1 + 2 * 3
 
 
 def test_sweep_matches_single_plume_contexts(lib):

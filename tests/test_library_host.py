@@ -269,8 +269,8 @@ def test_sweep_host_validation_and_info(adelib, orc):
         assert info.dt == pytest.approx(min(dts), rel=1e-14)
         assert info.tile[0] == 2                      # 12 sets = one group of 8 + one of 4
         v = ctypes.c_int(0)
-        scans = 2 if -(-info.ncells // 2048) <= 1024 else 3
-        assert lib.ade_sweep_launches_per_step(ctx, ctypes.byref(v)) == 0 and v.value == 4 + scans + 4
+        # count, the one-pass scan, place, order; the sets' gather; 2 per group (4 here)
+        assert lib.ade_sweep_launches_per_step(ctx, ctypes.byref(v)) == 0 and v.value == 4 + 1 + 4
     finally:
         lib.ade_sweep_destroy(ctx)
     bad = theta.copy()
