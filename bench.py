@@ -464,6 +464,7 @@ def run_batched(args):
         torch.cuda.synchronize()
         pp_ms += e0.elapsed_time(e1)
     pp_value, pp_ms, _ = sharding.aggregate(2.0 * pairs * args.steps, pp_ms, device=agg_dev)
+    pp_launches = sum(ade.launches_per_step(sm.ctx) for sm in sims)
     for sm in sims:
         sm.close()
 
@@ -548,7 +549,7 @@ def run_batched(args):
                   "persistent_grid": info0.tile[1], "work_items": info0.tile[2],
                   "cell_subdiv": [b.plume_info(i).cell_subdiv for i in range(len(plumes))]},
         "per_plume_launches": {"value": pp_value, "ms_per_step": pp_ms / args.steps,
-                               "launches_per_step": 8 * len(plumes),
+                               "launches_per_step": pp_launches,
                                "batched_speedup": value / pp_value},
         "steps_per_s": 1e3 / ms_per_step, "interactions_per_step": all_units / args.steps,
         "roofline": roofline, "e2e": e2e, "clocks": clk,

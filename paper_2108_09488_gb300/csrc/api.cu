@@ -1352,7 +1352,7 @@ struct ade_batch {
 namespace {
 
 struct BatchLayout {
-    size_t keys, rank, count, block_sums, perm_tmp, perm, cell_start, P0, P1, pred, corr, tiles,
+    size_t keys, rank, count, block_sums, tile_sums, perm_tmp, perm, cell_start, P0, P1, pred, corr, tiles,
         queue, plume_of, offsets, stats, status, pairs, total;
 };
 
@@ -1369,6 +1369,7 @@ BatchLayout batch_layout(int P, int N, int NC_max, int max_tiles)
     L.rank = take((size_t)N * 4);
     L.count = take((size_t)NC_max * 4);
     L.block_sums = take((size_t)ade::scan_blocks(NC_max) * 4);
+    L.tile_sums = take(ade::tile_sums_bytes(NC_max));
     L.perm_tmp = take((size_t)N * 4);
     L.perm = take((size_t)N * 4);
     L.cell_start = take(((size_t)NC_max + 1) * 4);
@@ -1619,6 +1620,7 @@ int ade_batch_init(ade_batch **out, int nplumes, const ade_params *p, const int 
     b->w.perm_tmp = at<uint32_t>(workspace_dev, L.perm_tmp);
     b->w.perm = at<uint32_t>(workspace_dev, L.perm);
     b->w.cell_start = at<uint32_t>(workspace_dev, L.cell_start);
+    b->w.tile_sums = at<uint32_t>(workspace_dev, L.tile_sums);   // cleared with the counts every build
     b->w.P0 = at<uint4>(workspace_dev, L.P0);
     b->w.P1 = at<uint4>(workspace_dev, L.P1);
     b->w.status = at<int>(workspace_dev, L.status);
@@ -1933,7 +1935,7 @@ int ade_batch_step_timed(ade_batch *b, double *phase_ms, void *stream)
 int ade_batch_launches_per_step(const ade_batch *b, int *launches)
 {
     if (!b || !launches) return fail(ADE_ERR_ARG, "NULL argument");
-    *launches = 8;  // count, 3 scan launches, place, order, predictor, corrector
+    *launches = b->w.tile_sums ? 6 : 8;  // count, the scan (one launch, else three), place, order, predictor, corrector
     return ADE_OK;
 }
 

@@ -53,27 +53,10 @@ constexpr int kTileStride = 32;   // words between two tile totals: one 128-byte
                                   // totals' atomics spread over the L2 slices
 constexpr int kTileWindow = 8;    // tiles a block aggregates in shared memory (from its lowest)
 
-__global__ __launch_bounds__(kThreads) void k_count(const uint32_t *__restrict__ xq, int n, int dim,
-                                                    int ncx, int ncy, int ncz,
-                                                    uint32_t *__restrict__ keys,
-                                                    uint32_t *__restrict__ rank,
-                                                    uint32_t *__restrict__ count,
-                                                    uint4 *__restrict__ pencil, int npencils,
-                                                    uint32_t *__restrict__ tile_sums)
+// Adds the block's particles to their tiles' totals (tile = key / kTileCells, 0xffffffff for no
+// particle).  Every thread of the block must call it.
+__device__ __forceinline__ void add_tile_totals(uint32_t tile, uint32_t *__restrict__ tile_sums)
 {
-    pdl_wait();
-    pdl_trigger();
-    const int i = blockIdx.x * kThreads + threadIdx.x;
-    if (pencil)   // empty boxes {min y, max y, min z, max z} = {+inf, 0, +inf, 0}: k_order merges into them
-        for (int q = i; q < npencils; q += gridDim.x * kThreads) pencil[q] = make_uint4(kInfBits, 0u, kInfBits, 0u);
-    uint32_t tile = 0xffffffffu;
-    if (i < n) {
-        const uint32_t key = cell_key(xq, n, i, dim, ncx, ncy, ncz);
-        keys[i] = key;
-        rank[i] = atomicAdd(count + key, 1u);
-        tile = key / (uint32_t)kTileCells;
-    }
-    if (!tile_sums) return;
     // Every particle also counts toward its tile's total.  Particles of a block mostly fall in a
     // few neighbouring tiles: a warp whose particles share one tile adds once, the block sums
     // tiles [t0, t0 + kTileWindow) in shared memory (t0 its lowest tile) and adds each once.
@@ -101,6 +84,29 @@ __global__ __launch_bounds__(kThreads) void k_count(const uint32_t *__restrict__
     __syncthreads();
     if (threadIdx.x < kTileWindow && s_win[threadIdx.x])
         atomicAdd(tile_sums + (size_t)(t0 + threadIdx.x) * kTileStride, s_win[threadIdx.x]);
+}
+
+__global__ __launch_bounds__(kThreads) void k_count(const uint32_t *__restrict__ xq, int n, int dim,
+                                                    int ncx, int ncy, int ncz,
+                                                    uint32_t *__restrict__ keys,
+                                                    uint32_t *__restrict__ rank,
+                                                    uint32_t *__restrict__ count,
+                                                    uint4 *__restrict__ pencil, int npencils,
+                                                    uint32_t *__restrict__ tile_sums)
+{
+    pdl_wait();
+    pdl_trigger();
+    const int i = blockIdx.x * kThreads + threadIdx.x;
+    if (pencil)   // empty boxes {min y, max y, min z, max z} = {+inf, 0, +inf, 0}: k_order merges into them
+        for (int q = i; q < npencils; q += gridDim.x * kThreads) pencil[q] = make_uint4(kInfBits, 0u, kInfBits, 0u);
+    uint32_t tile = 0xffffffffu;
+    if (i < n) {
+        const uint32_t key = cell_key(xq, n, i, dim, ncx, ncy, ncz);
+        keys[i] = key;
+        rank[i] = atomicAdd(count + key, 1u);
+        tile = key / (uint32_t)kTileCells;
+    }
+    if (tile_sums) add_tile_totals(tile, tile_sums);
 }
 
 // Three-launch exclusive scan of count[0..m) into start[0..m] (start[m] = total).
@@ -635,15 +641,21 @@ __global__ __launch_bounds__(kThreads) void k_count_batch(const uint32_t *__rest
                                                           const uint16_t *__restrict__ plume_of,
                                                           uint32_t *__restrict__ keys,
                                                           uint32_t *__restrict__ rank,
-                                                          uint32_t *__restrict__ count)
+                                                          uint32_t *__restrict__ count,
+                                                          uint32_t *__restrict__ tile_sums)
 {
     const int i = blockIdx.x * kThreads + threadIdx.x;
-    if (i >= n) return;
-    const RateParams &d = descs[__ldg(plume_of + i)];
-    const int np = d.n, goff = d.goff;
-    const uint32_t key = (uint32_t)d.coff + cell_key(xq + (size_t)dim * goff, np, i - goff, dim, d.ncx, d.ncy, d.ncz);
-    keys[i] = key;
-    rank[i] = atomicAdd(count + key, 1u);
+    uint32_t tile = 0xffffffffu;
+    if (i < n) {
+        const RateParams &d = descs[__ldg(plume_of + i)];
+        const int np = d.n, goff = d.goff;
+        const uint32_t key =
+            (uint32_t)d.coff + cell_key(xq + (size_t)dim * goff, np, i - goff, dim, d.ncx, d.ncy, d.ncz);
+        keys[i] = key;
+        rank[i] = atomicAdd(count + key, 1u);
+        tile = key / (uint32_t)kTileCells;
+    }
+    if (tile_sums) add_tile_totals(tile, tile_sums);
 }
 
 struct BatchRec {
@@ -704,17 +716,23 @@ cudaError_t launch_build_cells_batch(int dim, const uint32_t *xq, const float *C
                                      const RateParams *descs, const uint16_t *plume_of,
                                      const Work &w, cudaStream_t s)
 {
+    const int nt = tile_blocks(ncells);
     cudaError_t e = cudaMemsetAsync(w.count, 0, (size_t)ncells * sizeof(uint32_t), s);
+    if (e == cudaSuccess && w.tile_sums) e = cudaMemsetAsync(w.tile_sums, 0, (size_t)nt * kTileStride * 4, s);
     if (e != cudaSuccess) return e;
     const int nb = (n + kThreads - 1) / kThreads;
     if (nb > 0)
-        k_count_batch<<<nb, kThreads, 0, s>>>(xq, n, dim, descs, plume_of, w.keys, w.rank, w.count);
-    const int sb = scan_blocks(ncells);
-    k_scan_blocks<<<sb, kThreads, 0, s>>>(w.count, ncells, w.block_sums);
-    k_scan_top<<<1, kThreads, 0, s>>>(w.block_sums, sb);
-    k_scan_apply<false><<<sb, kThreads, 0, s>>>(w.count, ncells, w.block_sums, w.cell_start);
+        k_count_batch<<<nb, kThreads, 0, s>>>(xq, n, dim, descs, plume_of, w.keys, w.rank, w.count, w.tile_sums);
+    if (w.tile_sums) {
+        k_scan_tiles<<<nt, kThreads, 0, s>>>(w.count, ncells, w.cell_start, (const uint32_t *)w.tile_sums);
+    } else {
+        const int sb = scan_blocks(ncells);
+        k_scan_blocks<<<sb, kThreads, 0, s>>>(w.count, ncells, w.block_sums);
+        k_scan_top<<<1, kThreads, 0, s>>>(w.block_sums, sb);
+        k_scan_apply<false><<<sb, kThreads, 0, s>>>(w.count, ncells, w.block_sums, w.cell_start);
+    }
     if (nb > 0) {
-        k_place<<<nb, kThreads, 0, s>>>(w.keys, w.rank, n, w.cell_start, w.perm_tmp, nullptr, 0);
+        k_place<<<nb, kThreads, 0, s>>>(w.keys, w.rank, n, w.cell_start, w.perm_tmp, w.tile_sums, nt);
         k_order_batch<<<(ncells + kThreads - 1) / kThreads, kThreads, 0, s>>>(
             w.cell_start, ncells, w.perm_tmp, xq, C, n, dim, descs, plume_of, w.perm, w.P0);
     }
