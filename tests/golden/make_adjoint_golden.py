@@ -6,8 +6,8 @@ Only the oracle and the seeded inputs are used.  The target field C* is the orac
 precision the GPU library receives it in); the misfit is J = 1/2 sum_a (C_a^N - C*_a)^2 at
 theta = (1e-2, 1e-3, 1e-6).  Recorded: dt, J, dJ/dtheta by the oracle's tangent-linear model, and
 dJ/dtheta by FP64 central differences with eps = 1e-4 theta_k.  The dispersion tensor is Eq. 3, the
-rate Eq. 4-5 and the step Eq. 8-9 (Sec. 2); the inversion problem is this build's (the paper has no
-adjoint).
+rate Eq. 4-5 and the step Eq. 8-9 (Sec. 2); the inversion problem is derived from them (the paper
+has no adjoint).
 
 Usage: python tests/golden/make_adjoint_golden.py   (a few minutes on a multi-core host)
 """
