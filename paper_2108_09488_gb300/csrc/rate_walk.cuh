@@ -506,16 +506,29 @@ __device__ __forceinline__ void neumaier_add2(float2 &sum, float2 &comp, float2 
 // One trimmed row of the paired walk: cells [cx0 + floor(xa - xe), cx0 + floor(xb + xe)] of pencil
 // pidx, clipped to the row's half-width w = wx & 0xff; bit 24 of wx marks the targets' own pencil.
 template <int DIM, int KERNEL, bool ISO, bool BF>
+// The row's first and last candidates lie in whole cells at the ends of the range; one whose x
+// word is farther than xe (rounded up to words: wpc words per cell) left of the left target xl,
+// or right of the right target xr, is beyond H (1 + 2^-12) of both (the same bound as the cell
+// range) and adds an exact zero, so it is dropped before the loop (when every lane of a warp drops
+// one, the warp walks one candidate fewer).
 __device__ __forceinline__ void pair_trim_row(const uint4 *__restrict__ Pe, const uint32_t *__restrict__ cs,
                                               int pidx, int wx, float xe, float xa, float xb, int cx0, int dcx,
                                               int ncx, const uint4 &pa0, const uint4 &pa1, float2 Ca,
-                                              const PairConst2 &k2, float2 &acc, float2 &comp)
+                                              const PairConst2 &k2, float2 &acc, float2 &comp, uint32_t xl,
+                                              uint32_t xr, float wpc)
 {
     const int w = wx & 0xff;
     const int lo = cx0 + max(__float2int_rd(xa - xe), -w);
     const int hi = cx0 + min(__float2int_rd(xb + xe), w + dcx) + 1;
     int s0, e0, s1, e1;
     row_ranges(cs, pidx * ncx, lo, hi, ncx, s0, e0, s1, e1);
+    const int xw = __float2int_ru(fminf(xe * wpc, 2.0e9f));
+    if (s0 < e0 && (int)(__ldg(&Pe[s0].x) - xl) < -xw) ++s0;
+    if (e1 > s1) {
+        if ((int)(__ldg(&Pe[e1 - 1].x) - xr) > xw) --e1;
+    } else if (e0 > s0 && (int)(__ldg(&Pe[e0 - 1].x) - xr) > xw) {
+        --e0;
+    }
     float2 rs = f2(0.f, 0.f);
     if (!BF || (wx >> 24) != 0)   // the targets' own cell row
         pair_row2<DIM, KERNEL, ISO, true, BF>(Pe, s0, e0, s1, e1, pa0, pa1, Ca, k2, rs);
@@ -555,6 +568,9 @@ __device__ void rate_direct_pair(const uint4 *__restrict__ Pe, const uint32_t *_
         // the pair's x extent in cell coordinates from cell cx0 (two particles of one cell are
         // ordered by caller index, not by position)
         const float xa = fminf(m0.fx, m1.fx + (float)dcx), xb = fmaxf(m0.fx, m1.fx + (float)dcx);
+        const bool first_left = m0.fx <= m1.fx + (float)dcx;   // which particle is xa
+        const uint32_t xl = first_left ? pa0.x : pa1.x, xr = first_left ? pa1.x : pa0.x;
+        const float wpc = 4294967296.f / (float)ncx;              // x words per cell
         if (coop) {
             constexpr unsigned kFull = 0xffffffffu;
             warp_interval<DIM>(ylo, yhi, zlo, zhi);
@@ -566,7 +582,7 @@ __device__ void rate_direct_pair(const uint4 *__restrict__ Pe, const uint32_t *_
                     const int b = __ffs(mask) - 1;
                     pair_trim_row<DIM, KERNEL, ISO, BF>(Pe, cs, __shfl_sync(kFull, pidx, b), __shfl_sync(kFull, wx, b),
                                                         __shfl_sync(kFull, xe, b), xa, xb, cx0, dcx, ncx, pa0, pa1,
-                                                        Ca, k2, acc, comp);
+                                                        Ca, k2, acc, comp, xl, xr, wpc);
                 }
             }
         } else {
@@ -579,7 +595,7 @@ __device__ void rate_direct_pair(const uint4 *__restrict__ Pe, const uint32_t *_
                 const float t = g.Hm2 - e2;
                 const float xe = fmaf(t * rsqrt_ftz(t), g.inv_wx, 1.f / 4096.f);
                 pair_trim_row<DIM, KERNEL, ISO, BF>(Pe, cs, pidx, r.wdd | (r.off == 0 ? 1 << 24 : 0), xe, xa, xb,
-                                                    cx0, dcx, ncx, pa0, pa1, Ca, k2, acc, comp);
+                                                    cx0, dcx, ncx, pa0, pa1, Ca, k2, acc, comp, xl, xr, wpc);
             }
         }
     } else {
