@@ -92,23 +92,33 @@ MUFU_LANES_PER_SM = 16
 # corrector launch, from the ncu capture summarised in the named profile, keyed by workload and
 # walk, with the digest of the kernel sources the capture was taken of: a walk without a capture,
 # or whose sources have changed since, reports null traffic.
-TRAFFIC_PER_LAUNCH = {
-    ("cube-128-h2", "direct-branch-free-trimmed-paired"): (53.73e6, "profiles/k_rate_cube128.md", "05e611b359adae95"),
-    ("ladder-1024-n120-r10", "direct-branch-free-paired"): (23.88e6, "profiles/k_rate_ladder1024.md", "05e611b359adae95"),
-    ("batched-64", None): (42.26e6, "profiles/k_rate_batch_batched64.md", "05e611b359adae95"),
-    ("paper-1m-n31k-c4", "direct-branch-free-trimmed-paired"): (16.10e6, "profiles/k_rate_paper1m.md", "05e611b359adae95"),
-    ("field-1024-n120-r10", "velocity-field-direct"): (82.34e6, "profiles/k_rate_field_field1024.md", "05e611b359adae95"),
-    ("sweep-512-8", None): (18.25e6, "profiles/k_rate_sweep_sweep512.md", "05e611b359adae95"),
+# The source files each rate kernel is built from: a capture is tied to a digest of its own files.
+KERNEL_FILES = {
+    "pair": ("rate_pair.cu", "rate_walk.cuh", "rate_common.cuh", "ade_internal.h"),
+    "batch": ("rate.cu", "rate_walk.cuh", "rate_common.cuh", "ade_internal.h"),
+    "field": ("rate_field.cu", "rate_common.cuh", "ade_internal.h"),
+    "sweep": ("sweep.cu", "rate_common.cuh", "ade_internal.h"),
 }
-KERNEL_SOURCES = ("rate_walk.cuh", "rate_common.cuh", "rate.cu", "rate_pair.cu", "rate_field.cu", "sweep.cu",
-                  "ade_internal.h")
+# (workload, walk) -> (DRAM bytes read + written per launch, mean of one predictor and one corrector
+# from an ncu --set full capture, the profile that records it, kernel family, digest of its files)
+TRAFFIC_PER_LAUNCH = {
+    ("cube-128-h2", "direct-branch-free-trimmed-paired"): (53.62e6, "profiles/k_rate_cube128.md", "pair", "dd0f33488e40561a"),
+    ("ladder-1024-n120-r10", "direct-branch-free-trimmed-paired"): (25.13e6, "profiles/k_rate_ladder1024.md", "pair",
+                                                              "dd0f33488e40561a"),
+    ("batched-64", None): (42.19e6, "profiles/k_rate_batch_batched64.md", "batch", "f85a9b4952214a0c"),
+    ("paper-1m-n31k-c4", "direct-branch-free-trimmed-paired"): (16.09e6, "profiles/k_rate_paper1m.md", "pair",
+                                                          "dd0f33488e40561a"),
+    ("field-1024-n120-r10", "velocity-field-direct"): (82.34e6, "profiles/k_rate_field_field1024.md", "field",
+                                                       "33d53e1a706f6232"),
+    ("sweep-512-8", None): (18.25e6, "profiles/k_rate_sweep_sweep512.md", "sweep", "3fed28905bd475a7"),
+}
 
 
-def kernel_digest():
-    """Digest of the interaction kernels' sources (to tie a traffic capture to a kernel revision)."""
+def kernel_digest(family="pair"):
+    """Digest of one rate kernel family's source files (ties a traffic capture to a kernel revision)."""
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_FILES[family]:
         with open(os.path.join(ROOT, "paper_2108_09488_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -117,10 +127,10 @@ def kernel_digest():
 def traffic_entry(workload, walk):
     """(bytes per launch or None, source note) for the roofline line."""
     e = TRAFFIC_PER_LAUNCH.get((workload, walk))
-    if e is None:
+    if e is None or e[0] is None:
         return None, "no ncu capture of this walk on this workload"
-    nbytes, profile, digest = e
-    if digest != kernel_digest():
+    nbytes, profile, family, digest = e
+    if digest != kernel_digest(family):
         return None, f"stale: the kernel sources changed since the capture in {profile}"
     return nbytes, f"{profile} (kernel sources {digest})"
 
