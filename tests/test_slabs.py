@@ -163,7 +163,7 @@ def _fixed_worker(rank, world, port, dt, nsteps, q):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("world", [2, 3, 4])
 def test_fixed_point_slabs_match_serial_oracle_run(orc, world):
     """Halo and migration records in the library's format (uint32 position words + float32 C bits)
     over gloo: the first distributed evaluation and three steps equal the serial run of the same
